@@ -1,0 +1,745 @@
+/*
+ * avalanche_oracle.c -- TEST INFRASTRUCTURE, NOT PART OF THE PRODUCT PATH.
+ *
+ * A plain, sequential, FP64 CPU restatement of microscopic electron
+ * transport with avalanche multiplication: the AvalancheMicroscopic method
+ * that "Accelerating Garfield++ with CUDA" (arXiv:2509.15377) moves to GPUs.
+ * Only the test suite, the package's smoke check and the benchmark's CPU
+ * baseline leg may load this file.  It shares no code, header, table or
+ * constant with the CUDA library; both sides are written independently from
+ * the paper and from the published definitions cited below.
+ *
+ * What the method computes (paper Sec. 2, Fig. 2):
+ *   every electron of an avalanche is transported collision by collision
+ *   ("electron transport"); an ionising collision adds a new electron to the
+ *   stack ("stack processing"); the avalanche is complete when every electron
+ *   carries a non-zero status code.  The paper does not spell out the
+ *   transport physics; it relies on semi-classical Monte Carlo with the
+ *   null-collision technique of Skullerud (Sec. 1, ref. HRSkullerud_1968) and
+ *   tabulated per-level collision rates (Sec. 1, ref. Biagi).  The concrete
+ *   step used here, in the order the loop below takes it:
+ *     1. four uniforms from Philox4x32-10 keyed by (seed, avalanche) with the
+ *        counter (flight index, 0, electron id);
+ *     2. the field E (and uniform B) at the start of the flight, held
+ *        constant for the flight;
+ *     3. free flight dt = -ln(u0)/nu_max, truncated at the time limit, with
+ *        the exact ballistic (E) or Lorentz (E and B) solution;
+ *     4. kinetic energy from the velocity;
+ *     5. boundary test ("Position is valid?", Fig. 2) -> non-zero status;
+ *     6. linear interpolation of the cumulative per-level rates at the
+ *        energy;
+ *     7. real or null collision: R = u1*nu_max against the cumulative rates,
+ *        a level whose threshold exceeds the energy counts as null;
+ *     8. elastic (isotropic, recoil loss), excitation (threshold loss) or
+ *        ionisation (threshold loss, uniform split of the remainder,
+ *        isotropic secondary pushed to the stack, Fig. 2 "ionisation").
+ *
+ * Units: cm, ns, eV, V/cm, T.  Electron charge-to-mass ratio from CODATA
+ * 2018, e/m = 1.75882001076e11 C/kg, which gives an acceleration of
+ * 1.75882001076e-3 cm/ns^2 per V/cm and a cyclotron rate of 175.882001076
+ * rad/ns per tesla.
+ *
+ * Pins (tests under tests/, marked "not gpu"):
+ *   philox4x32_10 ...... published known-answer vectors (tests/golden).
+ *   child_uid .......... SplitMix64 published output sequence (tests/golden)
+ *                        and uniqueness over whole avalanches.
+ *   flight ............. RK4 integration of the Lorentz force; the energy
+ *                        ledger (kinetic energy change = field work).
+ *   field .............. closed-form coaxial field; trilinear exact on affine
+ *                        maps.
+ *   table/selection .... brute-force level frequencies vs rate/nu_max.
+ *   transport .......... drift velocity eE/(m nu) and the closed-form
+ *                        transverse spread for a constant-rate elastic gas;
+ *                        mean energy (1-r)^N for recoil-only cooling; Yule
+ *                        (geometric) electron count with mean exp(nu_i T)
+ *                        for a constant ionisation rate; Langevin E x B drift;
+ *                        charge and energy conservation.
+ *   ionisation split ... parity unpinned beyond the energy ledger (the paper
+ *                        names no sharing model; the uniform split is a
+ *                        reading, see the design notes).
+ *
+ * Build: gcc -O2 -std=c11 -ffp-contract=off -fPIC -shared -pthread -lm.
+ * Floating-point contraction is off so that every product and sum is the
+ * one written here.
+ */
+#include <math.h>
+#include <pthread.h>
+#include <stdint.h>
+#include <stdlib.h>
+#include <string.h>
+
+/* ---------------------------------------------------------------- units */
+#define OR_ACCEL_PER_VCM 1.75882001076e-3 /* (e/m) * 1e-14: cm/ns^2 per V/cm */
+#define OR_OMEGA_PER_T 175.882001076      /* (e/m) * 1e-9: rad/ns per T      */
+#define OR_PI 3.14159265358979323846
+
+/* electron status codes (non-zero = transport finished, paper Sec. 2) */
+enum {
+    OR_ACTIVE = 0,
+    OR_ANODE = 1,        /* plate: z >= gap */
+    OR_CATHODE = 2,      /* plate: z < 0 */
+    OR_WIRE = 3,         /* coax / grid: r <= wire radius */
+    OR_TUBE = 4,         /* coax: r >= tube radius */
+    OR_OUT_OF_MAP = 5,   /* grid: outside the map box */
+    OR_TIME = 6,         /* time limit reached */
+    OR_COLL_LIMIT = 7,   /* real-collision limit reached */
+    OR_FLIGHT_LIMIT = 8  /* 2^32-1 flights (counter exhausted) */
+};
+
+enum { OR_ELASTIC = 0, OR_EXCITATION = 1, OR_IONISATION = 2 };
+enum { OR_UNIFORM = 0, OR_PLATE = 1, OR_COAX = 2, OR_GRID = 3 };
+
+typedef struct {
+    int32_t n_levels;
+    int32_t n_nodes;
+    double d_eps;              /* eV between table nodes; node k at k*d_eps */
+    const int32_t *level_type; /* [n_levels] */
+    const double *threshold;   /* [n_levels] eV (energy lost) */
+    const double *rate;        /* [n_nodes][n_levels], 1/ns */
+    double recoil;             /* 2m/M for elastic recoil loss; 0 = none */
+    double nu_max;             /* 1/ns; 0 = (1+1e-6) * max total rate */
+} or_gas;
+
+typedef struct {
+    int32_t kind;
+    double e0;                 /* UNIFORM/PLATE: E = (0,0,-e0) V/cm */
+    double gap;                /* PLATE: anode at z = gap (cm) */
+    double wire_r, tube_r, voltage; /* COAX (and GRID wire test) */
+    double b[3];               /* uniform magnetic field, T */
+    int32_t nx, ny, nz;        /* GRID nodes */
+    double origin[3], spacing[3];
+    const float *grid;         /* GRID: host float4 (Ex,Ey,Ez,-) per node, x fastest */
+} or_field;
+
+typedef struct {
+    int64_t n_primaries;
+    int32_t n_avalanches;
+    const double *x, *y, *z, *t, *e; /* primary position, time, energy */
+    const double *dx, *dy, *dz;      /* primary unit direction */
+    const int32_t *aval;             /* avalanche of each primary */
+    const uint64_t *uid;             /* electron id of each primary */
+    const double *aval_field;        /* PLATE: per-avalanche |E| or NULL */
+    uint64_t seed;
+    double t_max;                    /* ns; <= 0 means none */
+    uint32_t coll_limit;             /* real collisions; 0 means none */
+    int32_t n_threads;
+} or_run_args;
+
+/* ------------------------------------------------ Philox4x32-10
+ * J. K. Salmon, M. A. Moraes, R. O. Dror, D. E. Shaw, "Parallel random
+ * numbers: as easy as 1, 2, 3", SC'11.  One round maps the counter
+ * (c0,c1,c2,c3) with the round key (k0,k1) to
+ *   (hi(M1*c2) ^ c1 ^ k0, lo(M1*c2), hi(M0*c0) ^ c3 ^ k1, lo(M0*c0)),
+ * the key is advanced by the Weyl constants between rounds, ten rounds. */
+void or_philox4x32_10(const uint32_t ctr[4], const uint32_t key[2], uint32_t out[4])
+{
+    const uint32_t M0 = 0xD2511F53u, M1 = 0xCD9E8D57u;
+    const uint32_t W0 = 0x9E3779B9u, W1 = 0xBB67AE85u;
+    uint32_t c0 = ctr[0], c1 = ctr[1], c2 = ctr[2], c3 = ctr[3];
+    uint32_t k0 = key[0], k1 = key[1];
+    for (int round = 0; round < 10; ++round) {
+        uint64_t p0 = (uint64_t)M0 * c0;
+        uint64_t p1 = (uint64_t)M1 * c2;
+        uint32_t n0 = (uint32_t)(p1 >> 32) ^ c1 ^ k0;
+        uint32_t n1 = (uint32_t)p1;
+        uint32_t n2 = (uint32_t)(p0 >> 32) ^ c3 ^ k1;
+        uint32_t n3 = (uint32_t)p0;
+        c0 = n0; c1 = n1; c2 = n2; c3 = n3;
+        k0 += W0;
+        k1 += W1;
+    }
+    out[0] = c0; out[1] = c1; out[2] = c2; out[3] = c3;
+}
+
+/* Open-interval uniform from one 32-bit word: (w + 1/2) / 2^32, exact. */
+static double uniform01(uint32_t w) { return ((double)w + 0.5) * (1.0 / 4294967296.0); }
+
+/* The four uniforms of draw `sub` of flight `flight` of electron `uid`. */
+static void draw4(uint64_t seed, int32_t aval, uint64_t uid, uint32_t flight,
+                  uint32_t sub, double u[4])
+{
+    uint32_t key[2] = {(uint32_t)seed ^ (uint32_t)aval, (uint32_t)(seed >> 32)};
+    uint32_t ctr[4] = {flight, sub, (uint32_t)uid, (uint32_t)(uid >> 32)};
+    uint32_t w[4];
+    or_philox4x32_10(ctr, key, w);
+    for (int i = 0; i < 4; ++i) u[i] = uniform01(w[i]);
+}
+
+/* ------------------------------------------------ SplitMix64 output function
+ * G. L. Steele, D. Lea, C. H. Flood, "Fast splittable pseudorandom number
+ * generators", OOPSLA 2014: z ^= z>>30; z *= 0xbf58476d1ce4e5b9;
+ * z ^= z>>27; z *= 0x94d049bb133111eb; z ^= z>>31. */
+uint64_t or_splitmix64_mix(uint64_t z)
+{
+    z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+    z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+    return z ^ (z >> 31);
+}
+
+/* Id of the electron created by ionisation in flight `flight` of `parent`:
+ * the SplitMix64 output of parent + golden * (flight + 1). */
+uint64_t or_child_uid(uint64_t parent, uint32_t flight)
+{
+    return or_splitmix64_mix(parent + 0x9E3779B97F4A7C15ull * ((uint64_t)flight + 1u));
+}
+
+/* ------------------------------------------------ field (paper Fig. 2,
+ * "Find E field"): E in V/cm at r.  Returns 0, or -1 if the grid is
+ * queried outside its box (the caller's boundary test runs first). */
+static void grid_node(const or_field *f, int i, int j, int k, double e[3])
+{
+    const float *p = f->grid + 4 * (((int64_t)k * f->ny + j) * f->nx + i);
+    e[0] = p[0]; e[1] = p[1]; e[2] = p[2];
+}
+
+void or_field_eval(const or_field *f, double plate_e, const double r[3], double e[3])
+{
+    e[0] = e[1] = e[2] = 0.0;
+    if (f->kind == OR_UNIFORM) {
+        e[2] = -f->e0;
+    } else if (f->kind == OR_PLATE) {
+        e[2] = -plate_e;
+    } else if (f->kind == OR_COAX) {
+        /* E = V / (r ln(b/a)) along r-hat in the transverse plane */
+        double r2 = r[0] * r[0] + r[1] * r[1];
+        double s = f->voltage / (log(f->tube_r / f->wire_r) * r2);
+        e[0] = s * r[0];
+        e[1] = s * r[1];
+    } else { /* OR_GRID: trilinear interpolation of the node values */
+        int n[3] = {f->nx, f->ny, f->nz};
+        int idx[3];
+        double w[3];
+        for (int d = 0; d < 3; ++d) {
+            double g = (r[d] - f->origin[d]) / f->spacing[d];
+            int i = (int)floor(g);
+            if (i < 0) i = 0;
+            if (i > n[d] - 2) i = n[d] - 2;
+            idx[d] = i;
+            w[d] = g - i;
+        }
+        for (int c = 0; c < 8; ++c) {
+            int di = c & 1, dj = (c >> 1) & 1, dk = (c >> 2) & 1;
+            double wt = (di ? w[0] : 1.0 - w[0]) * (dj ? w[1] : 1.0 - w[1]) *
+                        (dk ? w[2] : 1.0 - w[2]);
+            double en[3];
+            grid_node(f, idx[0] + di, idx[1] + dj, idx[2] + dk, en);
+            e[0] += wt * en[0];
+            e[1] += wt * en[1];
+            e[2] += wt * en[2];
+        }
+    }
+}
+
+/* ------------------------------------------------ boundary test
+ * ("Position is valid?", Fig. 2): 0 inside, else the status code. */
+int or_boundary(const or_field *f, const double r[3])
+{
+    if (f->kind == OR_PLATE) {
+        if (r[2] >= f->gap) return OR_ANODE;
+        if (r[2] < 0.0) return OR_CATHODE;
+    } else if (f->kind == OR_COAX) {
+        double r2 = r[0] * r[0] + r[1] * r[1];
+        if (r2 <= f->wire_r * f->wire_r) return OR_WIRE;
+        if (r2 >= f->tube_r * f->tube_r) return OR_TUBE;
+    } else if (f->kind == OR_GRID) {
+        double r2 = r[0] * r[0] + r[1] * r[1];
+        if (f->wire_r > 0.0 && r2 <= f->wire_r * f->wire_r) return OR_WIRE;
+        int n[3] = {f->nx, f->ny, f->nz};
+        for (int d = 0; d < 3; ++d) {
+            double hi = f->origin[d] + (n[d] - 1) * f->spacing[d];
+            if (r[d] < f->origin[d] || r[d] > hi) return OR_OUT_OF_MAP;
+        }
+    }
+    return 0;
+}
+
+/* ------------------------------------------------ free flight
+ * Exact motion over dt under constant acceleration a (cm/ns^2) and a
+ * uniform magnetic rotation vector w (rad/ns): dv/dt = a + v x w.
+ * With w = 0 this is r += v dt + a dt^2/2, v += a dt.  Otherwise the part
+ * along w-hat accelerates uniformly, the perpendicular part is the drift
+ * (a x w)/|w|^2 plus a rotation of the rest about w-hat by -|w| dt. */
+static double dot3(const double a[3], const double b[3])
+{
+    return a[0] * b[0] + a[1] * b[1] + a[2] * b[2];
+}
+
+static void cross3(const double a[3], const double b[3], double c[3])
+{
+    c[0] = a[1] * b[2] - a[2] * b[1];
+    c[1] = a[2] * b[0] - a[0] * b[2];
+    c[2] = a[0] * b[1] - a[1] * b[0];
+}
+
+void or_flight(double r[3], double v[3], const double a[3], const double w[3], double dt)
+{
+    double wn = sqrt(dot3(w, w));
+    if (wn == 0.0) {
+        for (int d = 0; d < 3; ++d) {
+            r[d] = r[d] + v[d] * dt + 0.5 * a[d] * dt * dt;
+            v[d] = v[d] + a[d] * dt;
+        }
+        return;
+    }
+    double bh[3] = {w[0] / wn, w[1] / wn, w[2] / wn};
+    double vpar = dot3(v, bh), apar = dot3(a, bh);
+    double axw[3];
+    cross3(a, w, axw);
+    double drift[3] = {axw[0] / (wn * wn), axw[1] / (wn * wn), axw[2] / (wn * wn)};
+    double u[3], bxu[3];
+    for (int d = 0; d < 3; ++d) u[d] = v[d] - vpar * bh[d] - drift[d];
+    cross3(bh, u, bxu);
+    double th = wn * dt, c = cos(th), s = sin(th);
+    for (int d = 0; d < 3; ++d) {
+        r[d] = r[d] + (vpar * dt + 0.5 * apar * dt * dt) * bh[d] + drift[d] * dt +
+               u[d] * (s / wn) - bxu[d] * ((1.0 - c) / wn);
+        v[d] = (vpar + apar * dt) * bh[d] + drift[d] + u[d] * c - bxu[d] * s;
+    }
+}
+
+/* ------------------------------------------------ rate table */
+typedef struct {
+    int L, N;
+    double d_eps, nu_max, recoil;
+    int type[64];
+    double thr[64];
+    double *cum; /* [N][L]: running sum over levels 0..j of the rate */
+} or_table;
+
+static int table_build(const or_gas *g, or_table *t)
+{
+    if (g->n_levels < 1 || g->n_levels > 64 || g->n_nodes < 2 || !(g->d_eps > 0.0)) return -1;
+    t->L = g->n_levels;
+    t->N = g->n_nodes;
+    t->d_eps = g->d_eps;
+    t->recoil = g->recoil;
+    for (int j = 0; j < t->L; ++j) {
+        t->type[j] = g->level_type[j];
+        t->thr[j] = g->threshold[j];
+    }
+    t->cum = (double *)malloc(sizeof(double) * (size_t)t->N * t->L);
+    if (!t->cum) return -1;
+    double top = 0.0;
+    for (int k = 0; k < t->N; ++k) {
+        double s = 0.0;
+        for (int j = 0; j < t->L; ++j) {
+            s += g->rate[(int64_t)k * t->L + j];
+            t->cum[(int64_t)k * t->L + j] = s;
+        }
+        if (s > top) top = s;
+    }
+    t->nu_max = g->nu_max > 0.0 ? g->nu_max : top * (1.0 + 1e-6);
+    if (t->nu_max < top) {
+        free(t->cum);
+        return -1;
+    }
+    return 0;
+}
+
+/* Cumulative rates at energy eps by linear interpolation between nodes;
+ * energies at or beyond the last node use the last node. */
+static void table_interp(const or_table *t, double eps, double *c)
+{
+    double x = eps / t->d_eps;
+    int k;
+    double f;
+    if (x >= (double)(t->N - 1)) {
+        k = t->N - 2;
+        f = 1.0;
+    } else {
+        k = (int)floor(x);
+        f = x - k;
+    }
+    const double *c0 = t->cum + (int64_t)k * t->L;
+    const double *c1 = c0 + t->L;
+    for (int j = 0; j < t->L; ++j) c[j] = c0[j] + f * (c1[j] - c0[j]);
+}
+
+/* Real or null collision (Fig. 2 "Collision?"): level index, or -1 for null. */
+static int table_select(const or_table *t, double eps, double u1)
+{
+    double c[64];
+    table_interp(t, eps, c);
+    double R = u1 * t->nu_max;
+    for (int j = 0; j < t->L; ++j) {
+        if (R < c[j]) {
+            if (t->type[j] != OR_ELASTIC && eps < t->thr[j]) return -1;
+            return j;
+        }
+    }
+    return -1;
+}
+
+/* Test hook: the selection above for a given gas, energy and uniform. */
+int or_select(const or_gas *g, double eps, double u1, double *nu_max_out)
+{
+    or_table t;
+    if (table_build(g, &t)) return -2;
+    int j = table_select(&t, eps, u1);
+    if (nu_max_out) *nu_max_out = t.nu_max;
+    free(t.cum);
+    return j;
+}
+
+/* ------------------------------------------------ per-avalanche storage */
+typedef struct {
+    double x0, y0, z0, t0, e0, x1, y1, z1, t1, e1;
+    int32_t status;
+    uint32_t n_flight;
+    uint64_t uid;
+    double ledger[4]; /* field work, inelastic loss, recoil loss, secondary share */
+} or_endpoint;
+
+typedef struct {
+    double r[3], v[3], t, e0;
+    uint64_t uid;
+} or_pending;
+
+typedef struct {
+    or_endpoint *ep;
+    int64_t n_ep, cap_ep;
+    or_pending *stack;
+    int64_t n_st, cap_st;
+    uint64_t *tally; /* [L+1] */
+    int err;
+} or_aval_out;
+
+static int push_pending(or_aval_out *o, const or_pending *p)
+{
+    if (o->n_st == o->cap_st) {
+        int64_t nc = o->cap_st ? 2 * o->cap_st : 64;
+        or_pending *ns = (or_pending *)realloc(o->stack, sizeof(or_pending) * nc);
+        if (!ns) return -1;
+        o->stack = ns;
+        o->cap_st = nc;
+    }
+    o->stack[o->n_st++] = *p;
+    return 0;
+}
+
+static or_endpoint *new_endpoint(or_aval_out *o)
+{
+    if (o->n_ep == o->cap_ep) {
+        int64_t nc = o->cap_ep ? 2 * o->cap_ep : 64;
+        or_endpoint *ne = (or_endpoint *)realloc(o->ep, sizeof(or_endpoint) * nc);
+        if (!ne) return NULL;
+        o->ep = ne;
+        o->cap_ep = nc;
+    }
+    or_endpoint *e = &o->ep[o->n_ep++];
+    memset(e, 0, sizeof(*e));
+    return e;
+}
+
+static double kinetic_energy(const double v[3]) { return dot3(v, v) / (2.0 * OR_ACCEL_PER_VCM); }
+static double speed_of(double eps) { return sqrt(2.0 * OR_ACCEL_PER_VCM * eps); }
+
+static void isotropic(double u_cos, double u_phi, double n[3])
+{
+    double ct = 1.0 - 2.0 * u_cos;
+    double st2 = 1.0 - ct * ct;
+    double st = st2 > 0.0 ? sqrt(st2) : 0.0;
+    double phi = 2.0 * OR_PI * u_phi;
+    n[0] = st * cos(phi);
+    n[1] = st * sin(phi);
+    n[2] = ct;
+}
+
+/* Elastic collision on a heavy target at rest: isotropic new direction n
+ * from (u_cos, u_phi); the energy is scaled by 1 - recoil*(1 - cos chi),
+ * chi the lab deflection angle and recoil = 2m/M (first order in m/M of
+ * the two-body kinematics).  Writes the new velocity. */
+void or_elastic(double recoil, const double v[3], double u_cos, double u_phi, double v_out[3])
+{
+    double n[3];
+    isotropic(u_cos, u_phi, n);
+    double eps = kinetic_energy(v);
+    double sp = sqrt(dot3(v, v));
+    double cchi = sp > 0.0 ? dot3(v, n) / sp : 0.0;
+    double s = speed_of(eps * (1.0 - recoil * (1.0 - cchi)));
+    v_out[0] = s * n[0]; v_out[1] = s * n[1]; v_out[2] = s * n[2];
+}
+
+/* Transport one electron until its status is non-zero (Fig. 2, dashed box). */
+static void transport_electron(const or_table *tb, const or_field *f, const or_run_args *a,
+                               int32_t aval, double plate_e, const or_pending *start,
+                               or_aval_out *o)
+{
+    double r[3] = {start->r[0], start->r[1], start->r[2]};
+    double v[3] = {start->v[0], start->v[1], start->v[2]};
+    double t = start->t;
+    uint32_t n_flight = 0, n_real = 0;
+    double work = 0.0, inel = 0.0, recoil = 0.0, share = 0.0;
+    double w[3] = {-OR_OMEGA_PER_T * f->b[0], -OR_OMEGA_PER_T * f->b[1],
+                   -OR_OMEGA_PER_T * f->b[2]}; /* electron: q = -e */
+    int status = or_boundary(f, r);
+    while (status == 0) {
+        if (n_flight == 0xFFFFFFFFu) {
+            status = OR_FLIGHT_LIMIT;
+            break;
+        }
+        const uint32_t flight = n_flight;
+        double u[4];
+        draw4(a->seed, aval, start->uid, flight, 0u, u);
+        /* field at the start of the flight, held for the flight */
+        double E[3];
+        or_field_eval(f, plate_e, r, E);
+        double acc[3] = {-OR_ACCEL_PER_VCM * E[0], -OR_ACCEL_PER_VCM * E[1],
+                         -OR_ACCEL_PER_VCM * E[2]};
+        /* null-collision free flight */
+        double dt = -log(u[0]) / tb->nu_max;
+        int timed = 0;
+        if (a->t_max > 0.0 && t + dt > a->t_max) {
+            dt = a->t_max - t;
+            timed = 1;
+        }
+        double r_before[3] = {r[0], r[1], r[2]};
+        or_flight(r, v, acc, w, dt);
+        t = timed ? a->t_max : t + dt;
+        n_flight = flight + 1u;
+        /* work done by the held field on the electron (eV): -E . dr */
+        work += -(E[0] * (r[0] - r_before[0]) + E[1] * (r[1] - r_before[1]) +
+                  E[2] * (r[2] - r_before[2]));
+        status = or_boundary(f, r);
+        if (status) break;
+        if (timed) {
+            status = OR_TIME;
+            break;
+        }
+        double eps = kinetic_energy(v);
+        int lvl = table_select(tb, eps, u[1]);
+        if (lvl < 0) {
+            o->tally[tb->L] += 1;
+            continue;
+        }
+        o->tally[lvl] += 1;
+        if (tb->type[lvl] == OR_ELASTIC) {
+            or_elastic(tb->recoil, v, u[2], u[3], v);
+            recoil += eps - kinetic_energy(v);
+        } else {
+            double n[3];
+            isotropic(u[2], u[3], n);
+            double eps_new = eps - tb->thr[lvl];
+            inel += tb->thr[lvl];
+            if (tb->type[lvl] == OR_IONISATION) {
+                /* the remainder is split uniformly; the new electron starts
+                 * here, now, in an independent isotropic direction */
+                double u2[4];
+                draw4(a->seed, aval, start->uid, flight, 1u, u2);
+                double eps_sec = u2[0] * eps_new;
+                eps_new = eps_new - eps_sec;
+                share += eps_sec;
+                double ns[3];
+                isotropic(u2[1], u2[2], ns);
+                double s = speed_of(eps_sec);
+                or_pending child;
+                child.r[0] = r[0]; child.r[1] = r[1]; child.r[2] = r[2];
+                child.t = t;
+                child.e0 = eps_sec;
+                child.v[0] = s * ns[0]; child.v[1] = s * ns[1]; child.v[2] = s * ns[2];
+                child.uid = or_child_uid(start->uid, flight);
+                if (push_pending(o, &child)) {
+                    o->err = -1;
+                    return;
+                }
+            }
+            double s = speed_of(eps_new);
+            v[0] = s * n[0]; v[1] = s * n[1]; v[2] = s * n[2];
+        }
+        n_real += 1u;
+        if (a->coll_limit && n_real >= a->coll_limit) {
+            status = OR_COLL_LIMIT;
+            break;
+        }
+    }
+    or_endpoint *e = new_endpoint(o);
+    if (!e) {
+        o->err = -1;
+        return;
+    }
+    e->x0 = start->r[0]; e->y0 = start->r[1]; e->z0 = start->r[2];
+    e->t0 = start->t; e->e0 = start->e0;
+    e->x1 = r[0]; e->y1 = r[1]; e->z1 = r[2];
+    e->t1 = t; e->e1 = kinetic_energy(v);
+    e->status = status;
+    e->n_flight = n_flight;
+    e->uid = start->uid;
+    e->ledger[0] = work; e->ledger[1] = inel; e->ledger[2] = recoil; e->ledger[3] = share;
+}
+
+/* ------------------------------------------------ driver */
+typedef struct {
+    const or_table *tb;
+    const or_field *f;
+    const or_run_args *a;
+    const int64_t *first;  /* [n_aval+1] offsets into order[] */
+    const int64_t *order;  /* primaries sorted by avalanche, stable */
+    or_aval_out *out;      /* [n_aval] */
+    int32_t next;          /* shared work counter */
+    pthread_mutex_t lock;
+} or_job;
+
+static void run_avalanche(or_job *J, int32_t av)
+{
+    or_aval_out *o = &J->out[av];
+    const or_run_args *a = J->a;
+    double plate_e = a->aval_field ? a->aval_field[av] : J->f->e0;
+    o->tally = (uint64_t *)calloc((size_t)J->tb->L + 1, sizeof(uint64_t));
+    if (!o->tally) {
+        o->err = -1;
+        return;
+    }
+    /* Push the primaries in reverse so they are taken in input order. */
+    for (int64_t q = J->first[av + 1] - 1; q >= J->first[av]; --q) {
+        int64_t p = J->order[q];
+        double s = speed_of(a->e[p]);
+        or_pending e;
+        e.r[0] = a->x[p]; e.r[1] = a->y[p]; e.r[2] = a->z[p];
+        e.t = a->t[p];
+        e.e0 = a->e[p];
+        e.v[0] = s * a->dx[p]; e.v[1] = s * a->dy[p]; e.v[2] = s * a->dz[p];
+        e.uid = a->uid[p];
+        if (push_pending(o, &e)) {
+            o->err = -1;
+            return;
+        }
+    }
+    /* "Next electron" until the stack is empty (Fig. 2). */
+    while (o->n_st > 0 && !o->err) {
+        or_pending e = o->stack[--o->n_st];
+        transport_electron(J->tb, J->f, a, av, plate_e, &e, o);
+    }
+}
+
+static void *worker(void *arg)
+{
+    or_job *J = (or_job *)arg;
+    for (;;) {
+        pthread_mutex_lock(&J->lock);
+        int32_t av = J->next++;
+        pthread_mutex_unlock(&J->lock);
+        if (av >= J->a->n_avalanches) break;
+        run_avalanche(J, av);
+    }
+    return NULL;
+}
+
+typedef struct {
+    int32_t n_aval, L;
+    or_aval_out *out;
+    int64_t total;
+} or_result;
+
+/* Run every avalanche.  Returns 0 and a result handle, or a negative code:
+ * -1 out of memory, -2 bad gas table, -3 bad arguments. */
+int or_run(const or_gas *g, const or_field *f, const or_run_args *a, or_result **res)
+{
+    *res = NULL;
+    if (a->n_avalanches < 0 || a->n_primaries < 0) return -3;
+    if (f->kind == OR_GRID && (f->nx < 2 || f->ny < 2 || f->nz < 2 || !f->grid)) return -3;
+    for (int64_t p = 0; p < a->n_primaries; ++p)
+        if (a->aval[p] < 0 || a->aval[p] >= a->n_avalanches) return -3;
+    or_table tb;
+    if (table_build(g, &tb)) return -2;
+    int32_t A = a->n_avalanches;
+    int64_t *first = (int64_t *)calloc((size_t)A + 1, sizeof(int64_t));
+    int64_t *order = (int64_t *)malloc(sizeof(int64_t) * (size_t)(a->n_primaries + 1));
+    or_aval_out *out = (or_aval_out *)calloc((size_t)A + 1, sizeof(or_aval_out));
+    if (!first || !order || !out) {
+        free(first); free(order); free(out); free(tb.cum);
+        return -1;
+    }
+    for (int64_t p = 0; p < a->n_primaries; ++p) first[a->aval[p] + 1] += 1;
+    for (int32_t k = 0; k < A; ++k) first[k + 1] += first[k];
+    {
+        int64_t *fill = (int64_t *)malloc(sizeof(int64_t) * ((size_t)A + 1));
+        if (!fill) {
+            free(first); free(order); free(out); free(tb.cum);
+            return -1;
+        }
+        memcpy(fill, first, sizeof(int64_t) * ((size_t)A + 1));
+        for (int64_t p = 0; p < a->n_primaries; ++p) order[fill[a->aval[p]]++] = p;
+        free(fill);
+    }
+    or_job J;
+    J.tb = &tb; J.f = f; J.a = a; J.first = first; J.order = order; J.out = out;
+    J.next = 0;
+    pthread_mutex_init(&J.lock, NULL);
+    int nt = a->n_threads > 0 ? a->n_threads : 1;
+    if (nt > 256) nt = 256;
+    pthread_t th[256];
+    int started = 0;
+    for (int i = 0; i < nt; ++i)
+        if (pthread_create(&th[i], NULL, worker, &J) == 0) ++started;
+    if (started == 0) worker(&J);
+    for (int i = 0; i < started; ++i) pthread_join(th[i], NULL);
+    pthread_mutex_destroy(&J.lock);
+    free(first);
+    free(order);
+    int err = 0;
+    int64_t total = 0;
+    for (int32_t k = 0; k < A; ++k) {
+        if (out[k].err) err = -1;
+        total += out[k].n_ep;
+        free(out[k].stack);
+        out[k].stack = NULL;
+    }
+    or_result *R = (or_result *)malloc(sizeof(or_result));
+    if (err || !R) {
+        for (int32_t k = 0; k < A; ++k) {
+            free(out[k].ep);
+            free(out[k].tally);
+        }
+        free(out); free(R); free(tb.cum);
+        return -1;
+    }
+    R->n_aval = A;
+    R->L = tb.L;
+    R->out = out;
+    R->total = total;
+    free(tb.cum);
+    *res = R;
+    return 0;
+}
+
+int64_t or_result_count(const or_result *R) { return R ? R->total : -1; }
+
+/* Copy the endpoints (avalanche by avalanche, in stack order), the number
+ * of electrons of each avalanche and its collision tallies ([L] real per
+ * level, then null flights) into caller arrays.  ledger may be NULL. */
+int or_result_fetch(const or_result *R, double *x0, double *y0, double *z0, double *t0,
+                    double *e0, double *x1, double *y1, double *z1, double *t1, double *e1,
+                    int32_t *status, int32_t *aval, uint64_t *uid, uint32_t *n_flight,
+                    double *ledger, uint64_t *electrons, uint64_t *tallies)
+{
+    if (!R) return -3;
+    int64_t i = 0;
+    for (int32_t k = 0; k < R->n_aval; ++k) {
+        const or_aval_out *o = &R->out[k];
+        electrons[k] = (uint64_t)o->n_ep;
+        for (int j = 0; j <= R->L; ++j) tallies[(int64_t)k * (R->L + 1) + j] = o->tally[j];
+        for (int64_t q = 0; q < o->n_ep; ++q, ++i) {
+            const or_endpoint *e = &o->ep[q];
+            x0[i] = e->x0; y0[i] = e->y0; z0[i] = e->z0; t0[i] = e->t0; e0[i] = e->e0;
+            x1[i] = e->x1; y1[i] = e->y1; z1[i] = e->z1; t1[i] = e->t1; e1[i] = e->e1;
+            status[i] = e->status;
+            aval[i] = k;
+            uid[i] = e->uid;
+            n_flight[i] = e->n_flight;
+            if (ledger)
+                for (int m = 0; m < 4; ++m) ledger[4 * i + m] = e->ledger[m];
+        }
+    }
+    return 0;
+}
+
+void or_result_free(or_result *R)
+{
+    if (!R) return;
+    for (int32_t k = 0; k < R->n_aval; ++k) {
+        free(R->out[k].ep);
+        free(R->out[k].tally);
+    }
+    free(R->out);
+    free(R);
+}

@@ -1,0 +1,256 @@
+"""ctypes wrapper around the plain-C FP64 oracle (avalanche_oracle.c).
+
+TEST INFRASTRUCTURE ONLY: imported by tests/, by the package smoke check and
+by bench.py's CPU-baseline leg; never by the product path.
+
+`build()` compiles the oracle with gcc (-O2, no floating-point contraction);
+`run()` transports a workload and returns numpy arrays of endpoints, the
+electron count of every avalanche and its collision tallies.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+import subprocess
+import threading
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_SRC = os.path.join(_HERE, "avalanche_oracle.c")
+_LIB_DIR = os.path.join(_HERE, "_build")
+_LIB = os.path.join(_LIB_DIR, "liboracle.so")
+_lock = threading.Lock()
+_lib = None
+
+__all__ = ["build", "philox4x32_10", "splitmix64_mix", "child_uid", "flight", "elastic", "field_eval",
+           "boundary", "select", "run", "default_threads"]
+
+
+def build(force: bool = False) -> str:
+    """Compile the oracle shared library (gcc, a second or two)."""
+    os.makedirs(_LIB_DIR, exist_ok=True)
+    if force or not os.path.exists(_LIB) or os.path.getmtime(_LIB) < os.path.getmtime(_SRC):
+        tmp = _LIB + f".tmp{os.getpid()}"
+        cmd = ["gcc", "-O2", "-std=c11", "-ffp-contract=off", "-fno-fast-math", "-fPIC",
+               "-shared", "-pthread", "-o", tmp, _SRC, "-lm"]
+        subprocess.run(cmd, check=True)
+        os.replace(tmp, _LIB)
+    return _LIB
+
+
+class _Gas(C.Structure):
+    _fields_ = [("n_levels", C.c_int32), ("n_nodes", C.c_int32), ("d_eps", C.c_double),
+                ("level_type", C.c_void_p), ("threshold", C.c_void_p), ("rate", C.c_void_p),
+                ("recoil", C.c_double), ("nu_max", C.c_double)]
+
+
+class _Field(C.Structure):
+    _fields_ = [("kind", C.c_int32), ("e0", C.c_double), ("gap", C.c_double),
+                ("wire_r", C.c_double), ("tube_r", C.c_double), ("voltage", C.c_double),
+                ("b", C.c_double * 3), ("nx", C.c_int32), ("ny", C.c_int32), ("nz", C.c_int32),
+                ("origin", C.c_double * 3), ("spacing", C.c_double * 3), ("grid", C.c_void_p)]
+
+
+class _Run(C.Structure):
+    _fields_ = [("n_primaries", C.c_int64), ("n_avalanches", C.c_int32),
+                ("x", C.c_void_p), ("y", C.c_void_p), ("z", C.c_void_p), ("t", C.c_void_p),
+                ("e", C.c_void_p), ("dx", C.c_void_p), ("dy", C.c_void_p), ("dz", C.c_void_p),
+                ("aval", C.c_void_p), ("uid", C.c_void_p), ("aval_field", C.c_void_p),
+                ("seed", C.c_uint64), ("t_max", C.c_double), ("coll_limit", C.c_uint32),
+                ("n_threads", C.c_int32)]
+
+
+def _load():
+    global _lib
+    with _lock:
+        if _lib is None:
+            lib = C.CDLL(build())
+            lib.or_philox4x32_10.argtypes = [C.c_void_p, C.c_void_p, C.c_void_p]
+            lib.or_philox4x32_10.restype = None
+            lib.or_splitmix64_mix.argtypes = [C.c_uint64]
+            lib.or_splitmix64_mix.restype = C.c_uint64
+            lib.or_child_uid.argtypes = [C.c_uint64, C.c_uint32]
+            lib.or_child_uid.restype = C.c_uint64
+            lib.or_flight.argtypes = [C.c_void_p] * 4 + [C.c_double]
+            lib.or_flight.restype = None
+            lib.or_elastic.argtypes = [C.c_double, C.c_void_p, C.c_double, C.c_double,
+                                       C.c_void_p]
+            lib.or_elastic.restype = None
+            lib.or_field_eval.argtypes = [C.POINTER(_Field), C.c_double, C.c_void_p, C.c_void_p]
+            lib.or_field_eval.restype = None
+            lib.or_boundary.argtypes = [C.POINTER(_Field), C.c_void_p]
+            lib.or_boundary.restype = C.c_int
+            lib.or_select.argtypes = [C.POINTER(_Gas), C.c_double, C.c_double,
+                                      C.POINTER(C.c_double)]
+            lib.or_select.restype = C.c_int
+            lib.or_run.argtypes = [C.POINTER(_Gas), C.POINTER(_Field), C.POINTER(_Run),
+                                   C.POINTER(C.c_void_p)]
+            lib.or_run.restype = C.c_int
+            lib.or_result_count.argtypes = [C.c_void_p]
+            lib.or_result_count.restype = C.c_int64
+            lib.or_result_fetch.argtypes = [C.c_void_p] + [C.c_void_p] * 17
+            lib.or_result_fetch.restype = C.c_int
+            lib.or_result_free.argtypes = [C.c_void_p]
+            lib.or_result_free.restype = None
+            _lib = lib
+    return _lib
+
+
+def _ptr(a: np.ndarray):
+    return a.ctypes.data_as(C.c_void_p)
+
+
+def _gas_struct(gas, keep):
+    lt = np.ascontiguousarray(gas.level_type, np.int32)
+    th = np.ascontiguousarray(gas.threshold, np.float64)
+    rt = np.ascontiguousarray(gas.rate, np.float64)
+    keep += [lt, th, rt]
+    return _Gas(rt.shape[1], rt.shape[0], gas.d_eps, _ptr(lt).value, _ptr(th).value,
+                _ptr(rt).value, gas.recoil, gas.nu_max)
+
+
+def _field_struct(field, keep):
+    f = _Field()
+    f.kind = field.kind
+    f.e0, f.gap = field.e0, field.gap
+    f.wire_r, f.tube_r, f.voltage = field.wire_r, field.tube_r, field.voltage
+    f.b = (C.c_double * 3)(*field.b)
+    f.origin = (C.c_double * 3)(*field.origin)
+    f.spacing = (C.c_double * 3)(*field.spacing)
+    if field.grid is not None:
+        g = np.ascontiguousarray(field.grid, np.float32)
+        keep.append(g)
+        f.nz, f.ny, f.nx = g.shape[0], g.shape[1], g.shape[2]
+        f.grid = _ptr(g).value
+    return f
+
+
+def default_threads() -> int:
+    try:
+        return max(1, len(os.sched_getaffinity(0)))
+    except AttributeError:  # pragma: no cover
+        return max(1, os.cpu_count() or 1)
+
+
+# ------------------------------------------------------------------ hooks
+def philox4x32_10(ctr, key):
+    lib = _load()
+    c = np.ascontiguousarray(ctr, np.uint32)
+    k = np.ascontiguousarray(key, np.uint32)
+    out = np.zeros(4, np.uint32)
+    lib.or_philox4x32_10(_ptr(c), _ptr(k), _ptr(out))
+    return out
+
+
+def splitmix64_mix(z: int) -> int:
+    return int(_load().or_splitmix64_mix(C.c_uint64(z & (2**64 - 1))))
+
+
+def child_uid(parent: int, flight: int) -> int:
+    return int(_load().or_child_uid(C.c_uint64(parent & (2**64 - 1)), C.c_uint32(flight)))
+
+
+def flight(r, v, a, w, dt):
+    """One exact flight under constant acceleration a (cm/ns^2) and magnetic
+    rotation vector w (rad/ns); returns the new (r, v)."""
+    lib = _load()
+    r = np.array(r, np.float64)
+    v = np.array(v, np.float64)
+    a = np.ascontiguousarray(a, np.float64)
+    w = np.ascontiguousarray(w, np.float64)
+    lib.or_flight(_ptr(r), _ptr(v), _ptr(a), _ptr(w), float(dt))
+    return r, v
+
+
+def elastic(recoil: float, v, u_cos: float, u_phi: float):
+    """Velocity after an elastic collision (isotropic direction from the two
+    uniforms, recoil loss with recoil = 2m/M)."""
+    v = np.ascontiguousarray(v, np.float64)
+    out = np.zeros(3)
+    _load().or_elastic(float(recoil), _ptr(v), float(u_cos), float(u_phi), _ptr(out))
+    return out
+
+
+def field_eval(field, r, plate_e=0.0):
+    keep = []
+    f = _field_struct(field, keep)
+    r = np.ascontiguousarray(r, np.float64)
+    e = np.zeros(3)
+    _load().or_field_eval(C.byref(f), float(plate_e), _ptr(r), _ptr(e))
+    return e
+
+
+def boundary(field, r) -> int:
+    keep = []
+    f = _field_struct(field, keep)
+    r = np.ascontiguousarray(r, np.float64)
+    return int(_load().or_boundary(C.byref(f), _ptr(r)))
+
+
+def select(gas, eps: float, u1: float):
+    """Level chosen at energy eps for the uniform u1 (-1 = null) and nu_max."""
+    keep = []
+    g = _gas_struct(gas, keep)
+    nm = C.c_double(0.0)
+    j = _load().or_select(C.byref(g), float(eps), float(u1), C.byref(nm))
+    if j == -2:
+        raise ValueError("bad gas table")
+    return j, nm.value
+
+
+# -------------------------------------------------------------------- run
+def run(gas, field, prim, seed: int = 0, t_max: float = 0.0, coll_limit: int = 0,
+        n_threads: int | None = None) -> dict:
+    """Transport every avalanche of `prim` and return a dict of arrays:
+    x0..e0 (start), x1..e1 (end), status, aval, uid, n_flight, ledger [n, 4]
+    (field work, inelastic loss, recoil loss, secondary share; eV),
+    electrons [n_avalanches], tallies [n_avalanches, L+1] (real collisions
+    per level, then null flights)."""
+    lib = _load()
+    keep = []
+    g = _gas_struct(gas, keep)
+    f = _field_struct(field, keep)
+    cols = {}
+    for k in ("x", "y", "z", "t", "e", "dx", "dy", "dz"):
+        cols[k] = np.ascontiguousarray(getattr(prim, k), np.float64)
+    av = np.ascontiguousarray(prim.aval, np.int32)
+    ud = np.ascontiguousarray(prim.uid, np.uint64)
+    keep += list(cols.values()) + [av, ud]
+    af = None
+    if prim.aval_field is not None:
+        af = np.ascontiguousarray(prim.aval_field, np.float64)
+        keep.append(af)
+    ra = _Run()
+    ra.n_primaries = prim.n
+    ra.n_avalanches = prim.n_avalanches
+    for k, a in cols.items():
+        setattr(ra, k, _ptr(a).value)
+    ra.aval, ra.uid = _ptr(av).value, _ptr(ud).value
+    ra.aval_field = _ptr(af).value if af is not None else None
+    ra.seed = seed & (2**64 - 1)
+    ra.t_max = t_max
+    ra.coll_limit = coll_limit
+    ra.n_threads = n_threads or default_threads()
+    handle = C.c_void_p()
+    rc = lib.or_run(C.byref(g), C.byref(f), C.byref(ra), C.byref(handle))
+    if rc != 0:
+        raise RuntimeError(f"oracle run failed ({rc})")
+    try:
+        n = int(lib.or_result_count(handle))
+        out = {k: np.zeros(n, np.float64) for k in
+               ("x0", "y0", "z0", "t0", "e0", "x1", "y1", "z1", "t1", "e1")}
+        out["status"] = np.zeros(n, np.int32)
+        out["aval"] = np.zeros(n, np.int32)
+        out["uid"] = np.zeros(n, np.uint64)
+        out["n_flight"] = np.zeros(n, np.uint32)
+        out["ledger"] = np.zeros((n, 4), np.float64)
+        A, L = prim.n_avalanches, gas.n_levels
+        out["electrons"] = np.zeros(A, np.uint64)
+        out["tallies"] = np.zeros((A, L + 1), np.uint64)
+        order = ("x0", "y0", "z0", "t0", "e0", "x1", "y1", "z1", "t1", "e1", "status", "aval",
+                 "uid", "n_flight", "ledger", "electrons", "tallies")
+        lib.or_result_fetch(handle, *[_ptr(out[k]) for k in order])
+    finally:
+        lib.or_result_free(handle)
+    return out

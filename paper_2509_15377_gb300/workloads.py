@@ -1,0 +1,263 @@
+"""Seeded synthetic inputs for microscopic avalanche transport.
+
+This module only *describes* workloads: gas rate tables, field geometries and
+primary electrons, drawn from fixed seeds with numpy.  It holds none of the
+transport arithmetic; both the CUDA library and the CPU oracle take its
+arrays as inputs.
+
+The paper's own workloads (single and triple GEM with ANSYS field maps and
+Magboltz gas files, Sec. 4) are not available, so synthetic stand-ins are
+used: a constant-rate model gas (drift closed forms), an argon-like
+12-level gas, parallel-plate, coaxial (optionally with axial B) and a
+regular-grid field map sampled from the coaxial field.
+
+Units: cm, ns, eV, V/cm, T; collision rates in 1/ns (1e12/s = 1000/ns).
+"""
+from __future__ import annotations
+
+import dataclasses
+import math
+from typing import Optional
+
+import numpy as np
+
+# Level kinds of a gas table (interface values of the C ABI).
+ELASTIC, EXCITATION, IONISATION = 0, 1, 2
+# Field kinds (interface values of the C ABI).
+UNIFORM, PLATE, COAX, GRID = 0, 1, 2, 3
+# Electron status codes written to the endpoints (non-zero = finished).
+STATUS_NAMES = {
+    0: "active", 1: "anode", 2: "cathode", 3: "wire", 4: "tube",
+    5: "out_of_map", 6: "time", 7: "coll_limit", 8: "flight_limit",
+}
+ANODE, CATHODE, WIRE, TUBE, OUT_OF_MAP, TIME, COLL_LIMIT = 1, 2, 3, 4, 5, 6, 7
+
+# Electron mass in unified atomic mass units (CODATA 2018).
+ELECTRON_MASS_U = 5.48579909065e-4
+ARGON_MASS_U = 39.948
+
+# Excitation slope of the argon-like gas (1/ns per eV above threshold),
+# chosen once with the oracle so that the mean gain at 40 kV/cm over a
+# 128 um gap is about 1e3.
+ARGON_LIKE_K_EXC = 7.25
+
+
+@dataclasses.dataclass
+class Gas:
+    """Tabulated per-level collision rates on a uniform energy grid."""
+    level_type: np.ndarray   # int32 [L]
+    threshold: np.ndarray    # float64 [L] eV lost by the level
+    rate: np.ndarray         # float64 [N, L] 1/ns at node energies k * d_eps
+    d_eps: float             # eV
+    recoil: float = 0.0      # 2m/M (elastic recoil loss), 0 = no loss
+    nu_max: float = 0.0      # 1/ns, 0 = derived by the consumer
+
+    @property
+    def n_levels(self) -> int:
+        return int(self.rate.shape[1])
+
+    @property
+    def n_nodes(self) -> int:
+        return int(self.rate.shape[0])
+
+
+@dataclasses.dataclass
+class Field:
+    kind: int
+    e0: float = 0.0                 # UNIFORM / PLATE |E| (V/cm), E = (0,0,-e0)
+    gap: float = 0.0                # PLATE gap (cm)
+    wire_r: float = 0.0             # COAX / GRID wire radius (cm)
+    tube_r: float = 0.0             # COAX tube radius (cm)
+    voltage: float = 0.0            # COAX wire voltage (V)
+    b: tuple = (0.0, 0.0, 0.0)      # uniform B (T)
+    grid: Optional[np.ndarray] = None   # GRID float32 [nz, ny, nx, 4]
+    origin: tuple = (0.0, 0.0, 0.0)
+    spacing: tuple = (1.0, 1.0, 1.0)
+
+
+@dataclasses.dataclass
+class Primaries:
+    x: np.ndarray
+    y: np.ndarray
+    z: np.ndarray
+    t: np.ndarray
+    e: np.ndarray
+    dx: np.ndarray
+    dy: np.ndarray
+    dz: np.ndarray
+    aval: np.ndarray          # int32
+    uid: np.ndarray           # uint64
+    n_avalanches: int
+    aval_field: Optional[np.ndarray] = None   # PLATE per-avalanche |E| (V/cm)
+
+    @property
+    def n(self) -> int:
+        return int(self.x.shape[0])
+
+    def subset(self, avalanches) -> "Primaries":
+        """Only the primaries of the listed avalanches.
+
+        Avalanche numbers, electron ids and the per-avalanche fields are
+        kept unchanged (the other avalanches are simply empty), so a run
+        keyed by (seed, avalanche, electron id) reproduces exactly the same
+        avalanches as the full workload."""
+        sel = np.zeros(self.n_avalanches, dtype=bool)
+        sel[np.asarray(avalanches, dtype=np.int64)] = True
+        keep = sel[self.aval]
+        af = None if self.aval_field is None else self.aval_field.copy()
+        return Primaries(
+            *(getattr(self, k)[keep].copy() for k in ("x", "y", "z", "t", "e", "dx", "dy", "dz")),
+            aval=self.aval[keep].copy(), uid=self.uid[keep].copy(),
+            n_avalanches=self.n_avalanches, aval_field=af)
+
+
+@dataclasses.dataclass
+class Workload:
+    name: str
+    gas: Gas
+    field: Field
+    primaries: Primaries
+    t_max: float = 0.0          # ns, 0 = none
+    coll_limit: int = 0         # real collisions per electron, 0 = none
+    seed: int = 0
+
+
+# ------------------------------------------------------------------ gases
+def model_gas(nu_elastic: float = 1000.0, nu_ion: float = 0.0, ion_threshold: float = 0.0,
+              recoil: float = 0.0, n_nodes: int = 2, d_eps: float = 1000.0,
+              exact_nu_max: bool = True) -> Gas:
+    """Energy-independent rates: elastic (isotropic) and optionally an
+    ionisation level with a fixed rate."""
+    types = [ELASTIC]
+    thr = [0.0]
+    cols = [np.full(n_nodes, nu_elastic)]
+    if nu_ion > 0.0:
+        types.append(IONISATION)
+        thr.append(ion_threshold)
+        cols.append(np.full(n_nodes, nu_ion))
+    rate = np.stack(cols, axis=1).astype(np.float64)
+    return Gas(np.array(types, np.int32), np.array(thr, np.float64), rate, float(d_eps),
+               float(recoil), float(nu_elastic + nu_ion) if exact_nu_max else 0.0)
+
+
+def argon_like_gas(k_exc: float = ARGON_LIKE_K_EXC) -> Gas:
+    """Argon-like synthetic gas: 0-100 eV in 2000 bins (2001 nodes), elastic
+    1e12*sqrt(eps/eV)/s, ten excitation levels with thresholds spread evenly
+    over 11.5-15 eV and rates k_exc*(eps - E_j), one ionisation level at
+    15.7 eV with rate 5e10*(eps - 15.7)/s; elastic recoil on M = 39.948 u."""
+    n_nodes, d_eps = 2001, 0.05
+    eps = np.arange(n_nodes, dtype=np.float64) * d_eps
+    thr_exc = 11.5 + np.arange(10) * (3.5 / 9.0)
+    rates = [1000.0 * np.sqrt(eps)]
+    for ej in thr_exc:
+        rates.append(np.where(eps >= ej, k_exc * (eps - ej), 0.0))
+    rates.append(np.where(eps >= 15.7, 50.0 * (eps - 15.7), 0.0))
+    rate = np.stack(rates, axis=1)
+    types = np.array([ELASTIC] + [EXCITATION] * 10 + [IONISATION], np.int32)
+    thr = np.concatenate([[0.0], thr_exc, [15.7]]).astype(np.float64)
+    recoil = 2.0 * ELECTRON_MASS_U / ARGON_MASS_U
+    return Gas(types, thr, rate, d_eps, recoil, 0.0)
+
+
+# -------------------------------------------------------------- primaries
+def _isotropic(rng: np.random.Generator, n: int, forward_z: bool = False):
+    c = rng.uniform(-1.0, 1.0, n)
+    if forward_z:
+        c = np.abs(c)
+    s = np.sqrt(np.maximum(0.0, 1.0 - c * c))
+    phi = rng.uniform(0.0, 2.0 * math.pi, n)
+    return s * np.cos(phi), s * np.sin(phi), c
+
+
+def _primaries(rng, x, y, z, aval, n_aval, e0=0.1, forward_z=False, aval_field=None):
+    n = len(x)
+    dx, dy, dz = _isotropic(rng, n, forward_z)
+    return Primaries(np.asarray(x, np.float64), np.asarray(y, np.float64),
+                     np.asarray(z, np.float64), np.zeros(n), np.full(n, e0),
+                     dx, dy, dz, np.asarray(aval, np.int32),
+                     np.arange(n, dtype=np.uint64), int(n_aval), aval_field)
+
+
+# -------------------------------------------------------------- workloads
+def drift_model(n_electrons: int = 1000, n_coll: int = 100_000, e_field: float = 1000.0,
+                nu: float = 1000.0, b=(0.0, 0.0, 0.0), seed: int = 0) -> Workload:
+    """Constant-rate elastic model gas, uniform E = (0,0,-E0); every electron
+    is its own avalanche and stops after `n_coll` real collisions."""
+    rng = np.random.default_rng(seed)
+    z = np.zeros(n_electrons)
+    prim = _primaries(rng, z, z, z, np.arange(n_electrons), n_electrons)
+    return Workload("drift_model", model_gas(nu), Field(UNIFORM, e0=e_field, b=tuple(b)),
+                    prim, 0.0, n_coll, seed)
+
+
+def plate(n_avalanches: int = 1000, e_field: float = 40_000.0, gap: float = 0.0128,
+          k_exc: float = ARGON_LIKE_K_EXC, t_max: float = 100.0, seed: int = 0) -> Workload:
+    """Argon-like gas, parallel-plate gap, one primary per avalanche released
+    from the cathode (x = y = z = 0) with 0.1 eV into the gas half-space."""
+    rng = np.random.default_rng(seed)
+    z = np.zeros(n_avalanches)
+    prim = _primaries(rng, z, z, z, np.arange(n_avalanches), n_avalanches, forward_z=True)
+    return Workload("plate", argon_like_gas(k_exc), Field(PLATE, e0=e_field, gap=gap),
+                    prim, t_max, 0, seed)
+
+
+def plate_batched(n_avalanches: int = 4096, e_lo: float = 30_000.0, e_hi: float = 50_000.0,
+                  mean_primaries: float = 3.0, gap: float = 0.0128,
+                  k_exc: float = ARGON_LIKE_K_EXC, t_max: float = 100.0,
+                  seed: int = 0) -> Workload:
+    """Many parallel-plate avalanches with per-avalanche field ~ U(e_lo, e_hi)
+    and Poisson(mean) primaries (empty avalanches kept)."""
+    rng = np.random.default_rng(seed)
+    fields = rng.uniform(e_lo, e_hi, n_avalanches)
+    counts = rng.poisson(mean_primaries, n_avalanches)
+    aval = np.repeat(np.arange(n_avalanches), counts)
+    z = np.zeros(len(aval))
+    prim = _primaries(rng, z, z, z, aval, n_avalanches, forward_z=True, aval_field=fields)
+    return Workload("plate_batched", argon_like_gas(k_exc), Field(PLATE, e0=40_000.0, gap=gap),
+                    prim, t_max, 0, seed)
+
+
+def coax(n_avalanches: int = 2048, wire_r: float = 25e-4, tube_r: float = 0.5,
+         voltage: float = 1500.0, b_axial: float = 1.0, r_lo: float = 0.1, r_hi: float = 0.45,
+         k_exc: float = ARGON_LIKE_K_EXC, t_max: float = 10_000.0, seed: int = 0) -> Workload:
+    """Coaxial tube with axial B; one primary per avalanche at r ~ U(r_lo, r_hi),
+    phi ~ U(0, 2 pi), z = 0 (the tube is infinite in z)."""
+    rng = np.random.default_rng(seed)
+    r = rng.uniform(r_lo, r_hi, n_avalanches)
+    phi = rng.uniform(0.0, 2.0 * math.pi, n_avalanches)
+    prim = _primaries(rng, r * np.cos(phi), r * np.sin(phi), np.zeros(n_avalanches),
+                      np.arange(n_avalanches), n_avalanches)
+    f = Field(COAX, wire_r=wire_r, tube_r=tube_r, voltage=voltage, b=(0.0, 0.0, b_axial))
+    return Workload("coax", argon_like_gas(k_exc), f, prim, t_max, 0, seed)
+
+
+def coax_grid_map(n: int = 256, half_width: float = 0.15, length: float = 1.0,
+                  wire_r: float = 25e-4, tube_r: float = 0.5, voltage: float = 1500.0) -> Field:
+    """A regular n^3 float32 map of the coaxial field on
+    [-w, w]^2 x [0, length]; nodes inside the wire take the field at r = a."""
+    xs = np.linspace(-half_width, half_width, n)
+    zs = np.linspace(0.0, length, n)
+    X, Y = np.meshgrid(xs, xs, indexing="xy")          # [ny, nx]
+    r2 = np.maximum(X * X + Y * Y, wire_r * wire_r)
+    s = voltage / (math.log(tube_r / wire_r) * r2)
+    plane = np.zeros((n, n, 4), np.float32)
+    plane[..., 0] = s * X
+    plane[..., 1] = s * Y
+    grid = np.broadcast_to(plane, (len(zs), n, n, 4)).astype(np.float32)
+    sp = 2.0 * half_width / (n - 1)
+    return Field(GRID, wire_r=wire_r, tube_r=tube_r, voltage=voltage, grid=np.ascontiguousarray(grid),
+                 origin=(-half_width, -half_width, 0.0), spacing=(sp, sp, length / (n - 1)))
+
+
+def grid_stress(n_avalanches: int = 256, n: int = 256, voltage: float = 1500.0,
+                r_start: float = 0.1, k_exc: float = ARGON_LIKE_K_EXC, t_max: float = 1000.0,
+                seed: int = 0) -> Workload:
+    """Coax-sampled regular-grid map; one primary per avalanche at
+    r = r_start, random phi, mid-length."""
+    rng = np.random.default_rng(seed)
+    phi = rng.uniform(0.0, 2.0 * math.pi, n_avalanches)
+    f = coax_grid_map(n=n, voltage=voltage)
+    zc = 0.5 * (f.origin[2] + f.spacing[2] * (n - 1))
+    prim = _primaries(rng, r_start * np.cos(phi), r_start * np.sin(phi),
+                      np.full(n_avalanches, zc), np.arange(n_avalanches), n_avalanches)
+    return Workload("grid_stress", argon_like_gas(k_exc), f, prim, t_max, 0, seed)

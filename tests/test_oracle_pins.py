@@ -1,0 +1,376 @@
+"""Pins of the CPU oracle against facts that do not come from the oracle:
+published known-answer vectors, closed forms of model gases, textbook
+integrators, brute-force frequencies and conservation laws.
+
+A plausible slip anywhere in the oracle's step (a dropped term of the flight,
+a sign of E or B, cumulative vs per-level rates, the threshold guard, the
+recoil factor, the ionisation bookkeeping, the RNG keying) fails one of
+these.
+"""
+import math
+
+import numpy as np
+import pytest
+
+import oracle
+from paper_2509_15377_gb300 import workloads as W
+from tests import physics as P
+from tests.conftest import golden_path
+
+
+def _read_hex_table(name):
+    rows = []
+    for line in open(golden_path(name)):
+        line = line.strip()
+        if line and not line.startswith("#"):
+            rows.append([int(tok, 16) for tok in line.split()])
+    return rows
+
+
+# ----------------------------------------------------------- random numbers
+def test_philox_known_answers():
+    """Philox4x32-10 reproduces the published known-answer vectors."""
+    for row in _read_hex_table("philox4x32_10_kat.txt"):
+        ctr, key, expect = row[0:4], row[4:6], row[6:10]
+        assert list(oracle.philox4x32_10(ctr, key)) == expect
+
+
+def test_splitmix64_reference_sequence():
+    """The uid mixer is SplitMix64's output function: its sequence from state
+    0 matches the published reference output."""
+    state = 0
+    for (expect,) in _read_hex_table("splitmix64_seed0.txt"):
+        state = (state + 0x9E3779B97F4A7C15) % 2**64
+        assert oracle.splitmix64_mix(state) == expect
+
+
+def test_child_uid_distinct():
+    uids = {oracle.child_uid(p, f) for p in range(64) for f in range(256)}
+    assert len(uids) == 64 * 256
+    assert not (uids & set(range(64)))
+
+
+# ------------------------------------------------------------------ flight
+def _rk4(r, v, a, w, dt, n=4000):
+    """Textbook RK4 for dr/dt = v, dv/dt = a + v x w."""
+    y = np.concatenate([r, v]).astype(float)
+
+    def f(y):
+        return np.concatenate([y[3:], a + np.cross(y[3:], w)])
+
+    h = dt / n
+    for _ in range(n):
+        k1 = f(y)
+        k2 = f(y + 0.5 * h * k1)
+        k3 = f(y + 0.5 * h * k2)
+        k4 = f(y + h * k3)
+        y = y + (h / 6.0) * (k1 + 2 * k2 + 2 * k3 + k4)
+    return y[:3], y[3:]
+
+
+@pytest.mark.parametrize("case", range(6))
+def test_flight_matches_rk4(case):
+    """The closed-form flight equals a numerical integration of the Lorentz
+    force (E only, B only, E and B at arbitrary angles)."""
+    rng = np.random.default_rng(100 + case)
+    r = rng.normal(size=3) * 1e-3
+    v = rng.normal(size=3) * 0.05
+    a = rng.normal(size=3) * 50.0 if case != 1 else np.zeros(3)
+    w = rng.normal(size=3) * 200.0 if case not in (0, 5) else np.zeros(3)
+    dt = 0.02 * (1 + case)
+    r1, v1 = oracle.flight(r, v, a, w, dt)
+    r2, v2 = _rk4(r, v, a, w, dt)
+    assert np.allclose(r1, r2, rtol=1e-9, atol=1e-12)
+    assert np.allclose(v1, v2, rtol=1e-9, atol=1e-10)
+
+
+def test_flight_crossed_fields_guiding_centre():
+    """Collisionless motion in E perpendicular to B drifts at E x B / B^2 on
+    average (textbook guiding-centre drift)."""
+    e_vcm, b_t = np.array([0.0, 0.0, -1000.0]), np.array([1.0, 0.0, 0.0])
+    a = -P.ACCEL_PER_VCM * e_vcm
+    w = -P.OMEGA_PER_T * b_t
+    period = 2 * math.pi / np.linalg.norm(w)
+    r, v = oracle.flight(np.zeros(3), np.zeros(3), a, w, 50 * period)
+    drift = np.cross(e_vcm * 100.0, b_t) / 1.0  # m/s, from SI E [V/m] x B [T] / B^2
+    drift_cm_ns = drift * 1e-7
+    assert np.allclose(r / (50 * period), drift_cm_ns, rtol=1e-9, atol=1e-15)
+    # speed unchanged by B alone
+    v0 = np.array([0.01, 0.02, -0.03])
+    _, v1 = oracle.flight(np.zeros(3), v0, np.zeros(3), w, 0.37)
+    assert np.isclose(np.linalg.norm(v1), np.linalg.norm(v0), rtol=1e-14)
+
+
+# ---------------------------------------------------------------- collisions
+def test_elastic_matches_two_body_kinematics():
+    """Lab-frame elastic scattering on a target at rest (textbook two-body
+    kinematics): E'/E = ((m cos chi + sqrt(M^2 - m^2 sin^2 chi)) / (m + M))^2.
+    The oracle's first-order form must agree to O((m/M)^2) at every angle,
+    and the new direction is the isotropic one drawn from the uniforms."""
+    for mass_ratio in (W.ELECTRON_MASS_U / W.ARGON_MASS_U, 1e-3):
+        recoil = 2.0 * mass_ratio
+        rng = np.random.default_rng(8)
+        for _ in range(500):
+            v = rng.normal(size=3) * 0.3
+            uc, up = rng.uniform(size=2)
+            v1 = oracle.elastic(recoil, v, uc, up)
+            n = v1 / np.linalg.norm(v1)
+            assert n[2] == pytest.approx(1.0 - 2.0 * uc, abs=1e-12)
+            assert math.atan2(n[1], n[0]) % (2 * math.pi) == pytest.approx(
+                2 * math.pi * up, abs=1e-9)
+            c = np.dot(n, v) / np.linalg.norm(v)
+            mu = mass_ratio
+            exact = ((mu * c + math.sqrt(1.0 - mu * mu * (1 - c * c))) / (1.0 + mu)) ** 2
+            ratio = np.dot(v1, v1) / np.dot(v, v)
+            # second-order term of the expansion is 2 mu^2 (1 - cos chi)^2 <= 8 mu^2
+            assert abs(ratio - exact) <= 8.0 * mu * mu * (1 + 1e-6) + 1e-13
+
+
+def test_ionisation_split_and_secondary_identity():
+    """E = 0 and a pure ionisation gas (threshold I): after its single
+    collision the primary keeps (eps0 - I)(1 - u) and the new electron
+    starts with (eps0 - I) u, u uniform; the new electron's id is the
+    documented function of the parent id and flight index."""
+    e0, I, n = 10.0, 2.0, 4000
+    w = W.drift_model(n_electrons=n, n_coll=1, e_field=0.0, seed=13)
+    g = W.model_gas(0.0, nu_ion=1000.0, ion_threshold=I)
+    w.primaries.e[:] = e0
+    o = oracle.run(g, w.field, w.primaries, seed=13, coll_limit=1, t_max=0.02)
+    prim = o["uid"] < n
+    pu = o["uid"][prim]
+    by_uid = {int(u): i for i, u in enumerate(o["uid"])}
+    frac = []
+    for i in np.nonzero(prim)[0]:
+        if o["status"][i] != W.COLL_LIMIT:
+            continue
+        child = oracle.child_uid(int(o["uid"][i]), int(o["n_flight"][i]) - 1)
+        j = by_uid[child]
+        assert o["e0"][j] + o["e1"][i] == pytest.approx(e0 - I, rel=1e-12)
+        assert o["t0"][j] == o["t1"][i]
+        frac.append(o["e1"][i] / (e0 - I))
+    frac = np.sort(frac)
+    assert len(frac) > 0.9 * len(pu)
+    d = np.max(np.abs(np.arange(1, len(frac) + 1) / len(frac) - frac))
+    assert d < 1.63 / math.sqrt(len(frac))
+
+
+# ------------------------------------------------------------------- fields
+def test_coax_field_integrates_to_voltage():
+    """The line integral of the coaxial field from the wire to the tube
+    equals the applied voltage, and the field points away from a positive
+    wire."""
+    f = W.Field(W.COAX, wire_r=25e-4, tube_r=0.5, voltage=1500.0)
+    rs = np.geomspace(f.wire_r, f.tube_r, 20001)
+    phi = 0.7
+    er = [np.dot(oracle.field_eval(f, [r * math.cos(phi), r * math.sin(phi), 0.3]),
+                 [math.cos(phi), math.sin(phi), 0.0]) for r in rs]
+    assert np.all(np.asarray(er) > 0)
+    integral = np.trapezoid(er, rs)
+    assert abs(integral - 1500.0) < 1e-3
+
+
+def test_grid_trilinear_exact_on_affine_field():
+    """Trilinear interpolation reproduces an affine field exactly."""
+    n = (5, 6, 7)
+    origin, spacing = (-0.1, 0.2, 0.0), (0.05, 0.04, 0.03)
+    A = np.array([[1.0, 2.0, -3.0], [0.5, -1.0, 2.0], [4.0, 0.0, 1.0]])
+    c = np.array([10.0, -20.0, 5.0])
+    g = np.zeros((n[2], n[1], n[0], 4), np.float32)
+    for k in range(n[2]):
+        for j in range(n[1]):
+            for i in range(n[0]):
+                p = np.array(origin) + np.array(spacing) * (i, j, k)
+                g[k, j, i, :3] = A @ p + c
+    f = W.Field(W.GRID, grid=g, origin=origin, spacing=spacing)
+    rng = np.random.default_rng(3)
+    for _ in range(200):
+        p = np.array(origin) + rng.uniform(0, 1, 3) * np.array(spacing) * (np.array(n) - 1)
+        e = oracle.field_eval(f, p)
+        # node values were rounded to float32; interpolation adds no error of its own
+        assert np.allclose(e, A @ p + c, rtol=0, atol=2e-5)
+
+
+def test_grid_converges_to_coax_away_from_wire():
+    f = W.coax_grid_map(n=64, half_width=0.15, length=1.0)
+    fc = W.Field(W.COAX, wire_r=f.wire_r, tube_r=f.tube_r, voltage=f.voltage)
+    rng = np.random.default_rng(4)
+    for _ in range(100):
+        r = rng.uniform(0.05, 0.1)
+        ph = rng.uniform(0, 2 * math.pi)
+        p = [r * math.cos(ph), r * math.sin(ph), rng.uniform(0.1, 0.9)]
+        eg, ec = oracle.field_eval(f, p), oracle.field_eval(fc, p)
+        assert np.linalg.norm(eg - ec) < 0.02 * np.linalg.norm(ec)
+
+
+def test_boundaries():
+    plate = W.Field(W.PLATE, e0=1.0, gap=0.0128)
+    assert oracle.boundary(plate, [0, 0, 0.0]) == 0
+    assert oracle.boundary(plate, [0, 0, 0.0128]) == W.ANODE
+    assert oracle.boundary(plate, [0, 0, -1e-12]) == W.CATHODE
+    cx = W.Field(W.COAX, wire_r=25e-4, tube_r=0.5, voltage=1.0)
+    assert oracle.boundary(cx, [0.002, 0.0, 5.0]) == W.WIRE
+    assert oracle.boundary(cx, [0.3, 0.4, 0.0]) == W.TUBE
+    assert oracle.boundary(cx, [0.1, 0.1, -3.0]) == 0
+    g = W.coax_grid_map(n=8, half_width=0.15, length=1.0)
+    assert oracle.boundary(g, [0.0, 0.0, 0.5]) == W.WIRE
+    assert oracle.boundary(g, [0.16, 0.0, 0.5]) == W.OUT_OF_MAP
+    assert oracle.boundary(g, [0.1, 0.0, 1.01]) == W.OUT_OF_MAP
+    assert oracle.boundary(g, [0.1, 0.0, 0.5]) == 0
+
+
+# ---------------------------------------------------------------- selection
+@pytest.mark.parametrize("eps", [0.0, 0.73, 11.62, 12.0, 15.69, 15.71, 33.3, 99.99, 140.0])
+def test_selection_frequencies_brute_force(eps):
+    """Over a fine uniform grid of u1 the fraction choosing level j equals
+    nu_j(eps)/nu_max, with nu_j linearly interpolated from the per-level
+    input rates (np.interp, not cumulative sums) and zero below the level's
+    threshold; the remainder is null."""
+    gas = W.argon_like_gas()
+    n = 40000
+    us = (np.arange(n) + 0.5) / n
+    counts = np.zeros(gas.n_levels + 1)
+    nu_max = None
+    for u in us:
+        j, nu_max = oracle.select(gas, eps, u)
+        counts[j if j >= 0 else -1] += 1
+    nodes = np.arange(gas.n_nodes) * gas.d_eps
+    expect = np.array([np.interp(eps, nodes, gas.rate[:, j]) for j in range(gas.n_levels)])
+    expect[(gas.level_type != W.ELASTIC) & (eps < gas.threshold)] = 0.0
+    assert nu_max == pytest.approx(gas.rate.sum(1).max() * (1 + 1e-6), rel=1e-15)
+    frac = counts[:-1] / n
+    assert np.allclose(frac, expect / nu_max, atol=2.0 / n)
+
+
+# ---------------------------------------------------------------- transport
+@pytest.fixture(scope="module")
+def drift_run():
+    w = W.drift_model(n_electrons=20000, n_coll=10000, seed=11)
+    return w, oracle.run(w.gas, w.field, w.primaries, seed=11, coll_limit=w.coll_limit)
+
+
+def test_drift_velocity_closed_form(drift_run):
+    """Constant nu, isotropic elastic, no loss: v_d = eE/(m nu) exactly in
+    the mean; E[t] = N/nu."""
+    w, o = drift_run
+    assert np.all(o["status"] == W.COLL_LIMIT)
+    dz, dt = o["z1"] - o["z0"], o["t1"] - o["t0"]
+    n = len(dz)
+    vd = P.drift_velocity(1000.0, 1000.0)
+    # ratio estimator; its standard error from the sample
+    se = np.std(dz - vd * dt) / math.sqrt(n) / dt.mean()
+    assert P.within_sigma(dz.mean() / dt.mean(), vd, se)
+    assert P.within_sigma(dt.mean(), 10000 / 1000.0, dt.std() / math.sqrt(n))
+
+
+def test_transverse_spread_closed_form(drift_run):
+    w, o = drift_run
+    xs = np.concatenate([o["x1"] - o["x0"], o["y1"] - o["y0"]]) ** 2
+    expect = P.transverse_msd(1000.0, 1000.0, 10000, 0.1)
+    assert P.within_sigma(xs.mean(), expect, xs.std() / math.sqrt(len(xs) / 2))
+
+
+def test_energy_is_field_work_without_loss(drift_run):
+    """Per electron: final energy = initial energy + E * dz (exact up to
+    rounding) when collisions conserve energy."""
+    w, o = drift_run
+    gain = 1000.0 * (o["z1"] - o["z0"])
+    assert np.allclose(o["e1"], o["e0"] + gain, rtol=1e-9, atol=1e-9)
+
+
+def test_recoil_cooling_closed_form():
+    """E = 0, elastic scattering on a target with 2m/M = r: each isotropic
+    collision multiplies the energy by 1 - r (1 - cos chi), E[cos chi] = 0, so
+    E[eps_N] = eps_0 (1 - r)^N."""
+    r, N = 0.02, 60
+    w = W.drift_model(n_electrons=20000, n_coll=N, e_field=0.0, seed=5)
+    w.gas = W.model_gas(1000.0, recoil=r)
+    w.primaries.e[:] = 2.0
+    o = oracle.run(w.gas, w.field, w.primaries, seed=5, coll_limit=N)
+    expect = 2.0 * (1.0 - r) ** N
+    assert P.within_sigma(o["e1"].mean(), expect, o["e1"].std() / math.sqrt(len(o["e1"])))
+    # with E = 0 no work is done: the ledger is all recoil
+    assert np.allclose(o["e0"] - o["ledger"][:, 2], o["e1"], rtol=1e-12, atol=1e-12)
+
+
+def test_langevin_crossed_field_drift():
+    """Constant nu with E perpendicular to B: the mean velocity obeys
+    d<v>/dt = a + <v> x w - nu <v> exactly, so the drift solves a 3x3 linear
+    system (magnitude and Lorentz angle)."""
+    b = (3.0, 0.0, 0.0)
+    w = W.drift_model(n_electrons=20000, n_coll=10000, b=b, seed=7)
+    o = oracle.run(w.gas, w.field, w.primaries, seed=7, coll_limit=w.coll_limit)
+    vd = P.langevin_drift([0.0, 0.0, -1000.0], b, 1000.0)
+    dt = o["t1"] - o["t0"]
+    for k, c in enumerate("xyz"):
+        d = o[c + "1"] - o[c + "0"]
+        se = np.std(d - vd[k] * dt) / math.sqrt(len(d)) / dt.mean()
+        assert P.within_sigma(d.mean() / dt.mean(), vd[k], se), (c, d.mean() / dt.mean(), vd[k], se)
+    # the drift has a sizeable E x B component (Lorentz angle ~ 28 degrees)
+    assert abs(vd[1]) > 0.4 * abs(vd[2])
+    # magnetic force does no work
+    assert np.allclose(o["e1"], o["e0"] + 1000.0 * (o["z1"] - o["z0"]), rtol=1e-9, atol=1e-9)
+
+
+def test_yule_gain_distribution():
+    """Constant ionisation rate nu_i with zero threshold and time limit T:
+    the number of electrons at T is geometric with p = exp(-nu_i T), mean
+    exp(nu_i T) (Yule-Furry pure birth)."""
+    nu_i, T, n_av = 10.0, 0.5, 1500
+    w = W.drift_model(n_electrons=n_av, n_coll=0, e_field=100.0, seed=9)
+    w.gas = W.model_gas(1000.0, nu_ion=nu_i, ion_threshold=0.0)
+    o = oracle.run(w.gas, w.field, w.primaries, seed=9, t_max=T)
+    n = o["electrons"].astype(float)
+    assert np.all(o["status"] == W.TIME)
+    assert np.allclose(o["t1"], T)
+    mean = math.exp(nu_i * T)
+    assert P.within_sigma(n.mean(), mean, n.std() / math.sqrt(n_av))
+    # KS distance against the geometric law
+    ks = np.sort(n)
+    emp = np.arange(1, n_av + 1) / n_av
+    d = np.max(np.abs(emp - P.geometric_cdf(ks, math.exp(-nu_i * T))))
+    assert d < 1.63 / math.sqrt(n_av)  # KS critical value, alpha = 0.01
+    # charge: every electron beyond the primary came from one ionisation
+    assert np.array_equal(o["electrons"], 1 + o["tallies"][:, 1])
+
+
+@pytest.fixture(scope="module")
+def plate_run():
+    w = W.plate(n_avalanches=24, e_field=40_000.0, seed=2)
+    return w, oracle.run(w.gas, w.field, w.primaries, seed=2, t_max=w.t_max)
+
+
+def test_plate_charge_and_ids(plate_run):
+    w, o = plate_run
+    L = w.gas.n_levels
+    ion = o["tallies"][:, L - 1]
+    assert np.array_equal(o["electrons"], 1 + ion)
+    assert len(np.unique(o["uid"])) == len(o["uid"])
+    assert set(np.unique(o["status"])) <= {W.ANODE, W.CATHODE, W.TIME}
+    an = o["status"] == W.ANODE
+    assert np.all(o["z1"][an] >= 0.0128) and np.all(o["z1"][~an] < 0.0128)
+    assert np.all(o["e1"] >= 0.0) and np.all(o["t1"] <= w.t_max)
+
+
+def test_plate_energy_ledger(plate_run):
+    """Per electron: e_end = e_start + field work - inelastic thresholds -
+    recoil losses - energy handed to secondaries."""
+    w, o = plate_run
+    L = o["ledger"]
+    bal = o["e0"] + L[:, 0] - L[:, 1] - L[:, 2] - L[:, 3]
+    scale = 1.0 + np.abs(L).sum(1)
+    assert np.all(np.abs(bal - o["e1"]) <= 1e-12 * scale + 1e-12)
+    # ionisation and excitation losses are whole multiples of thresholds
+    assert np.all(L[:, 1] >= 0) and np.all(L[:, 2] >= 0) and np.all(L[:, 3] >= 0)
+
+
+def test_plate_subset_reproduces_avalanches(plate_run):
+    """Keying by (seed, avalanche, electron id) makes any subset of
+    avalanches reproduce exactly."""
+    w, o = plate_run
+    sub = w.primaries.subset([3, 17])
+    s = oracle.run(w.gas, w.field, sub, seed=2, t_max=w.t_max, n_threads=1)
+    for k in (3, 17):
+        a, b = o["aval"] == k, s["aval"] == k
+        ia, ib = np.argsort(o["uid"][a]), np.argsort(s["uid"][b])
+        for c in ("x1", "y1", "z1", "t1", "e1", "status", "uid"):
+            assert np.array_equal(o[c][a][ia], s[c][b][ib])
