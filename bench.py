@@ -1,0 +1,382 @@
+"""Benchmark: real electron-collisions per second of the batched mixed-precision
+avalanche transport on one GB300 (configuration: 4096 parallel-plate
+avalanches in the argon-like gas, per-avalanche field U(30, 50) kV/cm,
+Poisson(3) primaries, one persistent launch per step), with the plain
+one-avalanche-at-a-time FP64 GPU path and the FP64 CPU oracle as
+comparators.
+
+    python bench.py [--gpus N --steps K --warmup W] [--impl reference]
+
+Prints one JSON line on rank 0.  Under torchrun every rank runs its own
+4096 avalanches (seed = rank): weak scaling, no collective on the data path.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+import numpy as np  # noqa: E402
+
+METRIC = "electron-collisions/sec on 1 GB300 (batched mixed vs plain FP64) at matched gain/v_d"
+UNIT = "electron-collisions/s"
+WORKLOAD = "plate_batched_4096"
+
+# Warp instructions per flight of the transport step, measured with ncu
+# (smsp__inst_executed.sum / warp-flights) on the straight-line calibration
+# run described in the design notes; None until measured.
+INST_PER_WARP_FLIGHT = None
+SM_COUNT = 152
+ISSUE_PER_SM_PER_CLK = 4
+
+
+# ---------------------------------------------------------------- sharding
+def shard_seed(rank: int) -> int:
+    """Each rank transports its own statistically identical workload."""
+    return rank
+
+
+def dist_env():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return ws, rank, local
+
+
+def max_over_ranks(value: float, backend_device=None) -> float:
+    import torch
+    import torch.distributed as dist
+    if not (dist.is_available() and dist.is_initialized()):
+        return value
+    t = torch.tensor([value], dtype=torch.float64, device=backend_device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def sum_over_ranks(value: float, backend_device=None) -> float:
+    import torch
+    import torch.distributed as dist
+    if not (dist.is_available() and dist.is_initialized()):
+        return value
+    t = torch.tensor([value], dtype=torch.float64, device=backend_device)
+    dist.all_reduce(t, op=dist.ReduceOp.SUM)
+    return float(t.item())
+
+
+def barrier():
+    import torch.distributed as dist
+    if dist.is_available() and dist.is_initialized():
+        dist.barrier()
+
+
+# ------------------------------------------------------------------ clocks
+class ClockSampler:
+    """nvidia-smi samples during the timed region (SM clock, reasons)."""
+
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, device_index: int):
+        self.dev = device_index
+        self.proc = None
+        self.lines = []
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.dev), f"--query-gpu={self.Q}",
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.reader = threading.Thread(target=self._read, daemon=True)
+            self.reader.start()
+        except (OSError, FileNotFoundError):
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self) -> dict:
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            parts = [p.strip() for p in ln.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                smax.append(float(parts[2]))
+            except ValueError:
+                continue
+            for n, v in zip(names, parts[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(n)
+        return {"sm_mhz": statistics.median(sm) if sm else None,
+                "sm_max_mhz": max(smax) if smax else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+# ------------------------------------------------------------ CPU baseline
+def oracle_baseline(w, seed: int, n_aval: int) -> dict:
+    """The FP64 oracle as it stands on the host cores, on the first n_aval
+    avalanches of the workload (a bounded sample)."""
+    import oracle
+    sub = w.primaries.subset(list(range(n_aval)))
+    threads = oracle.default_threads()
+    t0 = time.perf_counter()
+    o = oracle.run(w.gas, w.field, sub, seed=seed, t_max=w.t_max, n_threads=threads)
+    dt = time.perf_counter() - t0
+    L = w.gas.n_levels
+    real = int(o["tallies"][:, :L].sum())
+    return {"value": real / dt, "unit": UNIT, "cores": threads, "kind": "oracle",
+            "sample": f"avalanches 0..{n_aval - 1} of {w.primaries.n_avalanches} "
+                      f"({real:.3g} real collisions in {dt:.1f} s)",
+            "seconds": dt, "real_collisions": real}
+
+
+# ---------------------------------------------------------------- our arm
+def run_ours(args) -> None:
+    import torch
+    import torch.distributed as dist
+
+    ws, rank, local = dist_env()
+    if ws > 1 and not dist.is_initialized():
+        dist.init_process_group("nccl", device_id=torch.device(f"cuda:{local}"))
+    torch.cuda.set_device(local)
+    dev = torch.device(f"cuda:{local}")
+
+    import __graft_entry__
+    if rank == 0:
+        __graft_entry__.build()
+    barrier()
+    from paper_2509_15377_gb300 import avalanche as A
+    from paper_2509_15377_gb300 import workloads as W
+
+    seed = shard_seed(rank)
+    w = W.plate_batched(n_avalanches=args.avalanches, seed=seed)
+
+    cpu = None
+    if rank == 0 and ws == 1 and not args.no_cpu_baseline:
+        cpu = oracle_baseline(w, seed, args.cpu_avalanches)
+
+    av = A.Avalanche(local)
+    av.set_gas(w.gas)
+    av.set_field(w.field)
+    prim_dev = av.primaries_device(w.primaries)
+    opt = A.RunOptions(seed=seed, t_max=w.t_max, precision=A.GT_MIXED, mode=A.GT_BATCHED,
+                       block=args.block, flights_per_round=args.flights_per_round)
+    cap = args.capacity
+    stream = torch.cuda.current_stream(dev)
+    flush = torch.empty(256 * 1024 * 1024, dtype=torch.uint8, device=dev)  # > 129 MB L2
+
+    def step(prim):
+        flush.fill_(1)
+        return av.run(prim, opt, cap, stream=stream, allow=(A.GT_OK,))
+
+    for _ in range(args.warmup):
+        step(prim_dev)
+    torch.cuda.synchronize()
+    barrier()
+    clocks = ClockSampler(local)
+    clocks.start()
+    torch.cuda.synchronize()
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    ev0.record(stream)
+    real = flights = 0
+    kernel_ms = []
+    stats = []
+    for _ in range(args.steps):
+        st = step(prim_dev)
+        real += st["real_collisions"]
+        flights += st["flights"]
+        kernel_ms.append(st["transport_ms"])
+        stats.append(st)
+    ev1.record(stream)
+    torch.cuda.synchronize()
+    barrier()
+    elapsed = ev0.elapsed_time(ev1) / 1e3
+    clk = clocks.stop()
+    t_max_rank = max_over_ranks(elapsed, dev)
+    total_real = sum_over_ranks(float(real), dev)
+    value = total_real / t_max_rank
+
+    # observables of the last step (gain, drift velocity) for the matched check
+    last = stats[-1]
+    obs = av.observables(last["n_endpoints"], w.primaries, collect_status=W.ANODE,
+                         drift_status=W.ANODE, gap=w.field.gap)
+
+    # end to end through the public API: pinned host inputs copied inside
+    # every step, the per-avalanche results read back
+    prim_host = av.primaries_pinned(w.primaries)
+    h_elec = torch.empty(w.primaries.n_avalanches, dtype=torch.int64).pin_memory()
+    h_tal = torch.empty((w.primaries.n_avalanches, w.gas.n_levels + 1), dtype=torch.int64).pin_memory()
+    e2e_steps = max(1, min(args.steps, 3))
+    torch.cuda.synchronize()
+    barrier()
+    t0 = time.perf_counter()
+    e2e_real = 0
+    for _ in range(e2e_steps):
+        flush.fill_(1)
+        st = av.run(prim_host, opt, cap, stream=stream, allow=(A.GT_OK,))
+        h_elec.copy_(av.ep["electrons"], non_blocking=True)
+        h_tal.copy_(av.ep["tallies"], non_blocking=True)
+        torch.cuda.synchronize()
+        e2e_real += st["real_collisions"]
+    e2e_t = max_over_ranks(time.perf_counter() - t0, dev)
+    e2e_value = sum_over_ranks(float(e2e_real), dev) / e2e_t
+    h2d = sum(prim_host[k].numel() * prim_host[k].element_size()
+              for k in list(A.Avalanche.PRIM_KEYS) + ["aval", "uid", "aval_field"])
+    d2h = h_elec.numel() * 8 + h_tal.numel() * 8 + 256
+
+    # plain FP64 GPU path (one avalanche per launch sequence) on a sample
+    plain = None
+    if rank == 0 and not args.no_plain:
+        sub = w.primaries.subset(list(range(args.plain_avalanches)))
+        psub = av.primaries_device(sub)
+        popt = A.RunOptions(seed=seed, t_max=w.t_max, precision=A.GT_FP64, mode=A.GT_PLAIN)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        pst = av.run(psub, popt, cap, stream=stream, allow=(A.GT_OK,))
+        torch.cuda.synchronize()
+        pdt = time.perf_counter() - t0
+        pobs = av.observables(pst["n_endpoints"], sub, collect_status=W.ANODE,
+                              drift_status=W.ANODE, gap=w.field.gap)
+        # the mixed batched run restricted to the same avalanches, for the gain match
+        st_m = av.run(psub, opt, cap, stream=stream, allow=(A.GT_OK,))
+        mobs = av.observables(st_m["n_endpoints"], sub, collect_status=W.ANODE,
+                              drift_status=W.ANODE, gap=w.field.gap)
+        se = math.hypot(pobs[1], mobs[1])
+        plain = {"value": pst["real_collisions"] / pdt, "unit": UNIT,
+                 "sample": f"avalanches 0..{args.plain_avalanches - 1}",
+                 "launches": pst["launches"], "generations": pst["iterations"],
+                 "gain_fp64_plain": pobs[0], "gain_mixed_batched": mobs[0],
+                 "gain_sigma": se,
+                 "matched_gain_3sigma": bool(abs(pobs[0] - mobs[0]) <= 3 * se),
+                 "vd_fp64_plain": pobs[3], "vd_mixed_batched": mobs[3]}
+
+    if rank != 0:
+        av.close()
+        return
+    kms = statistics.mean(kernel_ms)
+    fl_per_launch = flights / len(kernel_ms)
+    peak_clk = clk.get("sm_max_mhz") or 2070.0
+    peak = SM_COUNT * ISSUE_PER_SM_PER_CLK * peak_clk * 1e6 / 1e9  # G warp-inst/s
+    if INST_PER_WARP_FLIGHT:
+        achieved = INST_PER_WARP_FLIGHT * fl_per_launch / 32.0 / (kms / 1e3) / 1e9
+        roof = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "Gwarp-inst/s",
+                "frac": achieved / peak, "traffic": None,
+                "kernel": "k_batched<MixedElectron,PLATE>", "kernel_ms": kms,
+                "flights_per_launch": fl_per_launch,
+                "inst_per_warp_flight": INST_PER_WARP_FLIGHT,
+                "peak_note": "152 SMs x 4 issue/clk x max SM clock"}
+    else:
+        roof = {"bound": "alu", "achieved": None, "peak": peak, "unit": "Gwarp-inst/s",
+                "frac": None, "traffic": None, "kernel_ms": kms,
+                "flights_per_launch": fl_per_launch}
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": t_max_rank * 1e3 / args.steps,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32+f64",
+        "data": "synthetic",
+        "config": {"workload": WORKLOAD, "avalanches_per_gpu": args.avalanches,
+                   "field_kv_cm": [30, 50], "primaries_mean": 3, "gap_um": 128,
+                   "gas": "argon-like 12-level", "precision": "mixed", "mode": "batched",
+                   "block": stats[-1]["block"], "grid": stats[-1]["grid"],
+                   "flights_per_round": stats[-1]["flights_per_round"],
+                   "l2": "flushed (256 MB write) before every step"},
+        "flights_per_s": sum_over_ranks(float(flights), dev) / t_max_rank,
+        "null_fraction": 1.0 - real / max(flights, 1),
+        "electrons_per_step": stats[-1]["n_endpoints"],
+        "observables": {"gain": obs[0], "gain_se": obs[1], "vd_cm_per_ns": obs[3],
+                        "dt_cm2_per_ns": obs[4], "dl_cm2_per_ns": obs[5]},
+        "plain_fp64": plain,
+        "speedup_vs_plain_fp64": (value / plain["value"]) if plain else None,
+        "roofline": roof,
+        "cpu_baseline": cpu,
+        "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": h2d,
+                "d2h_bytes_per_step": d2h, "steps": e2e_steps},
+        "gpu_launches": int(sum(s["launches"] for s in stats)),
+        "clocks": clk,
+    }
+    print(json.dumps(line), flush=True)
+    av.close()
+
+
+# ----------------------------------------------------------- reference arm
+def run_reference(args) -> None:
+    """The reference arm is the FP64 CPU oracle on the host cores, on a
+    bounded sample of this workload per step (rank 0 only)."""
+    ws, rank, _ = dist_env()
+    if rank != 0:
+        return
+    from paper_2509_15377_gb300 import workloads as W
+    import oracle
+    oracle.build()
+    w = W.plate_batched(n_avalanches=args.avalanches, seed=0)
+    for _ in range(args.warmup):
+        oracle_baseline(w, 0, max(1, args.cpu_avalanches // 8))
+    real = 0
+    secs = 0.0
+    res = None
+    for _ in range(args.steps):
+        res = oracle_baseline(w, 0, args.cpu_avalanches)
+        real += res["real_collisions"]
+        secs += res["seconds"]
+    value = real / secs
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": secs * 1e3 / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic",
+            "config": {"workload": WORKLOAD, "avalanches_per_gpu": args.avalanches},
+            "cpu_baseline": {"kind": "oracle", "cores": res["cores"], "sample": res["sample"],
+                             "value": value, "unit": UNIT},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0,
+                    "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def parse(argv=None):
+    ap = argparse.ArgumentParser(description=__doc__)
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--avalanches", type=int, default=4096)
+    ap.add_argument("--capacity", type=int, default=100_000_000)
+    ap.add_argument("--block", type=int, default=0)
+    ap.add_argument("--flights-per-round", type=int, default=0)
+    ap.add_argument("--cpu-avalanches", type=int, default=64)
+    ap.add_argument("--plain-avalanches", type=int, default=32)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-plain", action="store_true")
+    return ap.parse_args(argv)
+
+
+def main(argv=None):
+    args = parse(argv)
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_ours(args)
+
+
+if __name__ == "__main__":
+    main()

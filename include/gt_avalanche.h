@@ -1,0 +1,275 @@
+/*
+ * gt_avalanche.h -- C ABI of the GB300 microscopic avalanche transport library.
+ *
+ * The library transports electrons collision by collision through a gas in
+ * an electric (and optionally uniform magnetic) field and multiplies them by
+ * ionisation: the AvalancheMicroscopic method of "Accelerating Garfield++
+ * with CUDA" (arXiv:2509.15377, Sec. 2, Fig. 2).  Each electron takes
+ * null-collision free flights dt = -ln(u)/nu_max (Skullerud's technique,
+ * cited in Sec. 1) in the field at the start of the flight; its kinetic
+ * energy indexes tabulated per-level collision rates (Magboltz-style tables,
+ * Sec. 1 and Sec. 4); a real or null collision is chosen; an elastic,
+ * excitation or ionising collision is applied with isotropic scattering; an
+ * ionisation appends a new electron to a device work queue ("stack
+ * processing", Sec. 2).  An electron stops when it leaves the volume, reaches
+ * its time limit or its collision limit ("Position is valid?", Fig. 2; status
+ * codes, Sec. 2).  The run returns, per electron, its start and end point
+ * (the endpoint record of Sec. 3.2) and, per avalanche, the number of
+ * electrons and the collision tallies.
+ *
+ * Units everywhere: cm, ns, eV, V/cm, T; rates in 1/ns.
+ *
+ * Conventions of every entry point:
+ *   - returns GT_OK (0) or a negative GT_ERR_* code; no exception or abort
+ *     crosses the ABI; gt_strerror() names the code;
+ *   - "host" pointers are read during the call only; "device" pointers are
+ *     CUDA device memory of the context's device owned by the caller, which
+ *     must stay valid until the call returns;
+ *   - the library owns only the context and what it uploads into it (the
+ *     rate table and the field constants); every output buffer, the work
+ *     space and the stream belong to the caller;
+ *   - avalanche_run is stream-ordered on the caller's stream and returns
+ *     after that stream has finished the run (it reads back a small status
+ *     block); it is not safe to call concurrently on one context.
+ */
+#ifndef GT_AVALANCHE_H
+#define GT_AVALANCHE_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define GT_ABI_VERSION 1
+#define GT_MAX_LEVELS 32 /* collision levels per gas table */
+
+/* ---- return codes ---------------------------------------------------- */
+#define GT_OK 0
+#define GT_ERR_ARG (-1)            /* invalid argument (null pointer, size, range) */
+#define GT_ERR_STATE (-2)          /* gas table or field not set up */
+#define GT_ERR_WORKSPACE (-3)      /* work space too small or misaligned */
+#define GT_ERR_QUEUE_OVERFLOW (-4) /* more electrons than endpoint capacity: the
+                                      stored ones are complete, the rest dropped */
+#define GT_ERR_TIMEOUT (-5)        /* a bounded wait or the run's time budget ran
+                                      out: the result is partial */
+#define GT_ERR_CUDA (-6)           /* a CUDA runtime call failed */
+#define GT_ERR_NO_DEVICE (-7)      /* no usable CUDA device */
+#define GT_ERR_UNSUPPORTED (-8)    /* combination not implemented */
+
+/* ---- electron status codes (endpoint.status; non-zero = finished) ---- */
+#define GT_ST_ACTIVE 0        /* not finished (only in a partial result) */
+#define GT_ST_ANODE 1         /* PLATE: z >= gap */
+#define GT_ST_CATHODE 2       /* PLATE: z < 0 */
+#define GT_ST_WIRE 3          /* COAX/GRID: x^2 + y^2 <= wire_r^2 */
+#define GT_ST_TUBE 4          /* COAX: x^2 + y^2 >= tube_r^2 */
+#define GT_ST_OUT_OF_MAP 5    /* GRID: outside the map box */
+#define GT_ST_TIME 6          /* reached t_max */
+#define GT_ST_COLL_LIMIT 7    /* reached coll_limit real collisions */
+#define GT_ST_FLIGHT_LIMIT 8  /* 2^32 - 1 flights */
+
+/* ---- enumerations ---------------------------------------------------- */
+#define GT_LEVEL_ELASTIC 0    /* isotropic, energy x (1 - recoil (1 - cos chi)) */
+#define GT_LEVEL_EXCITATION 1 /* isotropic, energy - threshold */
+#define GT_LEVEL_IONISATION 2 /* isotropic, energy - threshold split uniformly
+                                 with a new isotropic electron */
+
+#define GT_FIELD_UNIFORM 0 /* E = (0, 0, -e0) everywhere, no boundary */
+#define GT_FIELD_PLATE 1   /* E = (0, 0, -E_k) between z = 0 and z = gap */
+#define GT_FIELD_COAX 2    /* E = V / (r ln(b/a)) r-hat, wire radius a, tube b */
+#define GT_FIELD_GRID 3    /* trilinear interpolation of a regular float4 map */
+
+#define GT_FP64 0  /* every step in FP64 */
+#define GT_MIXED 1 /* FP32 kinematics, table and scattering; FP64 position and
+                      time accumulation and FP64 threshold/boundary decisions */
+
+#define GT_BATCHED 0 /* all avalanches in one persistent kernel with a global
+                        electron queue */
+#define GT_PLAIN 1   /* one avalanche at a time, one transport launch per
+                        generation followed by stack compaction (the
+                        structure of the paper's GPU port, Sec. 2) */
+
+typedef struct gt_ctx gt_ctx;
+
+/* ---- gas table (Sec. 1 and Sec. 4: tabulated cross-sections) ----------
+ * rate[k * n_levels + j] is the collision rate of level j at the node energy
+ * k * d_eps (1/ns, >= 0); between nodes the rates are interpolated linearly,
+ * beyond the last node the last node is used.  nu_max <= 0 selects
+ * (1 + 1e-6) * max_k sum_j rate; a given nu_max must be >= that maximum. */
+typedef struct {
+    int32_t n_levels;          /* 1..GT_MAX_LEVELS */
+    int32_t n_nodes;           /* >= 2 */
+    double d_eps;              /* eV, > 0 */
+    const int32_t *level_type; /* host [n_levels] GT_LEVEL_* */
+    const double *threshold;   /* host [n_levels] eV lost (excitation, ionisation) */
+    const double *rate;        /* host [n_nodes * n_levels] 1/ns */
+    double recoil;             /* 2 m / M for elastic recoil loss, in [0, 0.5) */
+    double nu_max;             /* 1/ns */
+} gt_gas;
+
+/* ---- field and geometry (Fig. 2 "Find E field"; Sec. 3.1 field maps) -- */
+typedef struct {
+    int32_t kind;              /* GT_FIELD_* */
+    double e0;                 /* UNIFORM |E|; PLATE default |E| (V/cm) */
+    double gap;                /* PLATE anode position (cm) */
+    double wire_r, tube_r;     /* COAX radii; GRID wire radius (0 = none) (cm) */
+    double voltage;            /* COAX wire voltage (V) */
+    double b[3];               /* uniform magnetic field (T) */
+    int32_t nx, ny, nz;        /* GRID nodes, each >= 2 */
+    double origin[3];          /* GRID position of node (0,0,0) (cm) */
+    double spacing[3];         /* GRID node spacing (cm) */
+    const float *grid;         /* GRID device [nz][ny][nx] float4 (Ex, Ey, Ez, -),
+                                  16-byte aligned; kept by pointer, must stay
+                                  valid while runs use this field */
+} gt_field;
+
+/* ---- one run --------------------------------------------------------- */
+typedef struct {
+    int64_t n_primaries;
+    int32_t n_avalanches;
+    int32_t primaries_on_device;  /* 0: the arrays below are host memory and are
+                                     copied inside the run; 1: device memory */
+    const double *x, *y, *z, *t, *e;  /* [n_primaries] position, time, energy */
+    const double *dx, *dy, *dz;       /* [n_primaries] unit direction */
+    const int32_t *aval;              /* [n_primaries] avalanche in [0, n_avalanches) */
+    const uint64_t *uid;              /* [n_primaries] electron ids, unique */
+    const double *aval_field;         /* PLATE: [n_avalanches] |E| per avalanche
+                                         (same memory kind), or NULL for e0 */
+    uint64_t seed;
+    double t_max;                     /* ns, <= 0: none */
+    uint32_t coll_limit;              /* real collisions per electron, 0: none */
+    int32_t precision;                /* GT_FP64 / GT_MIXED */
+    int32_t mode;                     /* GT_BATCHED / GT_PLAIN */
+    int32_t block;                    /* threads per CTA, 0 = default */
+    int32_t flights_per_round;        /* BATCHED: flights between queue refills
+                                         and FP64 flushes, 0 = default */
+    int32_t grid;                     /* BATCHED: CTAs, 0 = one per SM */
+    uint64_t size_limit;              /* BATCHED: max electrons per avalanche,
+                                         further secondaries dropped; 0 = none */
+    double spin_limit_ms;             /* longest wait without queue progress, 0 =
+                                         60 s; exceeded -> GT_ERR_TIMEOUT */
+    double time_limit_ms;             /* whole-run budget, 0 = 600 s */
+    int32_t debug_flags;              /* GT_DEBUG_*, 0 in normal use */
+    int32_t reserved;
+} gt_run;
+
+/* Fault injection for tests: reserve one queue slot that is never filled,
+ * so every waiting worker eventually gives up after spin_limit_ms and the
+ * run returns GT_ERR_TIMEOUT (the GPU context stays usable). */
+#define GT_DEBUG_UNFILLED_SLOT 1
+
+/* ---- outputs (caller-owned device arrays) ------------------------------
+ * Endpoint slot i holds one electron: slots [0, n_primaries) are the
+ * primaries in input order, later slots the electrons created by ionisation
+ * in completion order (the order of those is not reproducible; sort by uid).
+ * This is the record of GetElectronEndpoint (Sec. 3.2): start x0..e0, end
+ * x1..e1 and the status, plus the avalanche, the id and the flight count. */
+typedef struct {
+    int64_t capacity;                 /* slots in every per-electron array */
+    double *x0, *y0, *z0, *t0, *e0;   /* [capacity] start */
+    double *x1, *y1, *z1, *t1, *e1;   /* [capacity] end */
+    int32_t *status;                  /* [capacity] GT_ST_* */
+    int32_t *aval;                    /* [capacity] */
+    uint64_t *uid;                    /* [capacity] */
+    uint32_t *n_flight;               /* [capacity] flights (real + null) */
+    uint64_t *electrons;              /* [n_avalanches] electrons stored */
+    uint64_t *tallies;                /* [n_avalanches][n_levels + 1] real
+                                         collisions per level, then null ones */
+} gt_endpoints;
+
+/* ---- run summary (host, filled by avalanche_run) ---------------------- */
+typedef struct {
+    int64_t n_endpoints;      /* slots written */
+    int64_t n_dropped;        /* secondaries not stored (capacity or size_limit) */
+    uint64_t real_collisions; /* elastic + excitation + ionisation */
+    uint64_t null_collisions; /* flights ending in a null collision */
+    uint64_t flights;         /* all flights, including the final ones */
+    double transport_ms;      /* GPU time of the transport kernel(s), CUDA
+                                 events on the run's stream */
+    int32_t launches;         /* kernels launched by the run */
+    int32_t iterations;       /* PLAIN: generations summed over avalanches */
+    int32_t status;           /* same value as the return code */
+    int32_t block, flights_per_round, grid; /* launch shape actually used */
+} gt_stats;
+
+/* ---- entry points ---------------------------------------------------- */
+
+/* ABI version of the loaded library (GT_ABI_VERSION). */
+int gt_abi_version(void);
+
+/* Human-readable name of a return code.  Static string, never NULL. */
+const char *gt_strerror(int code);
+
+/* sizeof of gt_gas, gt_field, gt_run, gt_endpoints and gt_stats, written to
+ * sizes[0..4] (n >= 5), so that bindings can check their struct layouts.
+ * Needs no device. */
+int gt_abi_sizes(size_t *sizes, int n);
+
+/* Text of the last CUDA failure seen by this context ("" if none).  Valid
+ * until the next call on the context. */
+const char *gt_last_cuda_error(gt_ctx *ctx);
+
+/* Create a context on CUDA device `device` (the GPUExclusive run mode and
+ * device index of SetRunModeOptions, Sec. 3.2).  *ctx receives the handle.
+ * GT_ERR_NO_DEVICE if the device does not exist or is not a GB300-class
+ * (sm_103) device this library was built for. */
+int gt_create(gt_ctx **ctx, int device);
+
+/* Release the context and everything it uploaded.  NULL is accepted. */
+int gt_destroy(gt_ctx *ctx);
+
+/* Upload a gas table (Sec. 3.1: preprocessed once on the host, copied once
+ * to the GPU).  Builds the cumulative per-level rate table in FP64 and FP32,
+ * nu_max and the per-level constants.  Replaces any previous table.
+ * GT_ERR_ARG for a negative rate, a bad size, an unknown level type or a
+ * nu_max below the total rate. */
+int gas_table_upload(gt_ctx *ctx, const gt_gas *gas);
+
+/* nu_max (1/ns) of the uploaded table. */
+int gt_gas_nu_max(gt_ctx *ctx, double *nu_max);
+
+/* Set the field and geometry used by later runs (Sec. 3.1: the field data
+ * is transferred once, before the first transport).  The GRID map stays in
+ * caller memory and is read by pointer. */
+int field_setup(gt_ctx *ctx, const gt_field *field);
+
+/* Work-space bytes that avalanche_run needs for `run` with endpoint
+ * `capacity`.  The work space is caller-owned device memory, 256-byte
+ * aligned; its contents need no initialisation. */
+int gt_workspace_bytes(gt_ctx *ctx, const gt_run *run, int64_t capacity, size_t *bytes);
+
+/* Transport every avalanche of `run` to completion (Fig. 2 repeated until
+ * no electron is active) and fill `out` and `*stats`.  `stream` is a
+ * cudaStream_t (NULL = the legacy default stream).  Returns GT_OK, or
+ * GT_ERR_QUEUE_OVERFLOW / GT_ERR_TIMEOUT with a partial but consistent
+ * result, or an argument / CUDA error with nothing guaranteed in `out`. */
+int avalanche_run(gt_ctx *ctx, const gt_run *run, const gt_endpoints *out, void *workspace,
+                  size_t workspace_bytes, void *stream, gt_stats *stats);
+
+/* Observables of a finished run (Sec. 2: gain = electrons at the end of the
+ * avalanche / initial electrons), computed on the device from the first
+ * n_endpoints slots of `ep` and written as GT_OBS_COUNT doubles to the
+ * device array obs:
+ *   [0] mean gain: electrons ending with status `collect_status`, averaged
+ *       over avalanches with at least one primary, per primary;
+ *   [1] standard error of [0];
+ *   [2] number of avalanches with at least one primary;
+ *   [3] drift velocity sum(z1 - z0) / sum(t1 - t0) (cm/ns) over electrons
+ *       ending with `drift_status` (any status if drift_status < 0);
+ *   [4] transverse diffusion <(x1-x0)^2 + (y1-y0)^2> / (4 <t1-t0>) (cm^2/ns);
+ *   [5] longitudinal diffusion var(z1 - z0) / (2 <t1-t0>) (cm^2/ns);
+ *   [6] electrons counted in [3]..[5];
+ *   [7] Townsend coefficient ln([0]) / gap (1/cm; 0 unless gap > 0).
+ * `n_primaries_per_aval` is a device int32 [n_avalanches] array. */
+#define GT_OBS_COUNT 8
+int avalanche_observables(gt_ctx *ctx, const gt_endpoints *ep, int64_t n_endpoints,
+                          int32_t n_avalanches, const int32_t *n_primaries_per_aval,
+                          int32_t collect_status, int32_t drift_status, double gap,
+                          double *obs, void *stream);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* GT_AVALANCHE_H */

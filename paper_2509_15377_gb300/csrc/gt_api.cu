@@ -1,0 +1,658 @@
+// gt_api.cu -- host runtime behind the C ABI of gt_avalanche.h: context,
+// gas-table and field upload (done once, outside the transport, as in the
+// paper's Sec. 3.1 and Fig. 3), work-space layout, the batched and plain
+// drivers and error mapping.
+#include <algorithm>
+#include <chrono>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <new>
+#include <vector>
+
+#include "gt_avalanche.h"
+#include "gt_kernels.cuh"
+#include "gt_launch.h"
+
+using namespace gt;
+
+struct gt_ctx {
+    int device = -1;
+    int sms = 0;
+    size_t smem_optin = 0;
+    bool has_gas = false, has_field = false;
+    DevGas gas{};
+    DevField field{};
+    double *d_cum64 = nullptr;
+    float *d_cum32 = nullptr;
+    cudaEvent_t ev0 = nullptr, ev1 = nullptr;
+    Header *h_hdr = nullptr;  // pinned copy of the work-space header
+    unsigned long long *d_obs_counts = nullptr;
+    size_t obs_counts_cap = 0;
+    double *d_obs_partials = nullptr;
+    size_t obs_partials_cap = 0;
+    char last_error[256] = {0};
+};
+
+namespace {
+
+// Makes the context's device current for the duration of a call.
+struct DeviceGuard {
+    int prev = -1;
+    bool ok = false;
+    explicit DeviceGuard(int dev)
+    {
+        if (cudaGetDevice(&prev) != cudaSuccess) prev = -1;
+        ok = cudaSetDevice(dev) == cudaSuccess;
+    }
+    ~DeviceGuard()
+    {
+        if (prev >= 0) cudaSetDevice(prev);
+    }
+};
+
+int cuda_fail(gt_ctx *ctx, cudaError_t e, const char *where)
+{
+    if (ctx)
+        snprintf(ctx->last_error, sizeof(ctx->last_error), "%s: %s", where,
+                 cudaGetErrorString(e));
+    return GT_ERR_CUDA;
+}
+
+#define GT_CUDA(ctx, call)                                                                 \
+    do {                                                                                   \
+        cudaError_t e_ = (call);                                                           \
+        if (e_ != cudaSuccess) return cuda_fail((ctx), e_, #call);                         \
+    } while (0)
+
+size_t align256(size_t x) { return (x + 255) & ~(size_t)255; }
+
+// Work-space layout.  Every region starts on a 256-byte boundary.
+struct Layout {
+    size_t hdr, ready, bvx, bvy, bvz, created, afield, prim, order, stacks, total;
+    size_t stack_entry_bytes;
+};
+
+constexpr size_t kStackEntry = 7 * sizeof(double) + 2 * sizeof(uint32_t) + sizeof(uint64_t) +
+                               sizeof(int64_t) + sizeof(int32_t);
+
+Layout layout_for(const gt_run *run, int64_t capacity)
+{
+    Layout L{};
+    size_t off = 0;
+    L.hdr = off; off = align256(off + sizeof(Header));
+    L.ready = off; off = align256(off + sizeof(uint32_t) * (size_t)capacity);
+    L.bvx = off; off = align256(off + sizeof(double) * (size_t)capacity);
+    L.bvy = off; off = align256(off + sizeof(double) * (size_t)capacity);
+    L.bvz = off; off = align256(off + sizeof(double) * (size_t)capacity);
+    const size_t na = (size_t)std::max(run->n_avalanches, 1);
+    L.created = off; off = align256(off + sizeof(unsigned long long) * na);
+    L.afield = off;
+    if (!run->primaries_on_device && run->aval_field) off = align256(off + sizeof(double) * na);
+    L.prim = off;
+    const size_t np = (size_t)std::max<int64_t>(run->n_primaries, 1);
+    if (!run->primaries_on_device)
+        off = align256(off + np * (8 * sizeof(double) + sizeof(int32_t) + sizeof(uint64_t)) + 8 * 256);
+    L.order = off;
+    L.stacks = off;
+    L.stack_entry_bytes = kStackEntry;
+    if (run->mode == GT_PLAIN) {
+        off = align256(off + sizeof(long long) * np);
+        L.stacks = off;
+        off = align256(off + 3 * (kStackEntry * (size_t)capacity + 16 * 256));
+    }
+    L.total = off;
+    return L;
+}
+
+// Carve one plain-mode stack (SoA) out of a region.
+Stack carve_stack(char *&p, int64_t cap)
+{
+    Stack s;
+    auto take = [&](size_t bytes) {
+        char *q = p;
+        p += align256(bytes);
+        return q;
+    };
+    s.x = (double *)take(sizeof(double) * cap);
+    s.y = (double *)take(sizeof(double) * cap);
+    s.z = (double *)take(sizeof(double) * cap);
+    s.t = (double *)take(sizeof(double) * cap);
+    s.vx = (double *)take(sizeof(double) * cap);
+    s.vy = (double *)take(sizeof(double) * cap);
+    s.vz = (double *)take(sizeof(double) * cap);
+    s.nf = (uint32_t *)take(sizeof(uint32_t) * cap);
+    s.nreal = (uint32_t *)take(sizeof(uint32_t) * cap);
+    s.uid = (uint64_t *)take(sizeof(uint64_t) * cap);
+    s.slot = (int64_t *)take(sizeof(int64_t) * cap);
+    s.alive = (int32_t *)take(sizeof(int32_t) * cap);
+    return s;
+}
+
+int default_block(int precision) { return precision == GT_FP64 ? 256 : 512; }
+
+bool finite_pos(double x) { return std::isfinite(x) && x > 0.0; }
+
+}  // namespace
+
+extern "C" {
+
+int gt_abi_version(void) { return GT_ABI_VERSION; }
+
+const char *gt_strerror(int code)
+{
+    switch (code) {
+    case GT_OK: return "ok";
+    case GT_ERR_ARG: return "invalid argument";
+    case GT_ERR_STATE: return "gas table or field not set up";
+    case GT_ERR_WORKSPACE: return "work space too small or misaligned";
+    case GT_ERR_QUEUE_OVERFLOW: return "endpoint capacity exceeded (result partial)";
+    case GT_ERR_TIMEOUT: return "bounded wait or time budget exceeded (result partial)";
+    case GT_ERR_CUDA: return "CUDA runtime error";
+    case GT_ERR_NO_DEVICE: return "no usable sm_103 CUDA device";
+    case GT_ERR_UNSUPPORTED: return "unsupported combination";
+    default: return "unknown error";
+    }
+}
+
+const char *gt_last_cuda_error(gt_ctx *ctx) { return ctx ? ctx->last_error : ""; }
+
+int gt_create(gt_ctx **out, int device)
+{
+    if (!out) return GT_ERR_ARG;
+    *out = nullptr;
+    int n = 0;
+    if (cudaGetDeviceCount(&n) != cudaSuccess || n <= 0) {
+        cudaGetLastError();
+        return GT_ERR_NO_DEVICE;
+    }
+    if (device < 0 || device >= n) return GT_ERR_NO_DEVICE;
+    cudaDeviceProp prop;
+    if (cudaGetDeviceProperties(&prop, device) != cudaSuccess) return GT_ERR_NO_DEVICE;
+    if (prop.major * 10 + prop.minor != 103) return GT_ERR_NO_DEVICE;
+    gt_ctx *ctx = new (std::nothrow) gt_ctx();
+    if (!ctx) return GT_ERR_CUDA;
+    ctx->device = device;
+    ctx->sms = prop.multiProcessorCount;
+    ctx->smem_optin = prop.sharedMemPerBlockOptin;
+    DeviceGuard g(device);
+    if (!g.ok || configure_fp64(ctx->smem_optin) != cudaSuccess ||
+        configure_mixed(ctx->smem_optin) != cudaSuccess ||
+        cudaEventCreate(&ctx->ev0) != cudaSuccess || cudaEventCreate(&ctx->ev1) != cudaSuccess ||
+        cudaMallocHost((void **)&ctx->h_hdr, sizeof(Header)) != cudaSuccess) {
+        gt_destroy(ctx);
+        return GT_ERR_CUDA;
+    }
+    *out = ctx;
+    return GT_OK;
+}
+
+int gt_abi_sizes(size_t *sizes, int n)
+{
+    if (!sizes || n < 5) return GT_ERR_ARG;
+    sizes[0] = sizeof(gt_gas);
+    sizes[1] = sizeof(gt_field);
+    sizes[2] = sizeof(gt_run);
+    sizes[3] = sizeof(gt_endpoints);
+    sizes[4] = sizeof(gt_stats);
+    return GT_OK;
+}
+
+int gt_destroy(gt_ctx *ctx)
+{
+    if (!ctx) return GT_OK;
+    {
+        DeviceGuard g(ctx->device);
+        if (ctx->d_cum64) cudaFree(ctx->d_cum64);
+        if (ctx->d_cum32) cudaFree(ctx->d_cum32);
+        if (ctx->d_obs_counts) cudaFree(ctx->d_obs_counts);
+        if (ctx->d_obs_partials) cudaFree(ctx->d_obs_partials);
+        if (ctx->ev0) cudaEventDestroy(ctx->ev0);
+        if (ctx->ev1) cudaEventDestroy(ctx->ev1);
+        if (ctx->h_hdr) cudaFreeHost(ctx->h_hdr);
+    }
+    delete ctx;
+    return GT_OK;
+}
+
+int gas_table_upload(gt_ctx *ctx, const gt_gas *g)
+{
+    if (!ctx || !g) return GT_ERR_ARG;
+    const int L = g->n_levels, N = g->n_nodes;
+    if (L < 1 || L > GT_MAX_LEVELS || N < 2 || !finite_pos(g->d_eps) || !g->level_type ||
+        !g->threshold || !g->rate || !(g->recoil >= 0.0 && g->recoil < 0.5))
+        return GT_ERR_ARG;
+    for (int j = 0; j < L; ++j) {
+        const int t = g->level_type[j];
+        if (t != GT_LEVEL_ELASTIC && t != GT_LEVEL_EXCITATION && t != GT_LEVEL_IONISATION)
+            return GT_ERR_ARG;
+        if (!(g->threshold[j] >= 0.0) || !std::isfinite(g->threshold[j])) return GT_ERR_ARG;
+    }
+    // cumulative rates over levels at every node, FP64, and their maximum
+    std::vector<double> cum((size_t)N * L);
+    double top = 0.0;
+    for (int k = 0; k < N; ++k) {
+        double s = 0.0;
+        for (int j = 0; j < L; ++j) {
+            const double r = g->rate[(size_t)k * L + j];
+            if (!(r >= 0.0) || !std::isfinite(r)) return GT_ERR_ARG;
+            s += r;
+            cum[(size_t)k * L + j] = s;
+        }
+        top = std::max(top, s);
+    }
+    const double nu_max = g->nu_max > 0.0 ? g->nu_max : top * (1.0 + 1e-6);
+    if (!finite_pos(nu_max) || nu_max < top) return GT_ERR_ARG;
+    std::vector<float> cum32(cum.size());
+    for (size_t i = 0; i < cum.size(); ++i) cum32[i] = (float)cum[i];
+
+    DeviceGuard dg(ctx->device);
+    if (!dg.ok) return GT_ERR_CUDA;
+    if (ctx->d_cum64) cudaFree(ctx->d_cum64);
+    if (ctx->d_cum32) cudaFree(ctx->d_cum32);
+    ctx->d_cum64 = nullptr;
+    ctx->d_cum32 = nullptr;
+    ctx->has_gas = false;
+    GT_CUDA(ctx, cudaMalloc((void **)&ctx->d_cum64, sizeof(double) * cum.size()));
+    GT_CUDA(ctx, cudaMalloc((void **)&ctx->d_cum32, sizeof(float) * cum.size()));
+    GT_CUDA(ctx, cudaMemcpy(ctx->d_cum64, cum.data(), sizeof(double) * cum.size(),
+                            cudaMemcpyHostToDevice));
+    GT_CUDA(ctx, cudaMemcpy(ctx->d_cum32, cum32.data(), sizeof(float) * cum.size(),
+                            cudaMemcpyHostToDevice));
+    DevGas &d = ctx->gas;
+    d = DevGas{};
+    d.n_levels = L;
+    d.n_nodes = N;
+    d.d_eps = g->d_eps;
+    d.inv_d_eps = 1.0 / g->d_eps;
+    d.nu_max = nu_max;
+    d.inv_nu_max = 1.0 / nu_max;
+    d.recoil = g->recoil;
+    d.inv_d_eps_f = (float)d.inv_d_eps;
+    d.nu_max_f = (float)nu_max;
+    d.inv_nu_max_f = (float)d.inv_nu_max;
+    d.recoil_f = (float)g->recoil;
+    d.last_x_f = (float)(N - 1);
+    d.cum64 = ctx->d_cum64;
+    d.cum32 = ctx->d_cum32;
+    for (int j = 0; j < L; ++j) {
+        d.type[j] = g->level_type[j];
+        d.thr[j] = g->threshold[j];
+    }
+    ctx->has_gas = true;
+    return GT_OK;
+}
+
+int gt_gas_nu_max(gt_ctx *ctx, double *nu_max)
+{
+    if (!ctx || !nu_max) return GT_ERR_ARG;
+    if (!ctx->has_gas) return GT_ERR_STATE;
+    *nu_max = ctx->gas.nu_max;
+    return GT_OK;
+}
+
+int field_setup(gt_ctx *ctx, const gt_field *f)
+{
+    if (!ctx || !f) return GT_ERR_ARG;
+    DevField d{};
+    d.kind = f->kind;
+    for (int i = 0; i < 3; ++i) {
+        if (!std::isfinite(f->b[i])) return GT_ERR_ARG;
+        d.w[i] = -kOmega * f->b[i];
+    }
+    d.has_b = (f->b[0] != 0.0 || f->b[1] != 0.0 || f->b[2] != 0.0) ? 1 : 0;
+    d.e0 = f->e0;
+    switch (f->kind) {
+    case GT_FIELD_UNIFORM:
+        if (!std::isfinite(f->e0)) return GT_ERR_ARG;
+        break;
+    case GT_FIELD_PLATE:
+        if (!std::isfinite(f->e0) || !finite_pos(f->gap)) return GT_ERR_ARG;
+        d.gap = f->gap;
+        break;
+    case GT_FIELD_COAX:
+        if (!finite_pos(f->wire_r) || !finite_pos(f->tube_r) || f->tube_r <= f->wire_r ||
+            !std::isfinite(f->voltage))
+            return GT_ERR_ARG;
+        d.wire_r2 = f->wire_r * f->wire_r;
+        d.tube_r2 = f->tube_r * f->tube_r;
+        d.coax_k = f->voltage / std::log(f->tube_r / f->wire_r);
+        break;
+    case GT_FIELD_GRID:
+        if (f->nx < 2 || f->ny < 2 || f->nz < 2 || !f->grid ||
+            ((uintptr_t)f->grid & 15u) != 0 || !(f->wire_r >= 0.0))
+            return GT_ERR_ARG;
+        d.nx = f->nx; d.ny = f->ny; d.nz = f->nz;
+        for (int i = 0; i < 3; ++i) {
+            if (!finite_pos(f->spacing[i]) || !std::isfinite(f->origin[i])) return GT_ERR_ARG;
+            d.origin[i] = f->origin[i];
+            d.inv_spacing[i] = 1.0 / f->spacing[i];
+        }
+        d.hi[0] = f->origin[0] + (f->nx - 1) * f->spacing[0];
+        d.hi[1] = f->origin[1] + (f->ny - 1) * f->spacing[1];
+        d.hi[2] = f->origin[2] + (f->nz - 1) * f->spacing[2];
+        d.wire_r2 = f->wire_r * f->wire_r;
+        d.grid = reinterpret_cast<const float4 *>(f->grid);
+        break;
+    default:
+        return GT_ERR_ARG;
+    }
+    ctx->field = d;
+    ctx->has_field = true;
+    return GT_OK;
+}
+
+int gt_workspace_bytes(gt_ctx *ctx, const gt_run *run, int64_t capacity, size_t *bytes)
+{
+    if (!ctx || !run || !bytes || capacity < 0 || run->n_avalanches < 0 || run->n_primaries < 0)
+        return GT_ERR_ARG;
+    *bytes = layout_for(run, capacity).total;
+    return GT_OK;
+}
+
+// ------------------------------------------------------------------ run
+static int validate_run(gt_ctx *ctx, const gt_run *r, const gt_endpoints *o, void *ws,
+                        size_t ws_bytes)
+{
+    if (!r || !o) return GT_ERR_ARG;
+    if (!ctx->has_gas || !ctx->has_field) return GT_ERR_STATE;
+    if (r->n_primaries < 0 || r->n_avalanches < 0) return GT_ERR_ARG;
+    if (r->n_primaries > 0 && r->n_avalanches < 1) return GT_ERR_ARG;
+    if (r->precision != GT_FP64 && r->precision != GT_MIXED) return GT_ERR_ARG;
+    if (r->mode != GT_BATCHED && r->mode != GT_PLAIN) return GT_ERR_ARG;
+    if (!std::isfinite(r->t_max)) return GT_ERR_ARG;
+    if (r->block < 0 || r->flights_per_round < 0 || r->grid < 0) return GT_ERR_ARG;
+    if (r->block && (r->block % 32 != 0 ||
+                     r->block > (r->precision == GT_FP64 ? max_block_fp64() : max_block_mixed())))
+        return GT_ERR_ARG;
+    if (r->spin_limit_ms < 0 || r->time_limit_ms < 0) return GT_ERR_ARG;
+    // an electron in the unbounded uniform field must stop somehow
+    if (ctx->field.kind == GT_FIELD_UNIFORM && !(r->t_max > 0.0) && r->coll_limit == 0)
+        return GT_ERR_ARG;
+    const int64_t need = r->n_primaries + ((r->debug_flags & GT_DEBUG_UNFILLED_SLOT) ? 1 : 0);
+    if (o->capacity < need || o->capacity < 0) return GT_ERR_ARG;
+    if (o->capacity > 0 && (!o->x0 || !o->y0 || !o->z0 || !o->t0 || !o->e0 || !o->x1 || !o->y1 ||
+                            !o->z1 || !o->t1 || !o->e1 || !o->status || !o->aval || !o->uid ||
+                            !o->n_flight))
+        return GT_ERR_ARG;
+    if (r->n_avalanches > 0 && (!o->electrons || !o->tallies)) return GT_ERR_ARG;
+    if (r->n_primaries > 0 && (!r->x || !r->y || !r->z || !r->t || !r->e || !r->dx || !r->dy ||
+                               !r->dz || !r->aval || !r->uid))
+        return GT_ERR_ARG;
+    if (!ws || ((uintptr_t)ws & 255u) != 0) return GT_ERR_WORKSPACE;
+    if (ws_bytes < layout_for(r, o->capacity).total) return GT_ERR_WORKSPACE;
+    if (!r->primaries_on_device) {
+        for (int64_t i = 0; i < r->n_primaries; ++i) {
+            if (r->aval[i] < 0 || r->aval[i] >= r->n_avalanches) return GT_ERR_ARG;
+            if (!(r->e[i] >= 0.0) || !std::isfinite(r->e[i])) return GT_ERR_ARG;
+        }
+    }
+    return GT_OK;
+}
+
+static int finish_status(const Header &h)
+{
+    if (h.error & ERR_BADARG) return GT_ERR_ARG;
+    if (h.error & ERR_TIMEOUT) return GT_ERR_TIMEOUT;
+    if (h.error & ERR_OVERFLOW) return GT_ERR_QUEUE_OVERFLOW;
+    return GT_OK;
+}
+
+int avalanche_run(gt_ctx *ctx, const gt_run *r, const gt_endpoints *o, void *ws, size_t ws_bytes,
+                  void *stream, gt_stats *stats)
+{
+    if (!ctx) return GT_ERR_ARG;
+    int rc = validate_run(ctx, r, o, ws, ws_bytes);
+    if (rc != GT_OK) return rc;
+    DeviceGuard dg(ctx->device);
+    if (!dg.ok) return GT_ERR_CUDA;
+    cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+    const Layout Ly = layout_for(r, o->capacity);
+    char *base = static_cast<char *>(ws);
+    const int64_t np = r->n_primaries;
+    const int na = r->n_avalanches;
+    const int L = ctx->gas.n_levels;
+    int launches = 0;
+
+    RunParams p{};
+    p.gas = ctx->gas;
+    p.field = ctx->field;
+    p.x0 = o->x0; p.y0 = o->y0; p.z0 = o->z0; p.t0 = o->t0; p.e0 = o->e0;
+    p.x1 = o->x1; p.y1 = o->y1; p.z1 = o->z1; p.t1 = o->t1; p.e1 = o->e1;
+    p.status = o->status; p.aval = o->aval; p.uid = o->uid; p.nflight = o->n_flight;
+    p.tallies = o->tallies; p.electrons = o->electrons;
+    p.capacity = o->capacity;
+    p.hdr = reinterpret_cast<Header *>(base + Ly.hdr);
+    p.ready = reinterpret_cast<unsigned int *>(base + Ly.ready);
+    p.bvx = reinterpret_cast<double *>(base + Ly.bvx);
+    p.bvy = reinterpret_cast<double *>(base + Ly.bvy);
+    p.bvz = reinterpret_cast<double *>(base + Ly.bvz);
+    p.created = reinterpret_cast<unsigned long long *>(base + Ly.created);
+    p.seed = r->seed;
+    p.t_max = r->t_max > 0.0 ? r->t_max : 0.0;
+    p.coll_limit = r->coll_limit;
+    p.flights_per_round = r->flights_per_round > 0 ? r->flights_per_round : 16;
+    p.size_limit = r->size_limit;
+    p.spin_limit_ns = (long long)((r->spin_limit_ms > 0 ? r->spin_limit_ms : 60000.0) * 1e6);
+    p.time_limit_ns = (long long)((r->time_limit_ms > 0 ? r->time_limit_ms : 600000.0) * 1e6);
+    p.n_avalanches = na;
+
+    // primaries: stage host arrays in the work space (inside the run)
+    SeedArgs sa{};
+    sa.n = np;
+    sa.unfilled_slot = (r->debug_flags & GT_DEBUG_UNFILLED_SLOT) ? 1 : 0;
+    p.aval_field = r->aval_field;
+    if (!r->primaries_on_device) {
+        char *q = base + Ly.prim;
+        auto stage = [&](const void *src, size_t bytes) -> void * {
+            void *dst = q;
+            q += align256(bytes);
+            if (bytes && cudaMemcpyAsync(dst, src, bytes, cudaMemcpyHostToDevice, s) != cudaSuccess)
+                return nullptr;
+            return dst;
+        };
+        const size_t db = sizeof(double) * (size_t)np;
+        void *ptrs[10] = {stage(r->x, db), stage(r->y, db), stage(r->z, db), stage(r->t, db),
+                          stage(r->e, db), stage(r->dx, db), stage(r->dy, db), stage(r->dz, db),
+                          stage(r->aval, sizeof(int32_t) * (size_t)np),
+                          stage(r->uid, sizeof(uint64_t) * (size_t)np)};
+        for (void *v : ptrs)
+            if (!v) return cuda_fail(ctx, cudaGetLastError(), "primaries upload");
+        sa.x = (const double *)ptrs[0]; sa.y = (const double *)ptrs[1];
+        sa.z = (const double *)ptrs[2]; sa.t = (const double *)ptrs[3];
+        sa.e = (const double *)ptrs[4]; sa.dx = (const double *)ptrs[5];
+        sa.dy = (const double *)ptrs[6]; sa.dz = (const double *)ptrs[7];
+        sa.aval = (const int32_t *)ptrs[8]; sa.uid = (const uint64_t *)ptrs[9];
+        if (r->aval_field) {
+            void *af = base + Ly.afield;
+            GT_CUDA(ctx, cudaMemcpyAsync(af, r->aval_field, sizeof(double) * (size_t)na,
+                                         cudaMemcpyHostToDevice, s));
+            p.aval_field = (const double *)af;
+        }
+    } else {
+        sa.x = r->x; sa.y = r->y; sa.z = r->z; sa.t = r->t; sa.e = r->e;
+        sa.dx = r->dx; sa.dy = r->dy; sa.dz = r->dz; sa.aval = r->aval; sa.uid = r->uid;
+    }
+
+    // outputs and queue flags start from zero
+    if (o->capacity > 0)
+        GT_CUDA(ctx, cudaMemsetAsync(p.ready, 0, sizeof(uint32_t) * (size_t)o->capacity, s));
+    if (na > 0) {
+        GT_CUDA(ctx, cudaMemsetAsync(o->tallies, 0, sizeof(uint64_t) * (size_t)na * (L + 1), s));
+        GT_CUDA(ctx, cudaMemsetAsync(o->electrons, 0, sizeof(uint64_t) * (size_t)na, s));
+        if (r->size_limit)
+            GT_CUDA(ctx, cudaMemsetAsync(p.created, 0, sizeof(unsigned long long) * (size_t)na, s));
+    }
+    GT_CUDA(ctx, launch_seed(p, sa, s));
+    ++launches;
+
+    const bool fp64 = r->precision == GT_FP64;
+    const int block = r->block ? r->block : default_block(r->precision);
+    const size_t smem_tab = shared_bytes(L, ctx->gas.n_nodes, block, true);
+    const bool smem_table = !fp64 && smem_tab <= ctx->smem_optin;
+    const size_t smem = shared_bytes(L, ctx->gas.n_nodes, block, smem_table);
+    if (smem > ctx->smem_optin) return GT_ERR_UNSUPPORTED;
+    int iterations = 0, grid = 0;
+    unsigned host_err = 0;  // aborts decided on the host (plain mode)
+    double transport_ms = 0.0;
+    const int K = p.flights_per_round;
+
+    if (r->mode == GT_BATCHED) {
+        const int occ = fp64 ? occupancy_batched_fp64(ctx->field.kind, block, smem)
+                             : occupancy_batched_mixed(ctx->field.kind, smem_table, block, smem);
+        if (occ < 1) return GT_ERR_UNSUPPORTED;
+        grid = r->grid ? r->grid : ctx->sms * occ;
+        GT_CUDA(ctx, cudaEventRecord(ctx->ev0, s));
+        GT_CUDA(ctx, fp64 ? launch_batched_fp64(p, grid, block, smem, s)
+                          : launch_batched_mixed(p, smem_table, grid, block, smem, s));
+        GT_CUDA(ctx, cudaEventRecord(ctx->ev1, s));
+        ++launches;
+        iterations = 1;
+    } else {
+        // one avalanche at a time: seed, then generations until none is active
+        std::vector<int32_t> av((size_t)np);
+        if (np > 0) {
+            if (r->primaries_on_device) {
+                GT_CUDA(ctx, cudaMemcpyAsync(av.data(), r->aval, sizeof(int32_t) * (size_t)np,
+                                             cudaMemcpyDeviceToHost, s));
+                GT_CUDA(ctx, cudaStreamSynchronize(s));
+            } else {
+                std::memcpy(av.data(), r->aval, sizeof(int32_t) * (size_t)np);
+            }
+        }
+        std::vector<long long> first((size_t)na + 1, 0), order((size_t)np);
+        for (int64_t i = 0; i < np; ++i)
+            if (av[i] >= 0 && av[i] < na) first[av[i] + 1]++;
+        for (int a = 0; a < na; ++a) first[a + 1] += first[a];
+        {
+            std::vector<long long> fill(first.begin(), first.end() - 1);
+            for (int64_t i = 0; i < np; ++i)
+                if (av[i] >= 0 && av[i] < na) order[fill[av[i]]++] = i;
+        }
+        long long *d_order = reinterpret_cast<long long *>(base + Ly.order);
+        if (np > 0)
+            GT_CUDA(ctx, cudaMemcpyAsync(d_order, order.data(), sizeof(long long) * (size_t)np,
+                                         cudaMemcpyHostToDevice, s));
+        char *sp = base + Ly.stacks;
+        Stack st[3] = {carve_stack(sp, o->capacity), carve_stack(sp, o->capacity),
+                       carve_stack(sp, o->capacity)};
+        const auto t_host0 = std::chrono::steady_clock::now();
+        GT_CUDA(ctx, cudaEventRecord(ctx->ev0, s));
+        // invalid device-side primaries are caught before any transport
+        GT_CUDA(ctx, cudaMemcpyAsync(ctx->h_hdr, p.hdr, sizeof(Header), cudaMemcpyDeviceToHost, s));
+        GT_CUDA(ctx, cudaStreamSynchronize(s));
+        bool stop = (ctx->h_hdr->error & ERR_BADARG) != 0;
+        for (int a = 0; a < na && !stop; ++a) {
+            const long long cnt = first[a + 1] - first[a];
+            if (cnt == 0) continue;
+            GT_CUDA(ctx, cudaMemsetAsync(&p.hdr->n_new[0], 0, 4 * sizeof(unsigned long long), s));
+            GT_CUDA(ctx, launch_plain_init(p, st[0], d_order, first[a], cnt, s));
+            ++launches;
+            int cur = 0, parity = 0;
+            long long n_active = cnt;
+            while (n_active > 0) {
+                PlainArgs pa;
+                pa.cur = st[cur];
+                pa.fresh = st[2];
+                pa.next = st[1 - cur];
+                pa.n_active = n_active;
+                pa.parity = parity;
+                pa.aval = a;
+                GT_CUDA(ctx, fp64 ? launch_plain_fp64(p, pa, std::min(block, 128),
+                                                      shared_bytes(L, ctx->gas.n_nodes, std::min(block, 128), false), s)
+                                  : launch_plain_mixed(p, pa, smem_table, std::min(block, 128),
+                                                       shared_bytes(L, ctx->gas.n_nodes, std::min(block, 128), smem_table), s));
+                GT_CUDA(ctx, launch_plain_compact(p, pa, s));
+                launches += 2;
+                GT_CUDA(ctx, cudaMemcpyAsync(ctx->h_hdr, p.hdr, sizeof(Header),
+                                             cudaMemcpyDeviceToHost, s));
+                GT_CUDA(ctx, cudaStreamSynchronize(s));
+                ++iterations;
+                n_active = (long long)ctx->h_hdr->n_next[parity];
+                cur = 1 - cur;
+                parity ^= 1;
+                const double host_ms = std::chrono::duration<double, std::milli>(
+                                           std::chrono::steady_clock::now() - t_host0).count();
+                if ((ctx->h_hdr->error & (ERR_TIMEOUT | ERR_BADARG)) ||
+                    host_ms > (double)p.time_limit_ns * 1e-6) {
+                    if (!(ctx->h_hdr->error & ERR_BADARG)) ctx->h_hdr->error |= ERR_TIMEOUT;
+                    stop = true;
+                    break;
+                }
+            }
+        }
+        GT_CUDA(ctx, cudaEventRecord(ctx->ev1, s));
+        grid = 0;
+        if (stop) host_err = ctx->h_hdr->error & (ERR_TIMEOUT | ERR_BADARG);
+    }
+
+    GT_CUDA(ctx, launch_count_electrons(p, ctx->sms, s));
+    ++launches;
+    GT_CUDA(ctx, cudaMemcpyAsync(ctx->h_hdr, p.hdr, sizeof(Header), cudaMemcpyDeviceToHost, s));
+    GT_CUDA(ctx, cudaStreamSynchronize(s));
+    float ms = 0.f;
+    GT_CUDA(ctx, cudaEventElapsedTime(&ms, ctx->ev0, ctx->ev1));
+    transport_ms = ms;
+    Header &h = *ctx->h_hdr;
+    h.error |= host_err;
+    rc = finish_status(h);
+    if (stats) {
+        stats->n_endpoints = (int64_t)std::min<unsigned long long>(h.tail, (unsigned long long)o->capacity);
+        stats->n_dropped = (int64_t)h.dropped;
+        stats->real_collisions = h.real;
+        stats->null_collisions = h.nul;
+        stats->flights = h.flights;
+        stats->transport_ms = transport_ms;
+        stats->launches = launches;
+        stats->iterations = iterations;
+        stats->status = rc;
+        stats->block = block;
+        stats->flights_per_round = K;
+        stats->grid = grid;
+    }
+    return rc;
+}
+
+int avalanche_observables(gt_ctx *ctx, const gt_endpoints *ep, int64_t n_endpoints,
+                          int32_t n_avalanches, const int32_t *n_prim, int32_t collect_status,
+                          int32_t drift_status, double gap, double *obs, void *stream)
+{
+    if (!ctx || !ep || !obs || n_endpoints < 0 || n_avalanches < 0 || n_endpoints > ep->capacity)
+        return GT_ERR_ARG;
+    if (n_avalanches > 0 && !n_prim) return GT_ERR_ARG;
+    if (n_endpoints > 0 && (!ep->x0 || !ep->y0 || !ep->z0 || !ep->t0 || !ep->x1 || !ep->y1 ||
+                            !ep->z1 || !ep->t1 || !ep->status || !ep->aval))
+        return GT_ERR_ARG;
+    DeviceGuard dg(ctx->device);
+    if (!dg.ok) return GT_ERR_CUDA;
+    cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+    const size_t need_counts = (size_t)std::max(n_avalanches, 1);
+    long long nb = (n_endpoints + 255) / 256;
+    nb = std::max(1LL, std::min<long long>(nb, (long long)ctx->sms * 4));
+    if (ctx->obs_counts_cap < need_counts) {
+        if (ctx->d_obs_counts) cudaFree(ctx->d_obs_counts);
+        ctx->d_obs_counts = nullptr;
+        ctx->obs_counts_cap = 0;
+        GT_CUDA(ctx, cudaMalloc((void **)&ctx->d_obs_counts, sizeof(unsigned long long) * need_counts));
+        ctx->obs_counts_cap = need_counts;
+    }
+    if (ctx->obs_partials_cap < (size_t)nb * 5) {
+        if (ctx->d_obs_partials) cudaFree(ctx->d_obs_partials);
+        ctx->d_obs_partials = nullptr;
+        ctx->obs_partials_cap = 0;
+        GT_CUDA(ctx, cudaMalloc((void **)&ctx->d_obs_partials, sizeof(double) * (size_t)nb * 5));
+        ctx->obs_partials_cap = (size_t)nb * 5;
+    }
+    RunParams p{};
+    p.x0 = ep->x0; p.y0 = ep->y0; p.z0 = ep->z0; p.t0 = ep->t0;
+    p.x1 = ep->x1; p.y1 = ep->y1; p.z1 = ep->z1; p.t1 = ep->t1;
+    p.status = ep->status; p.aval = ep->aval;
+    p.n_avalanches = n_avalanches;
+    GT_CUDA(ctx, launch_observables(p, n_endpoints, n_avalanches, n_prim, collect_status,
+                                    drift_status, gap, ctx->d_obs_counts, ctx->d_obs_partials,
+                                    (int)nb, obs, s));
+    GT_CUDA(ctx, cudaStreamSynchronize(s));
+    return GT_OK;
+}
+
+}  // extern "C"

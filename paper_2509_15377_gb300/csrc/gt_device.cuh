@@ -1,0 +1,750 @@
+// gt_device.cuh -- device-side state and the per-flight step of the
+// microscopic avalanche transport (arXiv:2509.15377, Sec. 2, Fig. 2), for
+// sm_103a.  Two precisions share the structure of the step:
+//   Fp64Electron   every quantity in FP64;
+//   MixedElectron  FP32 kinematics, field, table interpolation and
+//                  scattering; FP64 absolute position and time (FP32 offsets
+//                  since the last flush are folded into FP64 every round),
+//                  and FP64 decisions for the level-threshold and boundary
+//                  tests (an FP32 pre-test with a margin, confirmed in FP64
+//                  only inside the margin, takes the FP64 decision exactly).
+#pragma once
+
+#include <cstdint>
+#include <cuda_runtime.h>
+
+#include "gt_avalanche.h"
+
+namespace gt {
+
+// ---------------------------------------------------------------- units
+// e/m = 1.75882001076e11 C/kg (CODATA 2018): acceleration per V/cm in
+// cm/ns^2 and cyclotron rate per T in rad/ns.
+constexpr double kAccel = 1.75882001076e-3;
+constexpr double kOmega = 175.882001076;
+constexpr double kTwoAccel = 2.0 * kAccel;          // v^2 = kTwoAccel * eps
+constexpr double kInvTwoAccel = 1.0 / kTwoAccel;    // eps = v^2 * kInvTwoAccel
+constexpr double kTwoPi = 6.283185307179586476925;
+constexpr float kAccelF = 1.75882001076e-3f;
+constexpr float kTwoAccelF = (float)(2.0 * 1.75882001076e-3);
+constexpr float kInvTwoAccelF = (float)(1.0 / (2.0 * 1.75882001076e-3));
+constexpr float kTwoPiF = 6.28318530717958647692f;
+
+enum : int { EV_NONE = 0, EV_CHILD = 1, EV_RETIRE = 2 };
+
+// ------------------------------------------------------------ parameters
+struct DevGas {
+    int n_levels, n_nodes;
+    double d_eps, inv_d_eps, nu_max, inv_nu_max, recoil;
+    float inv_d_eps_f, nu_max_f, inv_nu_max_f, recoil_f, last_x_f;
+    const double *cum64;  // [n_nodes][n_levels] running sums over levels
+    const float *cum32;
+    int32_t type[GT_MAX_LEVELS];
+    double thr[GT_MAX_LEVELS];
+};
+
+struct DevField {
+    int kind;
+    int has_b;
+    double e0, gap;
+    double wire_r2, tube_r2, coax_k;   // coax_k = V / ln(b/a)
+    double w[3];                       // magnetic rotation vector -kOmega*B
+    int nx, ny, nz;
+    double origin[3], inv_spacing[3], hi[3];
+    const float4 *grid;
+};
+
+struct Header {  // at the start of the work space, 256 bytes
+    unsigned long long head;      // next queue ticket
+    unsigned long long tail;      // slots reserved (stored or dropped)
+    unsigned long long done;      // electrons finished or dropped
+    unsigned long long dropped;   // secondaries not stored
+    unsigned long long flights, real, nul;
+    unsigned int error;           // ERR_* bits
+    unsigned int pad0;
+    unsigned long long n_new[2];  // plain mode: secondaries of this generation
+    unsigned long long n_next[2]; // plain mode: electrons of next generation
+    unsigned long long t_start;   // %globaltimer at the start of the run
+    unsigned long long pad[19];
+};
+static_assert(sizeof(Header) == 256, "header size");
+
+constexpr unsigned ERR_OVERFLOW = 1u, ERR_TIMEOUT = 2u, ERR_BADARG = 4u;
+
+// Electron state parked between generations (plain mode), SoA.
+struct Stack {
+    double *x, *y, *z, *t, *vx, *vy, *vz;
+    uint32_t *nf, *nreal;
+    uint64_t *uid;
+    int64_t *slot;
+    int32_t *alive;
+};
+
+struct RunParams {
+    DevGas gas;
+    DevField field;
+    // endpoint arrays (caller)
+    double *x0, *y0, *z0, *t0, *e0, *x1, *y1, *z1, *t1, *e1;
+    int32_t *status, *aval;
+    uint64_t *uid;
+    uint32_t *nflight;
+    uint64_t *tallies;    // [n_avalanches][n_levels + 1]
+    uint64_t *electrons;  // [n_avalanches]
+    int64_t capacity;
+    // work space
+    Header *hdr;
+    unsigned int *ready;      // [capacity] queue slot filled
+    double *bvx, *bvy, *bvz;  // [capacity] velocity at birth
+    unsigned long long *created;  // [n_avalanches] (size_limit only)
+    const double *aval_field;     // [n_avalanches] or null
+    // run options
+    uint64_t seed;
+    double t_max;
+    uint32_t coll_limit;
+    int flights_per_round;
+    uint64_t size_limit;
+    long long spin_limit_ns, time_limit_ns;
+    int n_avalanches;
+};
+
+// --------------------------------------------------------- small helpers
+__device__ __forceinline__ unsigned long long globaltimer()
+{
+    unsigned long long t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
+
+__device__ __forceinline__ unsigned int lanemask_lt()
+{
+    unsigned int m;
+    asm("mov.u32 %0, %%lanemask_lt;" : "=r"(m));
+    return m;
+}
+
+__device__ __forceinline__ unsigned int ld_acquire_u32(const unsigned int *p)
+{
+    unsigned int v;
+    asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+    return v;
+}
+
+__device__ __forceinline__ unsigned long long ld_acquire_u64(const unsigned long long *p)
+{
+    unsigned long long v;
+    asm volatile("ld.acquire.gpu.global.u64 %0, [%1];" : "=l"(v) : "l"(p) : "memory");
+    return v;
+}
+
+__device__ __forceinline__ void st_release_u32(unsigned int *p, unsigned int v)
+{
+    asm volatile("st.release.gpu.global.u32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
+}
+
+// ------------------------------------------------------- random numbers
+// Philox4x32-10 (Salmon, Moraes, Dror, Shaw, SC'11): ten rounds of
+// (c0,c1,c2,c3) -> (hi(B*c2)^c1^k0, lo(B*c2), hi(A*c0)^c3^k1, lo(A*c0)),
+// A = 0xD2511F53, B = 0xCD9E8D57, with the key bumped by (0x9E3779B9,
+// 0xBB67AE85) after each round.
+__device__ __forceinline__ uint4 philox10(uint4 c, uint32_t k0, uint32_t k1)
+{
+#pragma unroll
+    for (int r = 0; r < 10; ++r) {
+        const uint32_t lo_a = 0xD2511F53u * c.x, hi_a = __umulhi(0xD2511F53u, c.x);
+        const uint32_t lo_b = 0xCD9E8D57u * c.z, hi_b = __umulhi(0xCD9E8D57u, c.z);
+        c = make_uint4(hi_b ^ c.y ^ k0, lo_b, hi_a ^ c.w ^ k1, lo_a);
+        k0 += 0x9E3779B9u;
+        k1 += 0xBB67AE85u;
+    }
+    return c;
+}
+
+// Stream of electron `uid` in avalanche `aval`: key (seed_lo ^ aval,
+// seed_hi), counter (flight, sub, uid_lo, uid_hi).
+__device__ __forceinline__ uint4 draw(uint64_t seed, int aval, uint64_t uid, uint32_t flight,
+                                      uint32_t sub)
+{
+    return philox10(make_uint4(flight, sub, (uint32_t)uid, (uint32_t)(uid >> 32)),
+                    (uint32_t)seed ^ (uint32_t)aval, (uint32_t)(seed >> 32));
+}
+
+// (w + 1/2) 2^-32 in (0, 1), exact in FP64.
+__device__ __forceinline__ double u01d(uint32_t w) { return ((double)w + 0.5) * 0x1p-32; }
+// (w>>9 + 1/2) 2^-23 in (0, 1), exact in FP32 (24 significant bits).
+__device__ __forceinline__ float u01f(uint32_t w)
+{
+    return ((float)(w >> 9) + 0.5f) * 0x1p-23f;
+}
+
+// SplitMix64 output function (Steele, Lea, Flood, OOPSLA 2014); the id of
+// the electron created in flight `flight` of `parent`.
+__device__ __forceinline__ uint64_t child_uid(uint64_t parent, uint32_t flight)
+{
+    uint64_t z = parent + 0x9E3779B97F4A7C15ull * ((uint64_t)flight + 1ull);
+    z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+    z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+    return z ^ (z >> 31);
+}
+
+// ------------------------------------------------------- shared tables
+// Per-CTA view of the gas constants; the FP32 cumulative table is staged
+// into shared memory when it fits (mixed precision).
+struct Tables {
+    const float *cum32;     // shared or global
+    const double *cum64;    // global (read-only path)
+    const int *type;        // shared [L]
+    const double *thr;      // shared [L]
+    const float *thr_f;     // shared [L]
+    uint32_t *tally;        // shared [L][blockDim]: real collisions per level
+};
+
+// --------------------------------------------------------------- fields
+template <int FK>
+__device__ __forceinline__ void field64(const DevField &f, double plate_e, double x, double y,
+                                        double z, double &ex, double &ey, double &ez)
+{
+    if (FK == GT_FIELD_UNIFORM) {
+        ex = 0.0; ey = 0.0; ez = -f.e0;
+    } else if (FK == GT_FIELD_PLATE) {
+        ex = 0.0; ey = 0.0; ez = -plate_e;
+    } else if (FK == GT_FIELD_COAX) {
+        const double s = f.coax_k / (x * x + y * y);
+        ex = s * x; ey = s * y; ez = 0.0;
+    } else {
+        const double p[3] = {x, y, z};
+        const int n[3] = {f.nx, f.ny, f.nz};
+        int i[3];
+        double w[3];
+#pragma unroll
+        for (int d = 0; d < 3; ++d) {
+            const double g = (p[d] - f.origin[d]) * f.inv_spacing[d];
+            int k = (int)floor(g);
+            k = k < 0 ? 0 : (k > n[d] - 2 ? n[d] - 2 : k);
+            i[d] = k;
+            w[d] = g - k;
+        }
+        ex = ey = ez = 0.0;
+#pragma unroll
+        for (int c = 0; c < 8; ++c) {
+            const int di = c & 1, dj = (c >> 1) & 1, dk = (c >> 2) & 1;
+            const double wt = (di ? w[0] : 1.0 - w[0]) * (dj ? w[1] : 1.0 - w[1]) *
+                              (dk ? w[2] : 1.0 - w[2]);
+            const float4 e = __ldg(f.grid + (((int64_t)(i[2] + dk) * f.ny + (i[1] + dj)) * f.nx +
+                                             (i[0] + di)));
+            ex += wt * (double)e.x; ey += wt * (double)e.y; ez += wt * (double)e.z;
+        }
+    }
+}
+
+template <int FK>
+__device__ __forceinline__ void field32(const DevField &f, float plate_e, float x, float y, float z,
+                                        float &ex, float &ey, float &ez)
+{
+    if (FK == GT_FIELD_UNIFORM) {
+        ex = 0.f; ey = 0.f; ez = -(float)f.e0;
+    } else if (FK == GT_FIELD_PLATE) {
+        ex = 0.f; ey = 0.f; ez = -plate_e;
+    } else if (FK == GT_FIELD_COAX) {
+        const float s = (float)f.coax_k / (x * x + y * y);
+        ex = s * x; ey = s * y; ez = 0.f;
+    } else {
+        const float gx = (x - (float)f.origin[0]) * (float)f.inv_spacing[0];
+        const float gy = (y - (float)f.origin[1]) * (float)f.inv_spacing[1];
+        const float gz = (z - (float)f.origin[2]) * (float)f.inv_spacing[2];
+        int ix = min(max((int)floorf(gx), 0), f.nx - 2);
+        int iy = min(max((int)floorf(gy), 0), f.ny - 2);
+        int iz = min(max((int)floorf(gz), 0), f.nz - 2);
+        const float wx = gx - ix, wy = gy - iy, wz = gz - iz;
+        const float4 *b = f.grid + (((int64_t)iz * f.ny + iy) * f.nx + ix);
+        const int64_t sy = f.nx, sz = (int64_t)f.nx * f.ny;
+        const float4 c000 = __ldg(b), c100 = __ldg(b + 1);
+        const float4 c010 = __ldg(b + sy), c110 = __ldg(b + sy + 1);
+        const float4 c001 = __ldg(b + sz), c101 = __ldg(b + sz + 1);
+        const float4 c011 = __ldg(b + sz + sy), c111 = __ldg(b + sz + sy + 1);
+        // interpolate along x, then y, then z
+        auto lerp = [](float a, float b, float t) { return fmaf(t, b - a, a); };
+        float e[3];
+        const float *p000 = &c000.x, *p100 = &c100.x, *p010 = &c010.x, *p110 = &c110.x;
+        const float *p001 = &c001.x, *p101 = &c101.x, *p011 = &c011.x, *p111 = &c111.x;
+#pragma unroll
+        for (int d = 0; d < 3; ++d) {
+            const float a00 = lerp(p000[d], p100[d], wx), a10 = lerp(p010[d], p110[d], wx);
+            const float a01 = lerp(p001[d], p101[d], wx), a11 = lerp(p011[d], p111[d], wx);
+            e[d] = lerp(lerp(a00, a10, wy), lerp(a01, a11, wy), wz);
+        }
+        ex = e[0]; ey = e[1]; ez = e[2];
+    }
+}
+
+// Boundary status of an FP64 position (0 inside).
+template <int FK>
+__device__ __forceinline__ int boundary64(const DevField &f, double x, double y, double z)
+{
+    if (FK == GT_FIELD_PLATE) {
+        if (z >= f.gap) return GT_ST_ANODE;
+        if (z < 0.0) return GT_ST_CATHODE;
+    } else if (FK == GT_FIELD_COAX) {
+        const double r2 = x * x + y * y;
+        if (r2 <= f.wire_r2) return GT_ST_WIRE;
+        if (r2 >= f.tube_r2) return GT_ST_TUBE;
+    } else if (FK == GT_FIELD_GRID) {
+        const double r2 = x * x + y * y;
+        if (f.wire_r2 > 0.0 && r2 <= f.wire_r2) return GT_ST_WIRE;
+        if (x < f.origin[0] || x > f.hi[0] || y < f.origin[1] || y > f.hi[1] ||
+            z < f.origin[2] || z > f.hi[2])
+            return GT_ST_OUT_OF_MAP;
+    }
+    return 0;
+}
+
+// ---------------------------------------------------- flight kinematics
+// Exact motion over dt with constant acceleration a and magnetic rotation
+// vector w (dv/dt = a + v x w): the component along w-hat accelerates
+// uniformly; across it the drift (a x w)/|w|^2 plus a rotation by -|w| dt.
+template <typename R>
+__device__ __forceinline__ void lorentz_step(const R w[3], R ax, R ay, R az, R dt, R &vx, R &vy,
+                                             R &vz, R &dx, R &dy, R &dz)
+{
+    const R wn2 = w[0] * w[0] + w[1] * w[1] + w[2] * w[2];
+    const R wn = sqrt(wn2);
+    const R bx = w[0] / wn, by = w[1] / wn, bz = w[2] / wn;
+    const R vpar = vx * bx + vy * by + vz * bz;
+    const R apar = ax * bx + ay * by + az * bz;
+    const R gx = (ay * w[2] - az * w[1]) / wn2;  // (a x w)/|w|^2
+    const R gy = (az * w[0] - ax * w[2]) / wn2;
+    const R gz = (ax * w[1] - ay * w[0]) / wn2;
+    const R ux = vx - vpar * bx - gx, uy = vy - vpar * by - gy, uz = vz - vpar * bz - gz;
+    const R cx = by * uz - bz * uy, cy = bz * ux - bx * uz, cz = bx * uy - by * ux;  // b x u
+    R s, c;
+    sincos(wn * dt, &s, &c);
+    const R sw = s / wn;
+    const R cw = (R)(1) - c;
+    const R cwn = cw / wn;
+    const R par = vpar * dt + (R)(0.5) * apar * dt * dt;
+    dx = par * bx + gx * dt + ux * sw - cx * cwn;
+    dy = par * by + gy * dt + uy * sw - cy * cwn;
+    dz = par * bz + gz * dt + uz * sw - cz * cwn;
+    const R vp = vpar + apar * dt;
+    vx = vp * bx + gx + ux * c - cx * s;
+    vy = vp * by + gy + uy * c - cy * s;
+    vz = vp * bz + gz + uz * c - cz * s;
+}
+
+// Cumulative-rate selection at energy eps for R = u1 * nu_max: the level j
+// with cum_{j-1}(eps) <= R < cum_j(eps), or -1 for a null collision.
+template <typename R, typename T>
+__device__ __forceinline__ int select_level(const T *cum, int L, int N, R inv_d_eps, R eps, R Rv)
+{
+    R xk = eps * inv_d_eps;
+    const R last = (R)(N - 1);
+    if (xk > last) xk = last;
+    int k = (int)xk;
+    if (k > N - 2) k = N - 2;
+    const R f = xk - (R)k;
+    const T *c0 = cum + (int64_t)k * L;
+    const T *c1 = c0 + L;
+    const R top = (R)c0[L - 1] + f * ((R)c1[L - 1] - (R)c0[L - 1]);
+    if (!(Rv < top)) return -1;
+    int lvl = 0;
+    for (int j = 0; j < L - 1; ++j) {
+        const R cj = (R)c0[j] + f * ((R)c1[j] - (R)c0[j]);
+        lvl += (cj <= Rv) ? 1 : 0;
+    }
+    return lvl;
+}
+
+// Isotropic unit vector from two uniforms: cos(theta) = 1 - 2 u, phi = 2 pi v.
+__device__ __forceinline__ void isotropic64(double u, double v, double &nx, double &ny,
+                                            double &nz)
+{
+    const double ct = 1.0 - 2.0 * u;
+    const double st2 = 1.0 - ct * ct;
+    const double st = st2 > 0.0 ? sqrt(st2) : 0.0;
+    double s, c;
+    sincos(kTwoPi * v, &s, &c);
+    nx = st * c; ny = st * s; nz = ct;
+}
+
+__device__ __forceinline__ void isotropic32(float u, float v, float &nx, float &ny, float &nz)
+{
+    const float ct = 1.0f - 2.0f * u;
+    const float st = sqrtf(fmaxf(1.0f - ct * ct, 0.0f));
+    float s, c;
+    __sincosf(kTwoPiF * v, &s, &c);
+    nx = st * c; ny = st * s; nz = ct;
+}
+
+// New electron produced by an ionising collision.
+struct Child {
+    double x, y, z, t, e, vx, vy, vz;
+    uint64_t uid;
+};
+
+// ============================================================ FP64 electron
+struct Fp64Electron {
+    double x, y, z, t, vx, vy, vz;
+    double plate_e;
+    uint32_t nf, nreal, nnull;
+    int status;
+    int aval;
+    uint64_t uid;
+    int64_t slot;
+
+    template <int FK>
+    __device__ void load_birth(const RunParams &p, int64_t s)
+    {
+        slot = s;
+        x = p.x0[s]; y = p.y0[s]; z = p.z0[s]; t = p.t0[s];
+        vx = p.bvx[s]; vy = p.bvy[s]; vz = p.bvz[s];
+        uid = p.uid[s];
+        aval = p.aval[s];
+        plate_e = p.aval_field ? p.aval_field[aval] : p.field.e0;
+        nf = nreal = nnull = 0;
+        status = 0;
+    }
+
+    template <int FK>
+    __device__ __forceinline__ int check_start(const RunParams &p)
+    {
+        status = boundary64<FK>(p.field, x, y, z);
+        return status ? EV_RETIRE : EV_NONE;
+    }
+
+    template <int FK>
+    __device__ __forceinline__ int fly(const RunParams &p, const Tables &tb, Child &ch)
+    {
+        if (nf == 0xFFFFFFFFu) {
+            status = GT_ST_FLIGHT_LIMIT;
+            return EV_RETIRE;
+        }
+        const uint32_t flight = nf;
+        const uint4 w = draw(p.seed, aval, uid, flight, 0u);
+        double ex, ey, ez;
+        field64<FK>(p.field, plate_e, x, y, z, ex, ey, ez);
+        const double ax = -kAccel * ex, ay = -kAccel * ey, az = -kAccel * ez;
+        double dt = -log(u01d(w.x)) * p.gas.inv_nu_max;
+        bool timed = false;
+        if (p.t_max > 0.0 && t + dt > p.t_max) {
+            dt = p.t_max - t;
+            timed = true;
+        }
+        if (!p.field.has_b) {
+            x = x + vx * dt + 0.5 * ax * dt * dt;
+            y = y + vy * dt + 0.5 * ay * dt * dt;
+            z = z + vz * dt + 0.5 * az * dt * dt;
+            vx += ax * dt; vy += ay * dt; vz += az * dt;
+        } else {
+            double dx, dy, dz;
+            lorentz_step<double>(p.field.w, ax, ay, az, dt, vx, vy, vz, dx, dy, dz);
+            x += dx; y += dy; z += dz;
+        }
+        t = timed ? p.t_max : t + dt;
+        nf = flight + 1u;
+        const int st = boundary64<FK>(p.field, x, y, z);
+        if (st) {
+            status = st;
+            return EV_RETIRE;
+        }
+        if (timed) {
+            status = GT_ST_TIME;
+            return EV_RETIRE;
+        }
+        const double eps = (vx * vx + vy * vy + vz * vz) * kInvTwoAccel;
+        int lvl = select_level<double, double>(tb.cum64, p.gas.n_levels, p.gas.n_nodes,
+                                                p.gas.inv_d_eps, eps, u01d(w.y) * p.gas.nu_max);
+        if (lvl >= 0 && tb.type[lvl] != GT_LEVEL_ELASTIC && eps < tb.thr[lvl]) lvl = -1;
+        if (lvl < 0) {
+            ++nnull;
+            return EV_NONE;
+        }
+        tb.tally[lvl * blockDim.x + threadIdx.x] += 1u;
+        double nx, ny, nz;
+        isotropic64(u01d(w.z), u01d(w.w), nx, ny, nz);
+        double eps_new;
+        int ev = EV_NONE;
+        const int type = tb.type[lvl];
+        if (type == GT_LEVEL_ELASTIC) {
+            const double sp = sqrt(vx * vx + vy * vy + vz * vz);
+            const double cchi = sp > 0.0 ? (vx * nx + vy * ny + vz * nz) / sp : 0.0;
+            eps_new = eps * (1.0 - p.gas.recoil * (1.0 - cchi));
+        } else {
+            eps_new = eps - tb.thr[lvl];
+            if (type == GT_LEVEL_IONISATION) {
+                const uint4 w2 = draw(p.seed, aval, uid, flight, 1u);
+                const double es = u01d(w2.x) * eps_new;
+                eps_new = eps_new - es;
+                double sx, sy, sz;
+                isotropic64(u01d(w2.y), u01d(w2.z), sx, sy, sz);
+                const double ss = sqrt(kTwoAccel * es);
+                ch.x = x; ch.y = y; ch.z = z; ch.t = t; ch.e = es;
+                ch.vx = ss * sx; ch.vy = ss * sy; ch.vz = ss * sz;
+                ch.uid = child_uid(uid, flight);
+                ev = EV_CHILD;
+            }
+        }
+        const double sp = sqrt(kTwoAccel * eps_new);
+        vx = sp * nx; vy = sp * ny; vz = sp * nz;
+        ++nreal;
+        if (p.coll_limit && nreal >= p.coll_limit) {
+            status = GT_ST_COLL_LIMIT;
+            return ev == EV_CHILD ? (EV_CHILD | EV_RETIRE) : EV_RETIRE;
+        }
+        return ev;
+    }
+
+    template <int FK>
+    __device__ __forceinline__ void round_end(const RunParams &) {}
+
+    __device__ void write_end(const RunParams &p) const
+    {
+        p.x1[slot] = x; p.y1[slot] = y; p.z1[slot] = z; p.t1[slot] = t;
+        p.e1[slot] = (vx * vx + vy * vy + vz * vz) * kInvTwoAccel;
+        p.status[slot] = status;
+        p.nflight[slot] = nf;
+    }
+
+    template <int FK>
+    __device__ void save(const RunParams &, const Stack &s, int64_t i)
+    {
+        s.x[i] = x; s.y[i] = y; s.z[i] = z; s.t[i] = t;
+        s.vx[i] = vx; s.vy[i] = vy; s.vz[i] = vz;
+        s.nf[i] = nf; s.nreal[i] = nreal; s.uid[i] = uid; s.slot[i] = slot;
+    }
+
+    template <int FK>
+    __device__ void restore(const RunParams &p, const Stack &s, int64_t i, int av)
+    {
+        x = s.x[i]; y = s.y[i]; z = s.z[i]; t = s.t[i];
+        vx = s.vx[i]; vy = s.vy[i]; vz = s.vz[i];
+        nf = s.nf[i]; nreal = s.nreal[i]; uid = s.uid[i]; slot = s.slot[i];
+        aval = av;
+        plate_e = p.aval_field ? p.aval_field[aval] : p.field.e0;
+        nnull = 0;
+        status = 0;
+    }
+};
+
+// ===================================================== mixed-precision electron
+struct MixedElectron {
+    double X, Y, Z, T;       // FP64 absolute position and time at the last flush
+    float ox, oy, oz, ot;    // FP32 offsets since the last flush
+    float vx, vy, vz;        // FP32 velocity
+    float px, py, pz;        // FP32 copy of (X, Y, Z) for field and pre-tests
+    float zhi, zlo, tlim;    // pre-test limits for the offsets (see flush)
+    float plate_e;
+    uint32_t nf, nreal, nnull;
+    int status;
+    int aval;
+    bool timed;
+    uint64_t uid;
+    int64_t slot;
+
+    // Fold the FP32 offsets into the FP64 state and refresh the FP32
+    // pre-test limits: an offset beyond a limit is re-tested in FP64.
+    template <int FK>
+    __device__ __forceinline__ void flush(const RunParams &p)
+    {
+        X += (double)ox; Y += (double)oy; Z += (double)oz; T += (double)ot;
+        ox = oy = oz = ot = 0.f;
+        px = (float)X; py = (float)Y; pz = (float)Z;
+        if (FK == GT_FIELD_PLATE) {
+            const float hi = (float)(p.field.gap - Z), lo = (float)(-Z);
+            zhi = hi - (fabsf(hi) * 1e-6f + 1e-12f);
+            zlo = lo + (fabsf(lo) * 1e-6f + 1e-12f);
+        }
+        if (p.t_max > 0.0) {
+            const float g = (float)(p.t_max - T);
+            tlim = g - (fabsf(g) * 1e-6f + 1e-12f);
+        } else {
+            tlim = 3.0e38f;
+        }
+    }
+
+    template <int FK>
+    __device__ void load_birth(const RunParams &p, int64_t s)
+    {
+        slot = s;
+        X = p.x0[s]; Y = p.y0[s]; Z = p.z0[s]; T = p.t0[s];
+        vx = (float)p.bvx[s]; vy = (float)p.bvy[s]; vz = (float)p.bvz[s];
+        uid = p.uid[s];
+        aval = p.aval[s];
+        plate_e = (float)(p.aval_field ? p.aval_field[aval] : p.field.e0);
+        nf = nreal = nnull = 0;
+        status = 0;
+        timed = false;
+        ox = oy = oz = ot = 0.f;
+        flush<FK>(p);
+    }
+
+    template <int FK>
+    __device__ __forceinline__ int check_start(const RunParams &p)
+    {
+        status = boundary64<FK>(p.field, X, Y, Z);
+        return status ? EV_RETIRE : EV_NONE;
+    }
+
+    // FP32 pre-test with a margin, then the FP64 boundary test of X + ox.
+    template <int FK>
+    __device__ __forceinline__ int boundary(const RunParams &p) const
+    {
+        bool maybe;
+        if (FK == GT_FIELD_UNIFORM) {
+            return 0;
+        } else if (FK == GT_FIELD_PLATE) {
+            maybe = (oz >= zhi) || (oz < zlo);
+        } else {
+            const float rx = px + ox, ry = py + oy;
+            const float r2 = rx * rx + ry * ry;
+            maybe = (r2 <= (float)p.field.wire_r2 * 1.00001f);
+            if (FK == GT_FIELD_COAX) {
+                maybe |= (r2 >= (float)p.field.tube_r2 * 0.99999f);
+            } else {
+                const float rz = pz + oz;
+                const float mx = 1e-5f * (float)(p.field.hi[0] - p.field.origin[0]);
+                const float my = 1e-5f * (float)(p.field.hi[1] - p.field.origin[1]);
+                const float mz = 1e-5f * (float)(p.field.hi[2] - p.field.origin[2]);
+                maybe |= (rx < (float)p.field.origin[0] + mx) || (rx > (float)p.field.hi[0] - mx) ||
+                         (ry < (float)p.field.origin[1] + my) || (ry > (float)p.field.hi[1] - my) ||
+                         (rz < (float)p.field.origin[2] + mz) || (rz > (float)p.field.hi[2] - mz);
+            }
+        }
+        if (!maybe) return 0;
+        return boundary64<FK>(p.field, X + (double)ox, Y + (double)oy, Z + (double)oz);
+    }
+
+    template <int FK>
+    __device__ __forceinline__ int fly(const RunParams &p, const Tables &tb, Child &ch)
+    {
+        if (nf == 0xFFFFFFFFu) {
+            status = GT_ST_FLIGHT_LIMIT;
+            return EV_RETIRE;
+        }
+        const uint32_t flight = nf;
+        const uint4 w = draw(p.seed, aval, uid, flight, 0u);
+        float dt = -__logf(u01f(w.x)) * p.gas.inv_nu_max_f;
+        if (ot + dt >= tlim) {  // near the time limit: decide in FP64
+            if (T + (double)(ot + dt) > p.t_max) {
+                dt = fmaxf((float)((p.t_max - T) - (double)ot), 0.0f);
+                timed = true;
+            }
+        }
+        float ex, ey, ez;
+        field32<FK>(p.field, plate_e, px + ox, py + oy, pz + oz, ex, ey, ez);
+        const float ax = -kAccelF * ex, ay = -kAccelF * ey, az = -kAccelF * ez;
+        float dx, dy, dz;
+        if (!p.field.has_b) {
+            const float h = 0.5f * dt;
+            dx = dt * fmaf(h, ax, vx);
+            dy = dt * fmaf(h, ay, vy);
+            dz = dt * fmaf(h, az, vz);
+            vx = fmaf(ax, dt, vx); vy = fmaf(ay, dt, vy); vz = fmaf(az, dt, vz);
+        } else {
+            const float wf[3] = {(float)p.field.w[0], (float)p.field.w[1], (float)p.field.w[2]};
+            lorentz_step<float>(wf, ax, ay, az, dt, vx, vy, vz, dx, dy, dz);
+        }
+        ox += dx; oy += dy; oz += dz; ot += dt;
+        nf = flight + 1u;
+        const int st = boundary<FK>(p);
+        if (st) {
+            status = st;
+            return EV_RETIRE;
+        }
+        if (timed) {
+            status = GT_ST_TIME;
+            return EV_RETIRE;
+        }
+        const float eps = (vx * vx + vy * vy + vz * vz) * kInvTwoAccelF;
+        int lvl = select_level<float, float>(tb.cum32, p.gas.n_levels, p.gas.n_nodes,
+                                             p.gas.inv_d_eps_f, eps, u01f(w.y) * p.gas.nu_max_f);
+        if (lvl >= 0 && tb.type[lvl] != GT_LEVEL_ELASTIC) {
+            const float th = tb.thr_f[lvl];
+            if (eps < th * (1.0f - 1e-6f)) {
+                lvl = -1;
+            } else if (eps < th * (1.0f + 1e-6f)) {  // within the margin: FP64 test
+                const double e64 = ((double)vx * vx + (double)vy * vy + (double)vz * vz) *
+                                   kInvTwoAccel;
+                if (e64 < tb.thr[lvl]) lvl = -1;
+            }
+        }
+        if (lvl < 0) {
+            ++nnull;
+            return EV_NONE;
+        }
+        tb.tally[lvl * blockDim.x + threadIdx.x] += 1u;
+        float nx, ny, nz;
+        isotropic32(u01f(w.z), u01f(w.w), nx, ny, nz);
+        float eps_new;
+        int ev = EV_NONE;
+        const int type = tb.type[lvl];
+        if (type == GT_LEVEL_ELASTIC) {
+            const float v2 = vx * vx + vy * vy + vz * vz;
+            const float cchi = v2 > 0.f ? (vx * nx + vy * ny + vz * nz) * rsqrtf(v2) : 0.f;
+            eps_new = eps * (1.0f - p.gas.recoil_f * (1.0f - cchi));
+        } else {
+            eps_new = fmaxf(eps - tb.thr_f[lvl], 0.0f);
+            if (type == GT_LEVEL_IONISATION) {
+                const uint4 w2 = draw(p.seed, aval, uid, flight, 1u);
+                const float es = u01f(w2.x) * eps_new;
+                eps_new = eps_new - es;
+                float sx, sy, sz;
+                isotropic32(u01f(w2.y), u01f(w2.z), sx, sy, sz);
+                const float ss = sqrtf(kTwoAccelF * es);
+                ch.x = X + (double)ox; ch.y = Y + (double)oy; ch.z = Z + (double)oz;
+                ch.t = T + (double)ot;
+                ch.e = (double)es;
+                ch.vx = (double)(ss * sx); ch.vy = (double)(ss * sy); ch.vz = (double)(ss * sz);
+                ch.uid = child_uid(uid, flight);
+                ev = EV_CHILD;
+            }
+        }
+        const float sp = sqrtf(kTwoAccelF * eps_new);
+        vx = sp * nx; vy = sp * ny; vz = sp * nz;
+        ++nreal;
+        if (p.coll_limit && nreal >= p.coll_limit) {
+            status = GT_ST_COLL_LIMIT;
+            return ev == EV_CHILD ? (EV_CHILD | EV_RETIRE) : EV_RETIRE;
+        }
+        return ev;
+    }
+
+    template <int FK>
+    __device__ __forceinline__ void round_end(const RunParams &p)
+    {
+        flush<FK>(p);
+    }
+
+    __device__ void write_end(const RunParams &p) const
+    {
+        p.x1[slot] = X + (double)ox; p.y1[slot] = Y + (double)oy; p.z1[slot] = Z + (double)oz;
+        p.t1[slot] = timed ? p.t_max : T + (double)ot;
+        p.e1[slot] = ((double)vx * vx + (double)vy * vy + (double)vz * vz) * kInvTwoAccel;
+        p.status[slot] = status;
+        p.nflight[slot] = nf;
+    }
+
+    template <int FK>
+    __device__ void save(const RunParams &p, const Stack &s, int64_t i)
+    {
+        flush<FK>(p);
+        s.x[i] = X; s.y[i] = Y; s.z[i] = Z; s.t[i] = T;
+        s.vx[i] = vx; s.vy[i] = vy; s.vz[i] = vz;
+        s.nf[i] = nf; s.nreal[i] = nreal; s.uid[i] = uid; s.slot[i] = slot;
+    }
+
+    template <int FK>
+    __device__ void restore(const RunParams &p, const Stack &s, int64_t i, int av)
+    {
+        X = s.x[i]; Y = s.y[i]; Z = s.z[i]; T = s.t[i];
+        vx = (float)s.vx[i]; vy = (float)s.vy[i]; vz = (float)s.vz[i];
+        nf = s.nf[i]; nreal = s.nreal[i]; uid = s.uid[i]; slot = s.slot[i];
+        aval = av;
+        plate_e = (float)(p.aval_field ? p.aval_field[aval] : p.field.e0);
+        nnull = 0;
+        status = 0;
+        timed = false;
+        ox = oy = oz = ot = 0.f;
+        flush<FK>(p);
+    }
+};
+
+}  // namespace gt

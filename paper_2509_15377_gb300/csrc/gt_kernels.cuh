@@ -1,0 +1,333 @@
+// gt_kernels.cuh -- transport kernels (templates), instantiated per precision
+// in gt_kernels_fp64.cu and gt_kernels_mixed.cu.
+//
+//   k_batched          one persistent launch for every avalanche: each lane
+//                      holds one electron for a round of K flights; lanes
+//                      without an electron take tickets on a global queue
+//                      (warp ballot + prefix sum, one atomic per warp);
+//                      ionisation appends the new electron to the queue the
+//                      same way; the launch ends when every queued electron
+//                      has finished (done == tail), or on a bounded wait.
+//   k_plain_transport  one generation of one avalanche: every active electron
+//                      flies until it ionises or finishes (Fig. 2 "electron
+//                      transport"); a separate compaction launch then removes
+//                      finished electrons and appends the new ones ("stack
+//                      processing"), and the host loops until none is left.
+#pragma once
+
+#include "gt_device.cuh"
+
+namespace gt {
+
+constexpr unsigned FULL = 0xFFFFFFFFu;
+
+// Dynamic shared memory: per-level constants, the per-thread collision
+// tallies [L][blockDim] and (optionally) the FP32 cumulative table.
+__host__ __device__ inline size_t shared_bytes(int n_levels, int n_nodes, int block, bool table)
+{
+    size_t b = GT_MAX_LEVELS * (sizeof(double) + sizeof(float) + sizeof(int));
+    b += (size_t)n_levels * block * sizeof(uint32_t);
+    b = (b + 15) & ~(size_t)15;
+    if (table) b += (size_t)n_levels * n_nodes * sizeof(float);
+    return b;
+}
+
+template <bool SMEM_TABLE>
+__device__ __forceinline__ Tables stage_tables(const RunParams &p, unsigned char *smem)
+{
+    const int L = p.gas.n_levels;
+    double *s_thr = reinterpret_cast<double *>(smem);
+    float *s_thr_f = reinterpret_cast<float *>(s_thr + GT_MAX_LEVELS);
+    int *s_type = reinterpret_cast<int *>(s_thr_f + GT_MAX_LEVELS);
+    uint32_t *s_tally = reinterpret_cast<uint32_t *>(s_type + GT_MAX_LEVELS);
+    size_t off = GT_MAX_LEVELS * (sizeof(double) + sizeof(float) + sizeof(int)) +
+                 (size_t)L * blockDim.x * sizeof(uint32_t);
+    off = (off + 15) & ~(size_t)15;
+    float *s_cum = reinterpret_cast<float *>(smem + off);
+    for (int i = threadIdx.x; i < L; i += blockDim.x) {
+        s_thr[i] = p.gas.thr[i];
+        s_thr_f[i] = (float)p.gas.thr[i];
+        s_type[i] = p.gas.type[i];
+    }
+    for (int i = threadIdx.x; i < L * (int)blockDim.x; i += blockDim.x) s_tally[i] = 0u;
+    if (SMEM_TABLE) {
+        const int n = p.gas.n_levels * p.gas.n_nodes;
+        for (int i = threadIdx.x; i < n; i += blockDim.x) s_cum[i] = p.gas.cum32[i];
+    }
+    __syncthreads();
+    Tables tb;
+    tb.cum32 = SMEM_TABLE ? s_cum : p.gas.cum32;
+    tb.cum64 = p.gas.cum64;
+    tb.type = s_type;
+    tb.thr = s_thr;
+    tb.thr_f = s_thr_f;
+    tb.tally = s_tally;
+    return tb;
+}
+
+// Per-lane run statistics, reduced per warp at the end.
+struct LaneStats {
+    unsigned long long flights = 0, real = 0, nul = 0;
+};
+
+// An electron has finished: write its endpoint, move its per-level
+// collision counts from shared memory to the avalanche's tallies.
+template <class E>
+__device__ __forceinline__ void finish(const RunParams &p, const Tables &tb, const E &e,
+                                       LaneStats &ls)
+{
+    e.write_end(p);
+    const int L = p.gas.n_levels;
+    uint64_t *tal = p.tallies + (int64_t)e.aval * (L + 1);
+    unsigned long long real = 0;
+    for (int j = 0; j < L; ++j) {
+        uint32_t &c = tb.tally[j * blockDim.x + threadIdx.x];
+        if (c) {
+            atomicAdd(reinterpret_cast<unsigned long long *>(tal + j), (unsigned long long)c);
+            real += c;
+            c = 0u;
+        }
+    }
+    if (e.nnull) atomicAdd(reinterpret_cast<unsigned long long *>(tal + L),
+                           (unsigned long long)e.nnull);
+    ls.flights += e.nf;
+    ls.real += real;
+    ls.nul += e.nnull;
+}
+
+// Write the birth record of a new electron into queue slot s.
+__device__ __forceinline__ void store_birth(const RunParams &p, int64_t s, const Child &c, int aval)
+{
+    p.x0[s] = c.x; p.y0[s] = c.y; p.z0[s] = c.z; p.t0[s] = c.t; p.e0[s] = c.e;
+    p.bvx[s] = c.vx; p.bvy[s] = c.vy; p.bvz[s] = c.vz;
+    p.uid[s] = c.uid;
+    p.aval[s] = aval;
+    p.status[s] = 0;
+}
+
+// Warp-collective append of the lanes' new electrons to the queue: ballot,
+// one atomic on the tail per warp, each lane's slot = base + its rank.
+// Returns the number of this lane's electrons dropped for lack of capacity
+// (they count as finished so that the queue can drain).
+__device__ __forceinline__ int push_children(const RunParams &p, bool want, const Child &ch,
+                                             int aval, int lane)
+{
+    bool ok = want;
+    if (want && p.size_limit) {
+        const unsigned long long old = atomicAdd(p.created + aval, 1ull);
+        if (old >= p.size_limit) {
+            ok = false;
+            atomicAdd(&p.hdr->dropped, 1ull);
+        }
+    }
+    const unsigned m = __ballot_sync(FULL, ok);
+    if (!m) return 0;
+    const int leader = __ffs(m) - 1;
+    unsigned long long base = 0;
+    if (lane == leader) base = atomicAdd(&p.hdr->tail, (unsigned long long)__popc(m));
+    base = __shfl_sync(FULL, base, leader);
+    if (!ok) return 0;
+    const unsigned long long s = base + __popc(m & lanemask_lt());
+    if (s >= (unsigned long long)p.capacity) {
+        atomicAdd(&p.hdr->dropped, 1ull);
+        atomicOr(&p.hdr->error, ERR_OVERFLOW);
+        return 1;
+    }
+    store_birth(p, (int64_t)s, ch, aval);
+    __threadfence();
+    st_release_u32(p.ready + s, 1u);
+    return 0;
+}
+
+template <class E, int FK, bool SMEM_TABLE, int MAXT>
+__global__ void __launch_bounds__(MAXT) k_batched(const RunParams p)
+{
+    extern __shared__ __align__(16) unsigned char smem[];
+    const Tables tb = stage_tables<SMEM_TABLE>(p, smem);
+    const int lane = threadIdx.x & 31;
+    const int K = p.flights_per_round;
+    const unsigned long long t_start = *reinterpret_cast<volatile unsigned long long *>(&p.hdr->t_start);
+
+    E e;
+    bool has = false;
+    long long ticket = -1;
+    LaneStats ls;
+    Child ch;
+    unsigned long long last_done = ~0ull, last_tail = ~0ull, t_progress = t_start;
+    unsigned sleep_ns = 64;
+
+    for (;;) {
+        // a run-wide abort (time budget or a wait that gave up)
+        unsigned err = 0;
+        if (lane == 0) err = *reinterpret_cast<volatile unsigned *>(&p.hdr->error);
+        if (__shfl_sync(FULL, err, 0) & (ERR_TIMEOUT | ERR_BADARG)) break;
+
+        // lanes without an electron take queue tickets: one atomic per warp
+        const bool need = !has && ticket < 0;
+        const unsigned m = __ballot_sync(FULL, need);
+        if (m) {
+            const int leader = __ffs(m) - 1;
+            unsigned long long base = 0;
+            if (lane == leader) base = atomicAdd(&p.hdr->head, (unsigned long long)__popc(m));
+            base = __shfl_sync(FULL, base, leader);
+            if (need) ticket = (long long)(base + __popc(m & lanemask_lt()));
+        }
+        int retired = 0;
+        if (!has && ticket >= 0 && ticket < p.capacity) {
+            if (ld_acquire_u32(p.ready + ticket)) {
+                e.template load_birth<FK>(p, ticket);
+                ticket = -1;
+                has = true;
+                if (e.template check_start<FK>(p) & EV_RETIRE) {
+                    finish(p, tb, e, ls);
+                    has = false;
+                    retired = 1;
+                }
+            }
+        }
+
+        if (!__any_sync(FULL, has)) {
+            // the whole warp waits: finished when every queued electron is done
+            unsigned long long d = 0, tl = 0;
+            if (lane == 0) {
+                d = ld_acquire_u64(&p.hdr->done);
+                tl = ld_acquire_u64(&p.hdr->tail);
+            }
+            d = __shfl_sync(FULL, d, 0);
+            tl = __shfl_sync(FULL, tl, 0);
+            const int r = __reduce_add_sync(FULL, retired);
+            if (r) {
+                __threadfence();
+                if (lane == 0) atomicAdd(&p.hdr->done, (unsigned long long)r);
+                continue;
+            }
+            if (d == tl) break;
+            const unsigned long long now = globaltimer();
+            if (d != last_done || tl != last_tail) {
+                last_done = d;
+                last_tail = tl;
+                t_progress = now;
+                sleep_ns = 64;
+            } else if ((long long)(now - t_progress) > p.spin_limit_ns ||
+                       (long long)(now - t_start) > p.time_limit_ns) {
+                if (lane == 0) atomicOr(&p.hdr->error, ERR_TIMEOUT);
+                break;
+            }
+            __nanosleep(sleep_ns);
+            sleep_ns = sleep_ns < 8192 ? sleep_ns * 2 : 8192;
+            continue;
+        }
+
+        // K flights per electron between refills
+        for (int k = 0; k < K; ++k) {
+            int ev = EV_NONE;
+            if (has) ev = e.template fly<FK>(p, tb, ch);
+            if (__any_sync(FULL, ev & EV_CHILD))
+                retired += push_children(p, (ev & EV_CHILD) != 0, ch, e.aval, lane);
+            if (ev & EV_RETIRE) {
+                finish(p, tb, e, ls);
+                has = false;
+                ++retired;
+            }
+        }
+        if (has) e.template round_end<FK>(p);
+
+        // finished electrons are published after their endpoint writes
+        const int r = __reduce_add_sync(FULL, retired);
+        if (r) {
+            __threadfence();
+            if (lane == 0) atomicAdd(&p.hdr->done, (unsigned long long)r);
+        }
+        if (lane == 0 && (long long)(globaltimer() - t_start) > p.time_limit_ns)
+            atomicOr(&p.hdr->error, ERR_TIMEOUT);
+    }
+
+    const unsigned long long f = ls.flights, rl = ls.real, nl = ls.nul;
+    unsigned long long wf = f, wr = rl, wn = nl;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        wf += __shfl_xor_sync(FULL, wf, o);
+        wr += __shfl_xor_sync(FULL, wr, o);
+        wn += __shfl_xor_sync(FULL, wn, o);
+    }
+    if (lane == 0) {
+        atomicAdd(&p.hdr->flights, wf);
+        atomicAdd(&p.hdr->real, wr);
+        atomicAdd(&p.hdr->nul, wn);
+    }
+}
+
+// One generation of one avalanche (plain mode): every electron of `cur`
+// flies until it ionises (it stays alive and its new electron goes to
+// `fresh`) or finishes (alive = 0).
+template <class E, int FK, bool SMEM_TABLE, int MAXT>
+__global__ void __launch_bounds__(MAXT)
+    k_plain_transport(const RunParams p, const Stack cur, long long n_active, const Stack fresh,
+                      int parity, int aval)
+{
+    extern __shared__ __align__(16) unsigned char smem[];
+    const Tables tb = stage_tables<SMEM_TABLE>(p, smem);
+    if (blockIdx.x == 0 && threadIdx.x == 0) p.hdr->n_next[parity] = 0ull;
+    const unsigned long long t_start = p.hdr->t_start;
+    const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n_active) return;
+
+    E e;
+    e.template restore<FK>(p, cur, i, aval);
+    const uint32_t nf0 = e.nf, nr0 = e.nreal;
+    LaneStats ls;
+    Child ch;
+    int ev = EV_NONE;
+    if (e.nf == 0u) ev = e.template check_start<FK>(p);
+    unsigned long long k = 0;
+    while (ev == EV_NONE) {
+        ev = e.template fly<FK>(p, tb, ch);
+        if ((++k & 4095ull) == 0ull) {
+            if ((long long)(globaltimer() - t_start) > p.time_limit_ns) {
+                atomicOr(&p.hdr->error, ERR_TIMEOUT);
+                break;
+            }
+        }
+    }
+    if (ev & EV_CHILD) {
+        const unsigned long long s = atomicAdd(&p.hdr->tail, 1ull);
+        if (s < (unsigned long long)p.capacity) {
+            store_birth(p, (int64_t)s, ch, aval);
+            p.ready[s] = 1u;
+            const unsigned long long j = atomicAdd(&p.hdr->n_new[parity], 1ull);
+            fresh.x[j] = ch.x; fresh.y[j] = ch.y; fresh.z[j] = ch.z; fresh.t[j] = ch.t;
+            fresh.vx[j] = ch.vx; fresh.vy[j] = ch.vy; fresh.vz[j] = ch.vz;
+            fresh.nf[j] = 0u; fresh.nreal[j] = 0u; fresh.uid[j] = ch.uid;
+            fresh.slot[j] = (int64_t)s;
+        } else {
+            atomicAdd(&p.hdr->dropped, 1ull);
+            atomicOr(&p.hdr->error, ERR_OVERFLOW);
+        }
+    }
+    // per-level counts of this stretch go to the avalanche's tallies
+    const int L = p.gas.n_levels;
+    uint64_t *tal = p.tallies + (int64_t)aval * (L + 1);
+    unsigned long long real = 0;
+    for (int j = 0; j < L; ++j) {
+        uint32_t &c = tb.tally[j * blockDim.x + threadIdx.x];
+        if (c) {
+            atomicAdd(reinterpret_cast<unsigned long long *>(tal + j), (unsigned long long)c);
+            real += c;
+            c = 0u;
+        }
+    }
+    if (e.nnull) atomicAdd(reinterpret_cast<unsigned long long *>(tal + L),
+                           (unsigned long long)e.nnull);
+    atomicAdd(&p.hdr->flights, (unsigned long long)(e.nf - nf0));
+    atomicAdd(&p.hdr->real, (unsigned long long)(e.nreal - nr0));
+    atomicAdd(&p.hdr->nul, (unsigned long long)e.nnull);
+    if (ev & EV_RETIRE) {
+        e.write_end(p);
+        cur.alive[i] = 0;
+    } else {
+        e.template save<FK>(p, cur, i);
+        cur.alive[i] = 1;
+    }
+}
+
+}  // namespace gt

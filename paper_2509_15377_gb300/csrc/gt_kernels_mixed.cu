@@ -1,0 +1,121 @@
+// gt_kernels_mixed.cu -- mixed-precision instantiations of the transport
+// kernels, with the FP32 cumulative table staged in shared memory when it
+// fits next to the per-thread tallies (else read through the read-only path).
+#include "gt_kernels.cuh"
+#include "gt_launch.h"
+
+namespace gt {
+
+constexpr int kMaxThreadsMixed = 512;
+
+template <int FK, bool TAB>
+static cudaError_t batched(const RunParams &p, int grid, int block, size_t smem, cudaStream_t s)
+{
+    k_batched<MixedElectron, FK, TAB, kMaxThreadsMixed><<<grid, block, smem, s>>>(p);
+    return cudaGetLastError();
+}
+
+template <int FK, bool TAB>
+static cudaError_t plain(const RunParams &p, const PlainArgs &a, int block, size_t smem,
+                         cudaStream_t s)
+{
+    const long long n = a.n_active;
+    if (n <= 0) return cudaSuccess;
+    k_plain_transport<MixedElectron, FK, TAB, kMaxThreadsMixed>
+        <<<(unsigned)((n + block - 1) / block), block, smem, s>>>(p, a.cur, n, a.fresh, a.parity,
+                                                                  a.aval);
+    return cudaGetLastError();
+}
+
+template <bool TAB>
+static cudaError_t batched_fk(const RunParams &p, int grid, int block, size_t smem, cudaStream_t s)
+{
+    switch (p.field.kind) {
+    case GT_FIELD_UNIFORM: return batched<GT_FIELD_UNIFORM, TAB>(p, grid, block, smem, s);
+    case GT_FIELD_PLATE: return batched<GT_FIELD_PLATE, TAB>(p, grid, block, smem, s);
+    case GT_FIELD_COAX: return batched<GT_FIELD_COAX, TAB>(p, grid, block, smem, s);
+    default: return batched<GT_FIELD_GRID, TAB>(p, grid, block, smem, s);
+    }
+}
+
+template <bool TAB>
+static cudaError_t plain_fk(const RunParams &p, const PlainArgs &a, int block, size_t smem,
+                            cudaStream_t s)
+{
+    switch (p.field.kind) {
+    case GT_FIELD_UNIFORM: return plain<GT_FIELD_UNIFORM, TAB>(p, a, block, smem, s);
+    case GT_FIELD_PLATE: return plain<GT_FIELD_PLATE, TAB>(p, a, block, smem, s);
+    case GT_FIELD_COAX: return plain<GT_FIELD_COAX, TAB>(p, a, block, smem, s);
+    default: return plain<GT_FIELD_GRID, TAB>(p, a, block, smem, s);
+    }
+}
+
+cudaError_t launch_batched_mixed(const RunParams &p, bool smem_table, int grid, int block,
+                                 size_t smem, cudaStream_t s)
+{
+    return smem_table ? batched_fk<true>(p, grid, block, smem, s)
+                      : batched_fk<false>(p, grid, block, smem, s);
+}
+
+cudaError_t launch_plain_mixed(const RunParams &p, const PlainArgs &a, bool smem_table, int block,
+                               size_t smem, cudaStream_t s)
+{
+    return smem_table ? plain_fk<true>(p, a, block, smem, s) : plain_fk<false>(p, a, block, smem, s);
+}
+
+template <int FK, bool TAB>
+static cudaError_t configure_one(size_t max_smem)
+{
+    cudaError_t e = cudaFuncSetAttribute(k_batched<MixedElectron, FK, TAB, kMaxThreadsMixed>,
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize, (int)max_smem);
+    if (e != cudaSuccess) return e;
+    return cudaFuncSetAttribute(k_plain_transport<MixedElectron, FK, TAB, kMaxThreadsMixed>,
+                                cudaFuncAttributeMaxDynamicSharedMemorySize, (int)max_smem);
+}
+
+template <bool TAB>
+static cudaError_t configure_tab(size_t max_smem)
+{
+    cudaError_t e;
+    if ((e = configure_one<GT_FIELD_UNIFORM, TAB>(max_smem)) != cudaSuccess) return e;
+    if ((e = configure_one<GT_FIELD_PLATE, TAB>(max_smem)) != cudaSuccess) return e;
+    if ((e = configure_one<GT_FIELD_COAX, TAB>(max_smem)) != cudaSuccess) return e;
+    return configure_one<GT_FIELD_GRID, TAB>(max_smem);
+}
+
+cudaError_t configure_mixed(size_t max_smem)
+{
+    cudaError_t e = configure_tab<true>(max_smem);
+    if (e != cudaSuccess) return e;
+    return configure_tab<false>(max_smem);
+}
+
+int max_block_mixed() { return kMaxThreadsMixed; }
+
+template <int FK, bool TAB>
+static int occ(int block, size_t smem)
+{
+    int n = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(
+            &n, k_batched<MixedElectron, FK, TAB, kMaxThreadsMixed>, block, smem) != cudaSuccess)
+        return 0;
+    return n;
+}
+
+template <bool TAB>
+static int occ_fk(int field_kind, int block, size_t smem)
+{
+    switch (field_kind) {
+    case GT_FIELD_UNIFORM: return occ<GT_FIELD_UNIFORM, TAB>(block, smem);
+    case GT_FIELD_PLATE: return occ<GT_FIELD_PLATE, TAB>(block, smem);
+    case GT_FIELD_COAX: return occ<GT_FIELD_COAX, TAB>(block, smem);
+    default: return occ<GT_FIELD_GRID, TAB>(block, smem);
+    }
+}
+
+int occupancy_batched_mixed(int field_kind, bool smem_table, int block, size_t smem)
+{
+    return smem_table ? occ_fk<true>(field_kind, block, smem) : occ_fk<false>(field_kind, block, smem);
+}
+
+}  // namespace gt

@@ -1,0 +1,86 @@
+"""Host-only checks of the C-ABI library (no GPU needed): it builds for
+sm_103a, loads, exports every entry point that include/gt_avalanche.h
+declares, its struct layouts match the binding, and calls that need no
+device behave as documented."""
+import ctypes as C
+import os
+import re
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+HEADER = os.path.join(ROOT, "include", "gt_avalanche.h")
+
+
+@pytest.fixture(scope="module")
+def lib():
+    from paper_2509_15377_gb300 import build as B
+    B.build()
+    from paper_2509_15377_gb300 import avalanche as A
+    return A.load()
+
+
+def declared_functions():
+    text = open(HEADER).read()
+    text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+    names = re.findall(r"^\s*(?:const\s+)?\w+\s*\*?\s*(\w+)\s*\(", text, flags=re.M)
+    return sorted(set(n for n in names if n not in ("sizeof",)))
+
+
+def test_every_declared_symbol_is_exported(lib):
+    from paper_2509_15377_gb300 import avalanche as A
+    names = declared_functions()
+    assert set(names) == set(A.EXPORTS), names
+    for n in names:
+        assert hasattr(lib, n), n
+
+
+def test_struct_layouts_match(lib):
+    from paper_2509_15377_gb300 import avalanche as A
+    sizes = (C.c_size_t * 5)()
+    assert lib.gt_abi_sizes(sizes, 5) == 0
+    assert list(sizes) == [C.sizeof(s) for s in (A.gt_gas, A.gt_field, A.gt_run,
+                                                    A.gt_endpoints, A.gt_stats)]
+    assert lib.gt_abi_sizes(sizes, 4) == A.GT_ERR_ARG
+    assert lib.gt_abi_version() == 1
+
+
+def test_error_strings(lib):
+    from paper_2509_15377_gb300 import avalanche as A
+    for code in (A.GT_OK, A.GT_ERR_ARG, A.GT_ERR_STATE, A.GT_ERR_WORKSPACE,
+                 A.GT_ERR_QUEUE_OVERFLOW, A.GT_ERR_TIMEOUT, A.GT_ERR_CUDA, A.GT_ERR_NO_DEVICE,
+                 A.GT_ERR_UNSUPPORTED):
+        assert A.strerror(code) and A.strerror(code) != "unknown error"
+    assert A.strerror(12345) == "unknown error"
+
+
+def test_null_arguments_rejected_without_device(lib):
+    from paper_2509_15377_gb300 import avalanche as A
+    assert lib.gt_create(None, 0) == A.GT_ERR_ARG
+    assert lib.gt_destroy(None) == A.GT_OK
+    assert lib.gas_table_upload(None, None) == A.GT_ERR_ARG
+    assert lib.field_setup(None, None) == A.GT_ERR_ARG
+    assert lib.avalanche_run(None, None, None, None, 0, None, None) == A.GT_ERR_ARG
+    assert lib.avalanche_observables(None, None, 0, 0, None, 0, 0, 0.0, None, None) == A.GT_ERR_ARG
+
+
+def test_create_reports_missing_device(lib):
+    import torch
+    from paper_2509_15377_gb300 import avalanche as A
+    if torch.cuda.is_available():
+        pytest.skip("a GPU is present")
+    h = C.c_void_p()
+    assert lib.gt_create(C.byref(h), 0) == A.GT_ERR_NO_DEVICE
+    with pytest.raises(A.GtError):
+        A.Avalanche(0)
+
+
+def test_binding_fails_loudly_without_library(tmp_path):
+    from paper_2509_15377_gb300 import avalanche as A
+    saved = A._lib
+    A._lib = None
+    try:
+        with pytest.raises(RuntimeError):
+            A.load(str(tmp_path / "missing.so"))
+    finally:
+        A._lib = saved
