@@ -247,6 +247,29 @@ int gt_workspace_bytes(gt_ctx *ctx, const gt_run *run, int64_t capacity, size_t 
 int avalanche_run(gt_ctx *ctx, const gt_run *run, const gt_endpoints *out, void *workspace,
                   size_t workspace_bytes, void *stream, gt_stats *stats);
 
+/* ---- autotuning of the batched launch shape ---------------------------
+ * The batched kernel's throughput depends on the threads per CTA (more
+ * resident warps against fewer registers each) and on the flights per
+ * round (fewer queue refills and FP64 flushes against lanes idling after
+ * their electron finishes).  gt_autotune runs `run` in GT_BATCHED mode once
+ * per candidate shape (after one warm-up run) and measures real collisions
+ * per millisecond of transport kernel time (CUDA events).  The fastest
+ * shape is remembered by the context for the run's precision and field
+ * kind, and used by later runs that leave block / flights_per_round at 0.
+ * points (may be NULL) receives up to max_points measurements, *n_points
+ * their number; *best the chosen shape.  Errors as avalanche_run; a
+ * candidate that fails is skipped. */
+typedef struct {
+    int32_t block;
+    int32_t flights_per_round;
+    double real_per_ms;
+    double transport_ms;
+} gt_tune_point;
+
+int gt_autotune(gt_ctx *ctx, const gt_run *run, const gt_endpoints *out, void *workspace,
+                size_t workspace_bytes, void *stream, gt_tune_point *points, int32_t max_points,
+                int32_t *n_points, gt_tune_point *best);
+
 /* Observables of a finished run (Sec. 2: gain = electrons at the end of the
  * avalanche / initial electrons), computed on the device from the first
  * n_endpoints slots of `ep` and written as GT_OBS_COUNT doubles to the

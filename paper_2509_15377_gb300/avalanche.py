@@ -86,9 +86,17 @@ class gt_stats(C.Structure):
         return {k: getattr(self, k) for k, _ in self._fields_}
 
 
+class gt_tune_point(C.Structure):
+    _fields_ = [("block", C.c_int32), ("flights_per_round", C.c_int32),
+                ("real_per_ms", C.c_double), ("transport_ms", C.c_double)]
+
+    def as_dict(self) -> dict:
+        return {k: getattr(self, k) for k, _ in self._fields_}
+
+
 EXPORTS = ("gt_abi_version", "gt_strerror", "gt_abi_sizes", "gt_last_cuda_error", "gt_create",
            "gt_destroy", "gas_table_upload", "gt_gas_nu_max", "field_setup",
-           "gt_workspace_bytes", "avalanche_run", "avalanche_observables")
+           "gt_workspace_bytes", "avalanche_run", "gt_autotune", "avalanche_observables")
 
 _lib = None
 
@@ -117,6 +125,9 @@ def load(path: str = LIB_PATH):
                            C.POINTER(gt_stats)], C.c_int),
         "avalanche_observables": ([vp, C.POINTER(gt_endpoints), i64, i32, vp, i32, i32,
                                    C.c_double, vp, vp], C.c_int),
+        "gt_autotune": ([vp, C.POINTER(gt_run), C.POINTER(gt_endpoints), vp, sz, vp,
+                         C.POINTER(gt_tune_point), i32, C.POINTER(i32),
+                         C.POINTER(gt_tune_point)], C.c_int),
     }
     for name, (args, res) in sig.items():
         f = getattr(lib, name)
@@ -198,6 +209,17 @@ def avalanche_run(ctx, run: gt_run, out: gt_endpoints, workspace_ptr: int, works
     _check(rc, "avalanche_run", ctx, allow)
     st.status = rc
     return st
+
+
+def gt_autotune(ctx, run: gt_run, out: gt_endpoints, workspace_ptr: int, workspace_nbytes: int,
+                stream_ptr: int):
+    """Measure every candidate launch shape; returns (best, [points])."""
+    pts = (gt_tune_point * 64)()
+    n = C.c_int32()
+    best = gt_tune_point()
+    _check(load().gt_autotune(ctx, C.byref(run), C.byref(out), workspace_ptr, workspace_nbytes,
+                              stream_ptr, pts, 64, C.byref(n), C.byref(best)), "gt_autotune", ctx)
+    return best.as_dict(), [pts[i].as_dict() for i in range(min(n.value, 64))]
 
 
 def avalanche_observables(ctx, out: gt_endpoints, n_endpoints: int, n_avalanches: int,
@@ -366,6 +388,16 @@ class Avalanche:
         st = avalanche_run(self.ctx, r, o, self.ws.data_ptr(), self.ws.numel(), s.cuda_stream,
                            allow)
         return st.as_dict()
+
+    def autotune(self, prim: dict, opt: RunOptions, capacity: int, stream=None):
+        """Pick the batched launch shape for this precision and field kind
+        (remembered by the context for runs that leave it at 0)."""
+        torch = self.torch
+        r = self.make_run(prim, opt)
+        self.alloc(capacity, r.n_avalanches, r)
+        o = self.endpoints_struct(capacity)
+        s = stream if stream is not None else torch.cuda.current_stream(self.device)
+        return gt_autotune(self.ctx, r, o, self.ws.data_ptr(), self.ws.numel(), s.cuda_stream)
 
     def fetch(self, n: int) -> dict:
         """Copy the first n endpoints and the per-avalanche arrays to numpy."""

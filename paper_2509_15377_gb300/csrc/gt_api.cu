@@ -31,6 +31,9 @@ struct gt_ctx {
     size_t obs_counts_cap = 0;
     double *d_obs_partials = nullptr;
     size_t obs_partials_cap = 0;
+    // autotuned batched launch shape per [precision][field kind] (0 = none)
+    int tuned_block[2][4] = {{0}};
+    int tuned_k[2][4] = {{0}};
     char last_error[256] = {0};
 };
 
@@ -219,7 +222,8 @@ int gas_table_upload(gt_ctx *ctx, const gt_gas *g)
 {
     if (!ctx || !g) return GT_ERR_ARG;
     const int L = g->n_levels, N = g->n_nodes;
-    if (L < 1 || L > GT_MAX_LEVELS || N < 2 || !finite_pos(g->d_eps) || !g->level_type ||
+    if (L < 1 || L > GT_MAX_LEVELS || N < 2 || N > (1 << 22) || !finite_pos(g->d_eps) ||
+        !g->level_type ||
         !g->threshold || !g->rate || !(g->recoil >= 0.0 && g->recoil < 0.5))
         return GT_ERR_ARG;
     for (int j = 0; j < L; ++j) {
@@ -273,6 +277,7 @@ int gas_table_upload(gt_ctx *ctx, const gt_gas *g)
     d.inv_nu_max_f = (float)d.inv_nu_max;
     d.recoil_f = (float)g->recoil;
     d.last_x_f = (float)(N - 1);
+    d.lastk_f = (float)(N - 2);
     d.cum64 = ctx->d_cum64;
     d.cum32 = ctx->d_cum32;
     for (int j = 0; j < L; ++j) {
@@ -319,7 +324,8 @@ int field_setup(gt_ctx *ctx, const gt_field *f)
         d.coax_k = f->voltage / std::log(f->tube_r / f->wire_r);
         break;
     case GT_FIELD_GRID:
-        if (f->nx < 2 || f->ny < 2 || f->nz < 2 || !f->grid ||
+        if (f->nx < 2 || f->ny < 2 || f->nz < 2 || f->nx > (1 << 22) || f->ny > (1 << 22) ||
+            f->nz > (1 << 22) || !f->grid ||
             ((uintptr_t)f->grid & 15u) != 0 || !(f->wire_r >= 0.0))
             return GT_ERR_ARG;
         d.nx = f->nx; d.ny = f->ny; d.nz = f->nz;
@@ -337,6 +343,23 @@ int field_setup(gt_ctx *ctx, const gt_field *f)
     default:
         return GT_ERR_ARG;
     }
+    // FP32 copies used by the mixed-precision step
+    d.e0_f = (float)d.e0;
+    d.coax_k_f = (float)d.coax_k;
+    for (int i = 0; i < 3; ++i) {
+        d.w_f[i] = (float)d.w[i];
+        d.origin_f[i] = (float)d.origin[i];
+        d.inv_spacing_f[i] = (float)d.inv_spacing[i];
+        const double m = 1e-5 * (d.hi[i] - d.origin[i]);
+        d.box_lo_f[i] = (float)(d.origin[i] + m);
+        d.box_hi_f[i] = (float)(d.hi[i] - m);
+    }
+    d.cell_hi_f[0] = (float)(d.nx - 2); d.cell_hi_f[1] = (float)(d.ny - 2);
+    d.cell_hi_f[2] = (float)(d.nz - 2);
+    d.node_hi_f[0] = (float)(d.nx - 1); d.node_hi_f[1] = (float)(d.ny - 1);
+    d.node_hi_f[2] = (float)(d.nz - 1);
+    d.wire_r2_hi_f = (float)(d.wire_r2 * 1.00001);
+    d.tube_r2_lo_f = (float)(d.tube_r2 * 0.99999);
     ctx->field = d;
     ctx->has_field = true;
     return GT_OK;
@@ -431,7 +454,10 @@ int avalanche_run(gt_ctx *ctx, const gt_run *r, const gt_endpoints *o, void *ws,
     p.seed = r->seed;
     p.t_max = r->t_max > 0.0 ? r->t_max : 0.0;
     p.coll_limit = r->coll_limit;
-    p.flights_per_round = r->flights_per_round > 0 ? r->flights_per_round : 16;
+    const int prec_i = r->precision == GT_FP64 ? 0 : 1;
+    const int tuned_k = ctx->tuned_k[prec_i][ctx->field.kind & 3];
+    p.flights_per_round = r->flights_per_round > 0 ? r->flights_per_round
+                                                   : (tuned_k > 0 ? tuned_k : 32);
     p.size_limit = r->size_limit;
     p.spin_limit_ns = (long long)((r->spin_limit_ms > 0 ? r->spin_limit_ms : 60000.0) * 1e6);
     p.time_limit_ns = (long long)((r->time_limit_ms > 0 ? r->time_limit_ms : 600000.0) * 1e6);
@@ -487,11 +513,15 @@ int avalanche_run(gt_ctx *ctx, const gt_run *r, const gt_endpoints *o, void *ws,
     ++launches;
 
     const bool fp64 = r->precision == GT_FP64;
-    const int block = r->block ? r->block : default_block(r->precision);
+    const int tuned_b = ctx->tuned_block[prec_i][ctx->field.kind & 3];
+    const int block = r->block ? r->block
+                               : (r->mode == GT_BATCHED && tuned_b > 0 ? tuned_b
+                                                                       : default_block(r->precision));
     const size_t smem_tab = shared_bytes(L, ctx->gas.n_nodes, block, true);
-    const bool smem_table = !fp64 && smem_tab <= ctx->smem_optin;
+    const size_t smem_cap = ctx->smem_optin - kStaticSmemReserve;
+    const bool smem_table = !fp64 && smem_tab <= smem_cap;
     const size_t smem = shared_bytes(L, ctx->gas.n_nodes, block, smem_table);
-    if (smem > ctx->smem_optin) return GT_ERR_UNSUPPORTED;
+    if (smem > smem_cap) return GT_ERR_UNSUPPORTED;
     int iterations = 0, grid = 0;
     unsigned host_err = 0;  // aborts decided on the host (plain mode)
     double transport_ms = 0.0;
@@ -611,6 +641,50 @@ int avalanche_run(gt_ctx *ctx, const gt_run *r, const gt_endpoints *o, void *ws,
         stats->grid = grid;
     }
     return rc;
+}
+
+int gt_autotune(gt_ctx *ctx, const gt_run *run, const gt_endpoints *out, void *ws,
+                size_t ws_bytes, void *stream, gt_tune_point *points, int32_t max_points,
+                int32_t *n_points, gt_tune_point *best)
+{
+    if (!ctx || !run || !best) return GT_ERR_ARG;
+    gt_run r = *run;
+    r.mode = GT_BATCHED;
+    const bool fp64 = r.precision == GT_FP64;
+    static const int blocks_mixed[] = {512, 640, 768, 1024};
+    static const int blocks_fp64[] = {128, 256, 512};
+    static const int ks[] = {8, 16, 32, 64};
+    const int *blocks = fp64 ? blocks_fp64 : blocks_mixed;
+    const int nb = fp64 ? 3 : 4;
+    gt_stats st{};
+    r.block = blocks[0];
+    r.flights_per_round = 32;
+    int rc = avalanche_run(ctx, &r, out, ws, ws_bytes, stream, &st);  // warm-up
+    if (rc != GT_OK) return rc;
+    int n = 0;
+    gt_tune_point top{0, 0, 0.0, 0.0};
+    for (int bi = 0; bi < nb; ++bi) {
+        for (int k : ks) {
+            r.block = blocks[bi];
+            r.flights_per_round = k;
+            if (avalanche_run(ctx, &r, out, ws, ws_bytes, stream, &st) != GT_OK) continue;
+            gt_tune_point pt;
+            pt.block = r.block;
+            pt.flights_per_round = k;
+            pt.transport_ms = st.transport_ms;
+            pt.real_per_ms = st.transport_ms > 0 ? (double)st.real_collisions / st.transport_ms : 0.0;
+            if (points && n < max_points) points[n] = pt;
+            ++n;
+            if (pt.real_per_ms > top.real_per_ms) top = pt;
+        }
+    }
+    if (n_points) *n_points = n;
+    if (top.block == 0) return GT_ERR_UNSUPPORTED;
+    const int pi = fp64 ? 0 : 1;
+    ctx->tuned_block[pi][ctx->field.kind & 3] = top.block;
+    ctx->tuned_k[pi][ctx->field.kind & 3] = top.flights_per_round;
+    *best = top;
+    return GT_OK;
 }
 
 int avalanche_observables(gt_ctx *ctx, const gt_endpoints *ep, int64_t n_endpoints,

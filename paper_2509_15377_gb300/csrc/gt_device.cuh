@@ -36,7 +36,8 @@ enum : int { EV_NONE = 0, EV_CHILD = 1, EV_RETIRE = 2 };
 struct DevGas {
     int n_levels, n_nodes;
     double d_eps, inv_d_eps, nu_max, inv_nu_max, recoil;
-    float inv_d_eps_f, nu_max_f, inv_nu_max_f, recoil_f, last_x_f;
+    float inv_d_eps_f, nu_max_f, inv_nu_max_f, recoil_f;
+    float last_x_f, lastk_f;  // n_nodes - 1 and n_nodes - 2 as floats
     const double *cum64;  // [n_nodes][n_levels] running sums over levels
     const float *cum32;
     int32_t type[GT_MAX_LEVELS];
@@ -52,6 +53,12 @@ struct DevField {
     int nx, ny, nz;
     double origin[3], inv_spacing[3], hi[3];
     const float4 *grid;
+    // FP32 copies for the mixed-precision step (no per-flight conversions)
+    float e0_f, coax_k_f, w_f[3];
+    float origin_f[3], inv_spacing_f[3];
+    float wire_r2_hi_f, tube_r2_lo_f;    // radial pre-test limits (1e-5 margins)
+    float box_lo_f[3], box_hi_f[3];      // map-box pre-test limits (inside by 1e-5)
+    float cell_hi_f[3], node_hi_f[3];    // n - 2 and n - 1 per axis
 };
 
 struct Header {  // at the start of the work space, 256 bytes
@@ -170,10 +177,12 @@ __device__ __forceinline__ uint4 draw(uint64_t seed, int aval, uint64_t uid, uin
 
 // (w + 1/2) 2^-32 in (0, 1), exact in FP64.
 __device__ __forceinline__ double u01d(uint32_t w) { return ((double)w + 0.5) * 0x1p-32; }
-// (w>>9 + 1/2) 2^-23 in (0, 1), exact in FP32 (24 significant bits).
+// (w>>9 + 1/2) 2^-23 in (0, 1), exact in FP32 (24 significant bits).  Built
+// from the bits (1 + (w>>9) 2^-23 has exponent 0) so that no int-to-float
+// conversion is issued: conversions share GB300's narrow FP64 pipe.
 __device__ __forceinline__ float u01f(uint32_t w)
 {
-    return ((float)(w >> 9) + 0.5f) * 0x1p-23f;
+    return __uint_as_float(0x3F800000u | (w >> 9)) - (1.0f - 0x1p-24f);
 }
 
 // SplitMix64 output function (Steele, Lea, Flood, OOPSLA 2014); the id of
@@ -190,12 +199,13 @@ __device__ __forceinline__ uint64_t child_uid(uint64_t parent, uint32_t flight)
 // Per-CTA view of the gas constants; the FP32 cumulative table is staged
 // into shared memory when it fits (mixed precision).
 struct Tables {
-    const float *cum32;     // shared or global
-    const double *cum64;    // global (read-only path)
+    const float *cum32;     // shared or global, rows of `stride32` floats
+    const double *cum64;    // global (read-only path), rows of n_levels
     const int *type;        // shared [L]
     const double *thr;      // shared [L]
     const float *thr_f;     // shared [L]
     uint32_t *tally;        // shared [L][blockDim]: real collisions per level
+    int stride32;           // odd in shared memory: rows start on every bank
 };
 
 // --------------------------------------------------------------- fields
@@ -241,20 +251,27 @@ __device__ __forceinline__ void field32(const DevField &f, float plate_e, float 
                                         float &ex, float &ey, float &ez)
 {
     if (FK == GT_FIELD_UNIFORM) {
-        ex = 0.f; ey = 0.f; ez = -(float)f.e0;
+        ex = 0.f; ey = 0.f; ez = -f.e0_f;
     } else if (FK == GT_FIELD_PLATE) {
         ex = 0.f; ey = 0.f; ez = -plate_e;
     } else if (FK == GT_FIELD_COAX) {
-        const float s = (float)f.coax_k / (x * x + y * y);
+        const float s = __fdividef(f.coax_k_f, x * x + y * y);
         ex = s * x; ey = s * y; ez = 0.f;
     } else {
-        const float gx = (x - (float)f.origin[0]) * (float)f.inv_spacing[0];
-        const float gy = (y - (float)f.origin[1]) * (float)f.inv_spacing[1];
-        const float gz = (z - (float)f.origin[2]) * (float)f.inv_spacing[2];
-        int ix = min(max((int)floorf(gx), 0), f.nx - 2);
-        int iy = min(max((int)floorf(gy), 0), f.ny - 2);
-        int iz = min(max((int)floorf(gz), 0), f.nz - 2);
-        const float wx = gx - ix, wy = gy - iy, wz = gz - iz;
+        // cell (clamped to the last one) and weights without int/float
+        // conversions: floor(g) by a round-down add of 2^23
+        float w3[3];
+        int i3[3];
+#pragma unroll
+        for (int d = 0; d < 3; ++d) {
+            const float g = fmaxf((d == 0 ? x : d == 1 ? y : z) - f.origin_f[d], 0.f) *
+                            f.inv_spacing_f[d];
+            const float t = __fadd_rd(fminf(g, f.cell_hi_f[d]), 8388608.0f);
+            i3[d] = __float_as_int(t) - 0x4B000000;
+            w3[d] = fminf(g, f.node_hi_f[d]) - (t - 8388608.0f);
+        }
+        const int ix = i3[0], iy = i3[1], iz = i3[2];
+        const float wx = w3[0], wy = w3[1], wz = w3[2];
         const float4 *b = f.grid + (((int64_t)iz * f.ny + iy) * f.nx + ix);
         const int64_t sy = f.nx, sz = (int64_t)f.nx * f.ny;
         const float4 c000 = __ldg(b), c100 = __ldg(b + 1);
@@ -353,6 +370,33 @@ __device__ __forceinline__ int select_level(const T *cum, int L, int N, R inv_d_
     return lvl;
 }
 
+// FP32 selection on a table with row stride `stride`, without int/float
+// conversions: floor(x) for 0 <= x < 2^23 is the round-down sum x + 2^23
+// read back as an integer.  Rows k and k+1 bracket the energy (the last
+// interval extends to energies beyond the table).  The level is found by a
+// branch-free binary search over the non-decreasing running sums.
+__device__ __forceinline__ int select_level32(const float *cum, int stride, int L, float lastk,
+                                              float last, float inv_d_eps, float eps, float Rv)
+{
+    const float xk = eps * inv_d_eps;
+    const float t = __fadd_rd(fminf(xk, lastk), 8388608.0f);
+    const int k = __float_as_int(t) - 0x4B000000;
+    const float f = fminf(xk, last) - (t - 8388608.0f);
+    const float *c0 = cum + k * stride;
+    const float *c1 = c0 + stride;
+    const float top = fmaf(f, c1[L - 1] - c0[L - 1], c0[L - 1]);
+    if (!(Rv < top)) return -1;
+    const int m = L - 1;  // levels below the last; the last is known to exceed R
+    int pos = 0;
+    if (m > 0) {
+        for (int step = 1 << (31 - __clz(m)); step > 0; step >>= 1) {
+            const int j = pos + step - 1;
+            if (j < m && fmaf(f, c1[j] - c0[j], c0[j]) <= Rv) pos += step;
+        }
+    }
+    return pos;
+}
+
 // Isotropic unit vector from two uniforms: cos(theta) = 1 - 2 u, phi = 2 pi v.
 __device__ __forceinline__ void isotropic64(double u, double v, double &nx, double &ny,
                                             double &nz)
@@ -365,13 +409,21 @@ __device__ __forceinline__ void isotropic64(double u, double v, double &nx, doub
     nx = st * c; ny = st * s; nz = ct;
 }
 
+// FP32 version.  The azimuth comes from the hardware sin/cos (no range
+// reduction instructions); (c, s) is then rescaled to unit length with a
+// Newton-refined rsqrt, so that |n| = 1 to rounding and the speed set from
+// it carries no systematic error from collision to collision.
 __device__ __forceinline__ void isotropic32(float u, float v, float &nx, float &ny, float &nz)
 {
     const float ct = 1.0f - 2.0f * u;
-    const float st = sqrtf(fmaxf(1.0f - ct * ct, 0.0f));
+    const float st = 2.0f * sqrtf(u * (1.0f - u));  // sqrt(1 - ct^2), well conditioned
     float s, c;
     __sincosf(kTwoPiF * v, &s, &c);
-    nx = st * c; ny = st * s; nz = ct;
+    const float g = fmaf(c, c, s * s);
+    float r = rsqrtf(g);
+    r = r * fmaf(-0.5f * g, r * r, 1.5f);
+    const float sr = st * r;
+    nx = sr * c; ny = sr * s; nz = ct;
 }
 
 // New electron produced by an ionising collision.
@@ -593,19 +645,16 @@ struct MixedElectron {
         } else if (FK == GT_FIELD_PLATE) {
             maybe = (oz >= zhi) || (oz < zlo);
         } else {
+            const DevField &f = p.field;
             const float rx = px + ox, ry = py + oy;
             const float r2 = rx * rx + ry * ry;
-            maybe = (r2 <= (float)p.field.wire_r2 * 1.00001f);
+            maybe = (r2 <= f.wire_r2_hi_f);
             if (FK == GT_FIELD_COAX) {
-                maybe |= (r2 >= (float)p.field.tube_r2 * 0.99999f);
+                maybe |= (r2 >= f.tube_r2_lo_f);
             } else {
                 const float rz = pz + oz;
-                const float mx = 1e-5f * (float)(p.field.hi[0] - p.field.origin[0]);
-                const float my = 1e-5f * (float)(p.field.hi[1] - p.field.origin[1]);
-                const float mz = 1e-5f * (float)(p.field.hi[2] - p.field.origin[2]);
-                maybe |= (rx < (float)p.field.origin[0] + mx) || (rx > (float)p.field.hi[0] - mx) ||
-                         (ry < (float)p.field.origin[1] + my) || (ry > (float)p.field.hi[1] - my) ||
-                         (rz < (float)p.field.origin[2] + mz) || (rz > (float)p.field.hi[2] - mz);
+                maybe |= (rx < f.box_lo_f[0]) || (rx > f.box_hi_f[0]) || (ry < f.box_lo_f[1]) ||
+                         (ry > f.box_hi_f[1]) || (rz < f.box_lo_f[2]) || (rz > f.box_hi_f[2]);
             }
         }
         if (!maybe) return 0;
@@ -639,8 +688,7 @@ struct MixedElectron {
             dz = dt * fmaf(h, az, vz);
             vx = fmaf(ax, dt, vx); vy = fmaf(ay, dt, vy); vz = fmaf(az, dt, vz);
         } else {
-            const float wf[3] = {(float)p.field.w[0], (float)p.field.w[1], (float)p.field.w[2]};
-            lorentz_step<float>(wf, ax, ay, az, dt, vx, vy, vz, dx, dy, dz);
+            lorentz_step<float>(p.field.w_f, ax, ay, az, dt, vx, vy, vz, dx, dy, dz);
         }
         ox += dx; oy += dy; oz += dz; ot += dt;
         nf = flight + 1u;
@@ -654,8 +702,9 @@ struct MixedElectron {
             return EV_RETIRE;
         }
         const float eps = (vx * vx + vy * vy + vz * vz) * kInvTwoAccelF;
-        int lvl = select_level<float, float>(tb.cum32, p.gas.n_levels, p.gas.n_nodes,
-                                             p.gas.inv_d_eps_f, eps, u01f(w.y) * p.gas.nu_max_f);
+        int lvl = select_level32(tb.cum32, tb.stride32, p.gas.n_levels, p.gas.lastk_f,
+                                 p.gas.last_x_f, p.gas.inv_d_eps_f, eps,
+                                 u01f(w.y) * p.gas.nu_max_f);
         if (lvl >= 0 && tb.type[lvl] != GT_LEVEL_ELASTIC) {
             const float th = tb.thr_f[lvl];
             if (eps < th * (1.0f - 1e-6f)) {
@@ -673,15 +722,20 @@ struct MixedElectron {
         tb.tally[lvl * blockDim.x + threadIdx.x] += 1u;
         float nx, ny, nz;
         isotropic32(u01f(w.z), u01f(w.w), nx, ny, nz);
-        float eps_new;
+        float sp;
         int ev = EV_NONE;
         const int type = tb.type[lvl];
         if (type == GT_LEVEL_ELASTIC) {
+            // scale the speed itself: |v'| = |v| sqrt(1 - recoil (1 - cos chi));
+            // a round trip through the energy would multiply by
+            // (2a)_f32 * (1/2a)_f32 != 1 at every collision and drift
+            // (cos chi only enters multiplied by recoil ~ 1e-5, so the
+            // hardware rsqrt is accurate enough there)
             const float v2 = vx * vx + vy * vy + vz * vz;
             const float cchi = v2 > 0.f ? (vx * nx + vy * ny + vz * nz) * rsqrtf(v2) : 0.f;
-            eps_new = eps * (1.0f - p.gas.recoil_f * (1.0f - cchi));
+            sp = sqrtf(v2 * (1.0f - p.gas.recoil_f * (1.0f - cchi)));
         } else {
-            eps_new = fmaxf(eps - tb.thr_f[lvl], 0.0f);
+            float eps_new = fmaxf(eps - tb.thr_f[lvl], 0.0f);
             if (type == GT_LEVEL_IONISATION) {
                 const uint4 w2 = draw(p.seed, aval, uid, flight, 1u);
                 const float es = u01f(w2.x) * eps_new;
@@ -696,8 +750,8 @@ struct MixedElectron {
                 ch.uid = child_uid(uid, flight);
                 ev = EV_CHILD;
             }
+            sp = sqrtf(kTwoAccelF * eps_new);
         }
-        const float sp = sqrtf(kTwoAccelF * eps_new);
         vx = sp * nx; vy = sp * ny; vz = sp * nz;
         ++nreal;
         if (p.coll_limit && nreal >= p.coll_limit) {

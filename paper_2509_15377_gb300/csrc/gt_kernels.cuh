@@ -21,27 +21,37 @@ namespace gt {
 
 constexpr unsigned FULL = 0xFFFFFFFFu;
 
-// Dynamic shared memory: per-level constants, the per-thread collision
-// tallies [L][blockDim] and (optionally) the FP32 cumulative table.
+// Row stride of the FP32 table staged in shared memory: odd, so that the
+// rows of a warp's random energies start on all 32 banks.
+__host__ __device__ inline int smem_stride(int n_levels) { return n_levels | 1; }
+
+// Dynamic shared memory: the per-thread collision tallies [L][blockDim] and
+// (optionally) the FP32 cumulative table with an odd row stride.
 __host__ __device__ inline size_t shared_bytes(int n_levels, int n_nodes, int block, bool table)
 {
-    size_t b = GT_MAX_LEVELS * (sizeof(double) + sizeof(float) + sizeof(int));
-    b += (size_t)n_levels * block * sizeof(uint32_t);
+    size_t b = (size_t)n_levels * block * sizeof(uint32_t);
     b = (b + 15) & ~(size_t)15;
-    if (table) b += (size_t)n_levels * n_nodes * sizeof(float);
+    if (table) b += (size_t)smem_stride(n_levels) * n_nodes * sizeof(float);
     return b;
 }
 
+// Per-CTA statistics and per-warp wait bookkeeping (static shared memory).
+struct BlockState {
+    unsigned long long flights, real, nul;
+    unsigned long long last_done[32], last_tail[32], t_progress[32];
+    unsigned int sleep_ns[32];
+};
+
 template <bool SMEM_TABLE>
-__device__ __forceinline__ Tables stage_tables(const RunParams &p, unsigned char *smem)
+__device__ __forceinline__ Tables stage_tables(const RunParams &p, unsigned char *smem,
+                                               BlockState &bs)
 {
+    __shared__ double s_thr[GT_MAX_LEVELS];
+    __shared__ float s_thr_f[GT_MAX_LEVELS];
+    __shared__ int s_type[GT_MAX_LEVELS];
     const int L = p.gas.n_levels;
-    double *s_thr = reinterpret_cast<double *>(smem);
-    float *s_thr_f = reinterpret_cast<float *>(s_thr + GT_MAX_LEVELS);
-    int *s_type = reinterpret_cast<int *>(s_thr_f + GT_MAX_LEVELS);
-    uint32_t *s_tally = reinterpret_cast<uint32_t *>(s_type + GT_MAX_LEVELS);
-    size_t off = GT_MAX_LEVELS * (sizeof(double) + sizeof(float) + sizeof(int)) +
-                 (size_t)L * blockDim.x * sizeof(uint32_t);
+    uint32_t *s_tally = reinterpret_cast<uint32_t *>(smem);
+    size_t off = (size_t)L * blockDim.x * sizeof(uint32_t);
     off = (off + 15) & ~(size_t)15;
     float *s_cum = reinterpret_cast<float *>(smem + off);
     for (int i = threadIdx.x; i < L; i += blockDim.x) {
@@ -50,13 +60,25 @@ __device__ __forceinline__ Tables stage_tables(const RunParams &p, unsigned char
         s_type[i] = p.gas.type[i];
     }
     for (int i = threadIdx.x; i < L * (int)blockDim.x; i += blockDim.x) s_tally[i] = 0u;
+    const int S = smem_stride(L);
     if (SMEM_TABLE) {
-        const int n = p.gas.n_levels * p.gas.n_nodes;
-        for (int i = threadIdx.x; i < n; i += blockDim.x) s_cum[i] = p.gas.cum32[i];
+        const int N = p.gas.n_nodes;
+        for (int i = threadIdx.x; i < N * L; i += blockDim.x) {
+            const int k = i / L, j = i - k * L;
+            s_cum[k * S + j] = p.gas.cum32[i];
+        }
+    }
+    if (threadIdx.x == 0) bs.flights = bs.real = bs.nul = 0ull;
+    if (threadIdx.x < 32) {
+        bs.last_done[threadIdx.x] = ~0ull;
+        bs.last_tail[threadIdx.x] = ~0ull;
+        bs.t_progress[threadIdx.x] = 0ull;
+        bs.sleep_ns[threadIdx.x] = 64u;
     }
     __syncthreads();
     Tables tb;
     tb.cum32 = SMEM_TABLE ? s_cum : p.gas.cum32;
+    tb.stride32 = SMEM_TABLE ? S : L;
     tb.cum64 = p.gas.cum64;
     tb.type = s_type;
     tb.thr = s_thr;
@@ -65,20 +87,24 @@ __device__ __forceinline__ Tables stage_tables(const RunParams &p, unsigned char
     return tb;
 }
 
-// Per-lane run statistics, reduced per warp at the end.
-struct LaneStats {
-    unsigned long long flights = 0, real = 0, nul = 0;
-};
-
-// An electron has finished: write its endpoint, move its per-level
-// collision counts from shared memory to the avalanche's tallies.
-template <class E>
-__device__ __forceinline__ void finish(const RunParams &p, const Tables &tb, const E &e,
-                                       LaneStats &ls)
+// Block statistics to the run header (after the block's last transport).
+__device__ __forceinline__ void flush_block_stats(const RunParams &p, BlockState &bs)
 {
-    e.write_end(p);
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        atomicAdd(&p.hdr->flights, bs.flights);
+        atomicAdd(&p.hdr->real, bs.real);
+        atomicAdd(&p.hdr->nul, bs.nul);
+    }
+}
+
+// Move an electron's per-level collision counts from shared memory to the
+// avalanche's tallies; returns the number of real collisions moved.
+__device__ __forceinline__ unsigned long long flush_tally(const RunParams &p, const Tables &tb,
+                                                          int aval, uint32_t nnull)
+{
     const int L = p.gas.n_levels;
-    uint64_t *tal = p.tallies + (int64_t)e.aval * (L + 1);
+    uint64_t *tal = p.tallies + (int64_t)aval * (L + 1);
     unsigned long long real = 0;
     for (int j = 0; j < L; ++j) {
         uint32_t &c = tb.tally[j * blockDim.x + threadIdx.x];
@@ -88,11 +114,20 @@ __device__ __forceinline__ void finish(const RunParams &p, const Tables &tb, con
             c = 0u;
         }
     }
-    if (e.nnull) atomicAdd(reinterpret_cast<unsigned long long *>(tal + L),
-                           (unsigned long long)e.nnull);
-    ls.flights += e.nf;
-    ls.real += real;
-    ls.nul += e.nnull;
+    if (nnull) atomicAdd(reinterpret_cast<unsigned long long *>(tal + L), (unsigned long long)nnull);
+    return real;
+}
+
+// An electron has finished: write its endpoint and move its counts.
+template <class E>
+__device__ __forceinline__ void finish(const RunParams &p, const Tables &tb, const E &e,
+                                       BlockState &bs)
+{
+    e.write_end(p);
+    const unsigned long long real = flush_tally(p, tb, e.aval, e.nnull);
+    atomicAdd(&bs.flights, (unsigned long long)e.nf);
+    atomicAdd(&bs.real, real);
+    atomicAdd(&bs.nul, (unsigned long long)e.nnull);
 }
 
 // Write the birth record of a new electron into queue slot s.
@@ -143,18 +178,14 @@ template <class E, int FK, bool SMEM_TABLE, int MAXT>
 __global__ void __launch_bounds__(MAXT) k_batched(const RunParams p)
 {
     extern __shared__ __align__(16) unsigned char smem[];
-    const Tables tb = stage_tables<SMEM_TABLE>(p, smem);
-    const int lane = threadIdx.x & 31;
+    __shared__ BlockState bs;
+    const Tables tb = stage_tables<SMEM_TABLE>(p, smem, bs);
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
     const int K = p.flights_per_round;
-    const unsigned long long t_start = *reinterpret_cast<volatile unsigned long long *>(&p.hdr->t_start);
 
     E e;
     bool has = false;
     long long ticket = -1;
-    LaneStats ls;
-    Child ch;
-    unsigned long long last_done = ~0ull, last_tail = ~0ull, t_progress = t_start;
-    unsigned sleep_ns = 64;
 
     for (;;) {
         // a run-wide abort (time budget or a wait that gave up)
@@ -179,7 +210,7 @@ __global__ void __launch_bounds__(MAXT) k_batched(const RunParams p)
                 ticket = -1;
                 has = true;
                 if (e.template check_start<FK>(p) & EV_RETIRE) {
-                    finish(p, tb, e, ls);
+                    finish(p, tb, e, bs);
                     has = false;
                     retired = 1;
                 }
@@ -188,44 +219,47 @@ __global__ void __launch_bounds__(MAXT) k_batched(const RunParams p)
 
         if (!__any_sync(FULL, has)) {
             // the whole warp waits: finished when every queued electron is done
-            unsigned long long d = 0, tl = 0;
-            if (lane == 0) {
-                d = ld_acquire_u64(&p.hdr->done);
-                tl = ld_acquire_u64(&p.hdr->tail);
-            }
-            d = __shfl_sync(FULL, d, 0);
-            tl = __shfl_sync(FULL, tl, 0);
             const int r = __reduce_add_sync(FULL, retired);
             if (r) {
                 __threadfence();
                 if (lane == 0) atomicAdd(&p.hdr->done, (unsigned long long)r);
                 continue;
             }
-            if (d == tl) break;
-            const unsigned long long now = globaltimer();
-            if (d != last_done || tl != last_tail) {
-                last_done = d;
-                last_tail = tl;
-                t_progress = now;
-                sleep_ns = 64;
-            } else if ((long long)(now - t_progress) > p.spin_limit_ns ||
-                       (long long)(now - t_start) > p.time_limit_ns) {
-                if (lane == 0) atomicOr(&p.hdr->error, ERR_TIMEOUT);
-                break;
+            int verdict = 0;  // 0 wait, 1 finished, 2 give up
+            if (lane == 0) {
+                const unsigned long long d = ld_acquire_u64(&p.hdr->done);
+                const unsigned long long tl = ld_acquire_u64(&p.hdr->tail);
+                const unsigned long long now = globaltimer();
+                if (d == tl) {
+                    verdict = 1;
+                } else if (d != bs.last_done[wid] || tl != bs.last_tail[wid]) {
+                    bs.last_done[wid] = d;
+                    bs.last_tail[wid] = tl;
+                    bs.t_progress[wid] = now;
+                    bs.sleep_ns[wid] = 64u;
+                } else if ((long long)(now - bs.t_progress[wid]) > p.spin_limit_ns ||
+                           (long long)(now - p.hdr->t_start) > p.time_limit_ns) {
+                    atomicOr(&p.hdr->error, ERR_TIMEOUT);
+                    verdict = 2;
+                }
+                if (!verdict) {
+                    __nanosleep(bs.sleep_ns[wid]);
+                    bs.sleep_ns[wid] = bs.sleep_ns[wid] < 8192u ? bs.sleep_ns[wid] * 2u : 8192u;
+                }
             }
-            __nanosleep(sleep_ns);
-            sleep_ns = sleep_ns < 8192 ? sleep_ns * 2 : 8192;
+            if (__shfl_sync(FULL, verdict, 0)) break;
             continue;
         }
 
         // K flights per electron between refills
         for (int k = 0; k < K; ++k) {
+            Child ch;
             int ev = EV_NONE;
             if (has) ev = e.template fly<FK>(p, tb, ch);
             if (__any_sync(FULL, ev & EV_CHILD))
                 retired += push_children(p, (ev & EV_CHILD) != 0, ch, e.aval, lane);
             if (ev & EV_RETIRE) {
-                finish(p, tb, e, ls);
+                finish(p, tb, e, bs);
                 has = false;
                 ++retired;
             }
@@ -238,23 +272,10 @@ __global__ void __launch_bounds__(MAXT) k_batched(const RunParams p)
             __threadfence();
             if (lane == 0) atomicAdd(&p.hdr->done, (unsigned long long)r);
         }
-        if (lane == 0 && (long long)(globaltimer() - t_start) > p.time_limit_ns)
+        if (lane == 0 && (long long)(globaltimer() - p.hdr->t_start) > p.time_limit_ns)
             atomicOr(&p.hdr->error, ERR_TIMEOUT);
     }
-
-    const unsigned long long f = ls.flights, rl = ls.real, nl = ls.nul;
-    unsigned long long wf = f, wr = rl, wn = nl;
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) {
-        wf += __shfl_xor_sync(FULL, wf, o);
-        wr += __shfl_xor_sync(FULL, wr, o);
-        wn += __shfl_xor_sync(FULL, wn, o);
-    }
-    if (lane == 0) {
-        atomicAdd(&p.hdr->flights, wf);
-        atomicAdd(&p.hdr->real, wr);
-        atomicAdd(&p.hdr->nul, wn);
-    }
+    flush_block_stats(p, bs);
 }
 
 // One generation of one avalanche (plain mode): every electron of `cur`
@@ -266,7 +287,8 @@ __global__ void __launch_bounds__(MAXT)
                       int parity, int aval)
 {
     extern __shared__ __align__(16) unsigned char smem[];
-    const Tables tb = stage_tables<SMEM_TABLE>(p, smem);
+    __shared__ BlockState bs;
+    const Tables tb = stage_tables<SMEM_TABLE>(p, smem, bs);
     if (blockIdx.x == 0 && threadIdx.x == 0) p.hdr->n_next[parity] = 0ull;
     const unsigned long long t_start = p.hdr->t_start;
     const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
@@ -275,7 +297,6 @@ __global__ void __launch_bounds__(MAXT)
     E e;
     e.template restore<FK>(p, cur, i, aval);
     const uint32_t nf0 = e.nf, nr0 = e.nreal;
-    LaneStats ls;
     Child ch;
     int ev = EV_NONE;
     if (e.nf == 0u) ev = e.template check_start<FK>(p);
@@ -305,19 +326,7 @@ __global__ void __launch_bounds__(MAXT)
         }
     }
     // per-level counts of this stretch go to the avalanche's tallies
-    const int L = p.gas.n_levels;
-    uint64_t *tal = p.tallies + (int64_t)aval * (L + 1);
-    unsigned long long real = 0;
-    for (int j = 0; j < L; ++j) {
-        uint32_t &c = tb.tally[j * blockDim.x + threadIdx.x];
-        if (c) {
-            atomicAdd(reinterpret_cast<unsigned long long *>(tal + j), (unsigned long long)c);
-            real += c;
-            c = 0u;
-        }
-    }
-    if (e.nnull) atomicAdd(reinterpret_cast<unsigned long long *>(tal + L),
-                           (unsigned long long)e.nnull);
+    flush_tally(p, tb, aval, e.nnull);
     atomicAdd(&p.hdr->flights, (unsigned long long)(e.nf - nf0));
     atomicAdd(&p.hdr->real, (unsigned long long)(e.nreal - nr0));
     atomicAdd(&p.hdr->nul, (unsigned long long)e.nnull);

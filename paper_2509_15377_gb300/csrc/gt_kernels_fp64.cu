@@ -52,11 +52,9 @@ cudaError_t launch_plain_fp64(const RunParams &p, const PlainArgs &a, int block,
 template <int FK>
 static cudaError_t configure_one(size_t max_smem)
 {
-    cudaError_t e = cudaFuncSetAttribute(k_batched<Fp64Electron, FK, false, kMaxThreads64>,
-                                         cudaFuncAttributeMaxDynamicSharedMemorySize, (int)max_smem);
+    cudaError_t e = allow_dynamic_smem(k_batched<Fp64Electron, FK, false, kMaxThreads64>, max_smem);
     if (e != cudaSuccess) return e;
-    return cudaFuncSetAttribute(k_plain_transport<Fp64Electron, FK, false, kMaxThreads64>,
-                                cudaFuncAttributeMaxDynamicSharedMemorySize, (int)max_smem);
+    return allow_dynamic_smem(k_plain_transport<Fp64Electron, FK, false, kMaxThreads64>, max_smem);
 }
 
 cudaError_t configure_fp64(size_t max_smem)

@@ -6,13 +6,25 @@
 
 namespace gt {
 
-constexpr int kMaxThreadsMixed = 512;
+// The batched kernel is built for three launch bounds: more resident warps
+// per SM against fewer registers per thread (the FP32 table in shared
+// memory limits an SM to one CTA).
+constexpr int kMaxThreadsMixed = 1024;
+constexpr int kPlainThreadsMixed = 512;
+
+template <int FK, bool TAB, int MAXT>
+static cudaError_t batched_t(const RunParams &p, int grid, int block, size_t smem, cudaStream_t s)
+{
+    k_batched<MixedElectron, FK, TAB, MAXT><<<grid, block, smem, s>>>(p);
+    return cudaGetLastError();
+}
 
 template <int FK, bool TAB>
 static cudaError_t batched(const RunParams &p, int grid, int block, size_t smem, cudaStream_t s)
 {
-    k_batched<MixedElectron, FK, TAB, kMaxThreadsMixed><<<grid, block, smem, s>>>(p);
-    return cudaGetLastError();
+    if (block <= 512) return batched_t<FK, TAB, 512>(p, grid, block, smem, s);
+    if (block <= 768) return batched_t<FK, TAB, 768>(p, grid, block, smem, s);
+    return batched_t<FK, TAB, 1024>(p, grid, block, smem, s);
 }
 
 template <int FK, bool TAB>
@@ -21,7 +33,7 @@ static cudaError_t plain(const RunParams &p, const PlainArgs &a, int block, size
 {
     const long long n = a.n_active;
     if (n <= 0) return cudaSuccess;
-    k_plain_transport<MixedElectron, FK, TAB, kMaxThreadsMixed>
+    k_plain_transport<MixedElectron, FK, TAB, kPlainThreadsMixed>
         <<<(unsigned)((n + block - 1) / block), block, smem, s>>>(p, a.cur, n, a.fresh, a.parity,
                                                                   a.aval);
     return cudaGetLastError();
@@ -66,11 +78,15 @@ cudaError_t launch_plain_mixed(const RunParams &p, const PlainArgs &a, bool smem
 template <int FK, bool TAB>
 static cudaError_t configure_one(size_t max_smem)
 {
-    cudaError_t e = cudaFuncSetAttribute(k_batched<MixedElectron, FK, TAB, kMaxThreadsMixed>,
-                                         cudaFuncAttributeMaxDynamicSharedMemorySize, (int)max_smem);
-    if (e != cudaSuccess) return e;
-    return cudaFuncSetAttribute(k_plain_transport<MixedElectron, FK, TAB, kMaxThreadsMixed>,
-                                cudaFuncAttributeMaxDynamicSharedMemorySize, (int)max_smem);
+    cudaError_t e;
+    if ((e = allow_dynamic_smem(k_batched<MixedElectron, FK, TAB, 512>, max_smem)) != cudaSuccess)
+        return e;
+    if ((e = allow_dynamic_smem(k_batched<MixedElectron, FK, TAB, 768>, max_smem)) != cudaSuccess)
+        return e;
+    if ((e = allow_dynamic_smem(k_batched<MixedElectron, FK, TAB, 1024>, max_smem)) != cudaSuccess)
+        return e;
+    return allow_dynamic_smem(k_plain_transport<MixedElectron, FK, TAB, kPlainThreadsMixed>,
+                              max_smem);
 }
 
 template <bool TAB>
@@ -96,10 +112,17 @@ template <int FK, bool TAB>
 static int occ(int block, size_t smem)
 {
     int n = 0;
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(
-            &n, k_batched<MixedElectron, FK, TAB, kMaxThreadsMixed>, block, smem) != cudaSuccess)
-        return 0;
-    return n;
+    cudaError_t e;
+    if (block <= 512)
+        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_batched<MixedElectron, FK, TAB, 512>,
+                                                          block, smem);
+    else if (block <= 768)
+        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_batched<MixedElectron, FK, TAB, 768>,
+                                                          block, smem);
+    else
+        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_batched<MixedElectron, FK, TAB, 1024>,
+                                                          block, smem);
+    return e == cudaSuccess ? n : 0;
 }
 
 template <bool TAB>

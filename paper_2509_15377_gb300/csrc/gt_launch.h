@@ -8,6 +8,22 @@
 
 namespace gt {
 
+// Static shared memory of the transport kernels stays below this; the
+// dynamic part (tallies and table) may use the rest of a CTA's opt-in size.
+constexpr size_t kStaticSmemReserve = 4096;
+
+// Let a kernel use all the dynamic shared memory a CTA may have beyond the
+// kernel's own static shared memory.
+template <typename F>
+inline cudaError_t allow_dynamic_smem(F *kernel, size_t optin)
+{
+    cudaFuncAttributes a;
+    cudaError_t e = cudaFuncGetAttributes(&a, kernel);
+    if (e != cudaSuccess) return e;
+    const size_t dyn = optin > a.sharedSizeBytes ? optin - a.sharedSizeBytes : 0;
+    return cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)dyn);
+}
+
 struct SeedArgs {
     const double *x, *y, *z, *t, *e, *dx, *dy, *dz;
     const int32_t *aval;

@@ -120,8 +120,8 @@ def test_fp64_batched_equals_plain_bitwise(av):
 def test_batched_runs_are_reproducible(av):
     w = W.plate_batched(n_avalanches=64, seed=13)
     _setup(av, w)
-    _, a = run_gpu(av, w, seed=13, precision=A.GT_MIXED, capacity=400000)
-    _, b = run_gpu(av, w, seed=13, precision=A.GT_MIXED, capacity=400000)
+    _, a = run_gpu(av, w, seed=13, precision=A.GT_MIXED, capacity=4_000_000)
+    _, b = run_gpu(av, w, seed=13, precision=A.GT_MIXED, capacity=4_000_000)
     ga, gb = by_uid(a), by_uid(b)
     for k in ("uid", "status", "n_flight", "x1", "z1", "t1", "e1"):
         assert np.array_equal(ga[k], gb[k]), k
