@@ -182,20 +182,20 @@ def run_ours(args) -> None:
     av.set_field(w.field)
     prim_dev = av.primaries_device(w.primaries)
     opt = A.RunOptions(seed=seed, t_max=w.t_max, precision=A.GT_MIXED, mode=A.GT_BATCHED,
-                       block=args.block, flights_per_round=args.flights_per_round)
+                       block=args.block, refill_period=args.refill_period)
     cap = args.capacity
     stream = torch.cuda.current_stream(dev)
     flush = torch.empty(256 * 1024 * 1024, dtype=torch.uint8, device=dev)  # > 129 MB L2
     tune = None
-    if not args.no_autotune and not (args.block or args.flights_per_round):
+    if not args.no_autotune and not (args.block or args.refill_period):
         # launch shape chosen by the library's autotuner on a sample of the
         # workload (outside the timed region); later runs use it
         sample = w.primaries.subset(list(range(min(args.tune_avalanches, args.avalanches))))
         best, pts = av.autotune(av.primaries_device(sample), opt, cap, stream=stream)
         tune = {"best": best, "sample_avalanches": args.tune_avalanches,
-                "points": [[q["block"], q["flights_per_round"], round(q["real_per_ms"] / 1e6, 4)]
-                           for q in pts],
-                "points_unit": "[block, flights_per_round, 1e9 real collisions/s]"}
+                "points": [[q["block"], q["refill_period"], q["flights_per_phase"],
+                            round(q["real_per_ms"] / 1e6, 4)] for q in pts],
+                "points_unit": "[block, refill_period, flights_per_phase, 1e9 real collisions/s]"}
 
     def step(prim):
         flush.fill_(1)
@@ -310,7 +310,8 @@ def run_ours(args) -> None:
                    "field_kv_cm": [30, 50], "primaries_mean": 3, "gap_um": 128,
                    "gas": "argon-like 12-level", "precision": "mixed", "mode": "batched",
                    "block": stats[-1]["block"], "grid": stats[-1]["grid"],
-                   "flights_per_round": stats[-1]["flights_per_round"],
+                   "refill_period": stats[-1]["refill_period"],
+                   "flights_per_phase": stats[-1]["flights_per_phase"],
                    "autotune": tune,
                    "l2": "flushed (256 MB write) before every step"},
         "flights_per_s": sum_over_ranks(float(flights), dev) / t_max_rank,
@@ -359,7 +360,7 @@ def run_calibration(args) -> None:
     av.set_field(w.field)
     prim = av.primaries_device(w.primaries)
     opt = A.RunOptions(seed=0, coll_limit=w.coll_limit, precision=A.GT_MIXED, mode=A.GT_BATCHED,
-                       block=args.block, flights_per_round=args.flights_per_round)
+                       block=args.block, refill_period=args.refill_period)
     for _ in range(max(1, args.steps)):
         st = av.run(prim, opt, threads, allow=(A.GT_OK,))
     torch.cuda.synchronize()
@@ -412,7 +413,7 @@ def parse(argv=None):
     ap.add_argument("--avalanches", type=int, default=4096)
     ap.add_argument("--capacity", type=int, default=100_000_000)
     ap.add_argument("--block", type=int, default=0)
-    ap.add_argument("--flights-per-round", type=int, default=0)
+    ap.add_argument("--refill-period", type=int, default=0)
     ap.add_argument("--cpu-avalanches", type=int, default=64)
     ap.add_argument("--plain-avalanches", type=int, default=32)
     ap.add_argument("--no-cpu-baseline", action="store_true")

@@ -142,8 +142,10 @@ typedef struct {
     int32_t precision;                /* GT_FP64 / GT_MIXED */
     int32_t mode;                     /* GT_BATCHED / GT_PLAIN */
     int32_t block;                    /* threads per CTA, 0 = default */
-    int32_t flights_per_round;        /* BATCHED: flights between queue refills
-                                         and FP64 flushes, 0 = default */
+    int32_t refill_period;            /* BATCHED: steps between refills of idle lanes
+                                         from the queue (and FP32-to-FP64 flushes):
+                                         FP64 one flight per step, MIXED one
+                                         collision round per step; 0 = default */
     int32_t grid;                     /* BATCHED: CTAs, 0 = one per SM */
     uint64_t size_limit;              /* BATCHED: max electrons per avalanche,
                                          further secondaries dropped; 0 = none */
@@ -151,7 +153,11 @@ typedef struct {
                                          60 s; exceeded -> GT_ERR_TIMEOUT */
     double time_limit_ms;             /* whole-run budget, 0 = 600 s */
     int32_t debug_flags;              /* GT_DEBUG_*, 0 in normal use */
-    int32_t reserved;
+    int32_t flights_per_phase;        /* BATCHED MIXED: a collision round lets each
+                                         lane fly up to this many flights until it
+                                         meets a real collision, then the warp
+                                         applies its lanes' collisions together;
+                                         0 = default */
 } gt_run;
 
 /* Fault injection for tests: reserve one queue slot that is never filled,
@@ -190,7 +196,9 @@ typedef struct {
     int32_t launches;         /* kernels launched by the run */
     int32_t iterations;       /* PLAIN: generations summed over avalanches */
     int32_t status;           /* same value as the return code */
-    int32_t block, flights_per_round, grid; /* launch shape actually used */
+    int32_t block, refill_period, grid; /* launch shape actually used */
+    int32_t flights_per_phase;
+    int32_t pad;
 } gt_stats;
 
 /* ---- entry points ---------------------------------------------------- */
@@ -255,13 +263,16 @@ int avalanche_run(gt_ctx *ctx, const gt_run *run, const gt_endpoints *out, void 
  * per candidate shape (after one warm-up run) and measures real collisions
  * per millisecond of transport kernel time (CUDA events).  The fastest
  * shape is remembered by the context for the run's precision and field
- * kind, and used by later runs that leave block / flights_per_round at 0.
+ * kind, and used by later runs that leave block / refill_period /
+ * flights_per_phase at 0.
  * points (may be NULL) receives up to max_points measurements, *n_points
  * their number; *best the chosen shape.  Errors as avalanche_run; a
  * candidate that fails is skipped. */
 typedef struct {
     int32_t block;
-    int32_t flights_per_round;
+    int32_t refill_period;
+    int32_t flights_per_phase;
+    int32_t pad;
     double real_per_ms;
     double transport_ms;
 } gt_tune_point;

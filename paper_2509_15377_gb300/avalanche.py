@@ -60,10 +60,10 @@ class gt_run(C.Structure):
                 ("aval", C.c_void_p), ("uid", C.c_void_p), ("aval_field", C.c_void_p),
                 ("seed", C.c_uint64), ("t_max", C.c_double), ("coll_limit", C.c_uint32),
                 ("precision", C.c_int32), ("mode", C.c_int32), ("block", C.c_int32),
-                ("flights_per_round", C.c_int32), ("grid", C.c_int32),
+                ("refill_period", C.c_int32), ("grid", C.c_int32),
                 ("size_limit", C.c_uint64), ("spin_limit_ms", C.c_double),
                 ("time_limit_ms", C.c_double), ("debug_flags", C.c_int32),
-                ("reserved", C.c_int32)]
+                ("flights_per_phase", C.c_int32)]
 
 
 _EP_ARRAYS = ("x0", "y0", "z0", "t0", "e0", "x1", "y1", "z1", "t1", "e1", "status", "aval",
@@ -80,14 +80,16 @@ class gt_stats(C.Structure):
                 ("real_collisions", C.c_uint64), ("null_collisions", C.c_uint64),
                 ("flights", C.c_uint64), ("transport_ms", C.c_double),
                 ("launches", C.c_int32), ("iterations", C.c_int32), ("status", C.c_int32),
-                ("block", C.c_int32), ("flights_per_round", C.c_int32), ("grid", C.c_int32)]
+                ("block", C.c_int32), ("refill_period", C.c_int32), ("grid", C.c_int32),
+                ("flights_per_phase", C.c_int32), ("pad", C.c_int32)]
 
     def as_dict(self) -> dict:
-        return {k: getattr(self, k) for k, _ in self._fields_}
+        return {k: getattr(self, k) for k, _ in self._fields_ if k != "pad"}
 
 
 class gt_tune_point(C.Structure):
-    _fields_ = [("block", C.c_int32), ("flights_per_round", C.c_int32),
+    _fields_ = [("block", C.c_int32), ("refill_period", C.c_int32),
+                ("flights_per_phase", C.c_int32), ("pad", C.c_int32),
                 ("real_per_ms", C.c_double), ("transport_ms", C.c_double)]
 
     def as_dict(self) -> dict:
@@ -239,7 +241,8 @@ class RunOptions:
     precision: int = GT_MIXED
     mode: int = GT_BATCHED
     block: int = 0
-    flights_per_round: int = 0
+    refill_period: int = 0
+    flights_per_phase: int = 0
     grid: int = 0
     size_limit: int = 0
     spin_limit_ms: float = 0.0
@@ -370,7 +373,8 @@ class Avalanche:
         r.precision = opt.precision
         r.mode = opt.mode
         r.block = opt.block
-        r.flights_per_round = opt.flights_per_round
+        r.refill_period = opt.refill_period
+        r.flights_per_phase = opt.flights_per_phase
         r.grid = opt.grid
         r.size_limit = opt.size_limit
         r.spin_limit_ms = opt.spin_limit_ms

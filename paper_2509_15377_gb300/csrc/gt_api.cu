@@ -34,6 +34,7 @@ struct gt_ctx {
     // autotuned batched launch shape per [precision][field kind] (0 = none)
     int tuned_block[2][4] = {{0}};
     int tuned_k[2][4] = {{0}};
+    int tuned_m[2][4] = {{0}};
     char last_error[256] = {0};
 };
 
@@ -384,7 +385,8 @@ static int validate_run(gt_ctx *ctx, const gt_run *r, const gt_endpoints *o, voi
     if (r->precision != GT_FP64 && r->precision != GT_MIXED) return GT_ERR_ARG;
     if (r->mode != GT_BATCHED && r->mode != GT_PLAIN) return GT_ERR_ARG;
     if (!std::isfinite(r->t_max)) return GT_ERR_ARG;
-    if (r->block < 0 || r->flights_per_round < 0 || r->grid < 0) return GT_ERR_ARG;
+    if (r->block < 0 || r->refill_period < 0 || r->grid < 0 || r->flights_per_phase < 0)
+        return GT_ERR_ARG;
     if (r->block && (r->block % 32 != 0 ||
                      r->block > (r->precision == GT_FP64 ? max_block_fp64() : max_block_mixed())))
         return GT_ERR_ARG;
@@ -456,8 +458,11 @@ int avalanche_run(gt_ctx *ctx, const gt_run *r, const gt_endpoints *o, void *ws,
     p.coll_limit = r->coll_limit;
     const int prec_i = r->precision == GT_FP64 ? 0 : 1;
     const int tuned_k = ctx->tuned_k[prec_i][ctx->field.kind & 3];
-    p.flights_per_round = r->flights_per_round > 0 ? r->flights_per_round
-                                                   : (tuned_k > 0 ? tuned_k : 32);
+    const int tuned_m = ctx->tuned_m[prec_i][ctx->field.kind & 3];
+    p.refill_period = r->refill_period > 0 ? r->refill_period
+                                           : (tuned_k > 0 ? tuned_k : (prec_i ? 8 : 32));
+    p.flights_per_phase = r->flights_per_phase > 0 ? r->flights_per_phase
+                                                   : (tuned_m > 0 ? tuned_m : 6);
     p.size_limit = r->size_limit;
     p.spin_limit_ns = (long long)((r->spin_limit_ms > 0 ? r->spin_limit_ms : 60000.0) * 1e6);
     p.time_limit_ns = (long long)((r->time_limit_ms > 0 ? r->time_limit_ms : 600000.0) * 1e6);
@@ -525,7 +530,7 @@ int avalanche_run(gt_ctx *ctx, const gt_run *r, const gt_endpoints *o, void *ws,
     int iterations = 0, grid = 0;
     unsigned host_err = 0;  // aborts decided on the host (plain mode)
     double transport_ms = 0.0;
-    const int K = p.flights_per_round;
+    const int K = p.refill_period;
 
     if (r->mode == GT_BATCHED) {
         const int occ = fp64 ? occupancy_batched_fp64(ctx->field.kind, block, smem)
@@ -637,8 +642,9 @@ int avalanche_run(gt_ctx *ctx, const gt_run *r, const gt_endpoints *o, void *ws,
         stats->iterations = iterations;
         stats->status = rc;
         stats->block = block;
-        stats->flights_per_round = K;
+        stats->refill_period = K;
         stats->grid = grid;
+        stats->flights_per_phase = p.flights_per_phase;
     }
     return rc;
 }
@@ -651,38 +657,51 @@ int gt_autotune(gt_ctx *ctx, const gt_run *run, const gt_endpoints *out, void *w
     gt_run r = *run;
     r.mode = GT_BATCHED;
     const bool fp64 = r.precision == GT_FP64;
-    static const int blocks_mixed[] = {512, 640, 768, 1024};
+    // candidate shapes: threads per CTA x refill period (x flights per phase)
+    static const int blocks_mixed[] = {512, 768, 1024};
     static const int blocks_fp64[] = {128, 256, 512};
-    static const int ks[] = {8, 16, 32, 64};
+    static const int ks_mixed[] = {2, 4, 8, 16};
+    static const int ks_fp64[] = {8, 16, 32, 64};
+    static const int ms_mixed[] = {4, 6, 8};
+    static const int ms_fp64[] = {1};
     const int *blocks = fp64 ? blocks_fp64 : blocks_mixed;
-    const int nb = fp64 ? 3 : 4;
+    const int *ks = fp64 ? ks_fp64 : ks_mixed;
+    const int *ms = fp64 ? ms_fp64 : ms_mixed;
+    const int nb = 3, nk = 4, nm = fp64 ? 1 : 3;
     gt_stats st{};
     r.block = blocks[0];
-    r.flights_per_round = 32;
+    r.refill_period = ks[1];
+    r.flights_per_phase = ms[0];
     int rc = avalanche_run(ctx, &r, out, ws, ws_bytes, stream, &st);  // warm-up
     if (rc != GT_OK) return rc;
     int n = 0;
-    gt_tune_point top{0, 0, 0.0, 0.0};
+    gt_tune_point top{0, 0, 0, 0, 0.0, 0.0};
     for (int bi = 0; bi < nb; ++bi) {
-        for (int k : ks) {
-            r.block = blocks[bi];
-            r.flights_per_round = k;
-            if (avalanche_run(ctx, &r, out, ws, ws_bytes, stream, &st) != GT_OK) continue;
-            gt_tune_point pt;
-            pt.block = r.block;
-            pt.flights_per_round = k;
-            pt.transport_ms = st.transport_ms;
-            pt.real_per_ms = st.transport_ms > 0 ? (double)st.real_collisions / st.transport_ms : 0.0;
-            if (points && n < max_points) points[n] = pt;
-            ++n;
-            if (pt.real_per_ms > top.real_per_ms) top = pt;
+        for (int ki = 0; ki < nk; ++ki) {
+            for (int mi = 0; mi < nm; ++mi) {
+                r.block = blocks[bi];
+                r.refill_period = ks[ki];
+                r.flights_per_phase = ms[mi];
+                if (avalanche_run(ctx, &r, out, ws, ws_bytes, stream, &st) != GT_OK) continue;
+                gt_tune_point pt;
+                pt.block = r.block;
+                pt.refill_period = r.refill_period;
+                pt.flights_per_phase = r.flights_per_phase;
+                pt.transport_ms = st.transport_ms;
+                pt.real_per_ms =
+                    st.transport_ms > 0 ? (double)st.real_collisions / st.transport_ms : 0.0;
+                if (points && n < max_points) points[n] = pt;
+                ++n;
+                if (pt.real_per_ms > top.real_per_ms) top = pt;
+            }
         }
     }
     if (n_points) *n_points = n;
     if (top.block == 0) return GT_ERR_UNSUPPORTED;
     const int pi = fp64 ? 0 : 1;
     ctx->tuned_block[pi][ctx->field.kind & 3] = top.block;
-    ctx->tuned_k[pi][ctx->field.kind & 3] = top.flights_per_round;
+    ctx->tuned_k[pi][ctx->field.kind & 3] = top.refill_period;
+    ctx->tuned_m[pi][ctx->field.kind & 3] = top.flights_per_phase;
     *best = top;
     return GT_OK;
 }

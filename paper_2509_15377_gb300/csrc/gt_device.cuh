@@ -108,7 +108,8 @@ struct RunParams {
     uint64_t seed;
     double t_max;
     uint32_t coll_limit;
-    int flights_per_round;
+    int refill_period;  // batched: collision rounds between queue refills
+    int flights_per_phase;  // batched mixed: flights before a warp's collisions
     uint64_t size_limit;
     long long spin_limit_ns, time_limit_ns;
     int n_avalanches;
@@ -426,14 +427,78 @@ __device__ __forceinline__ void isotropic32(float u, float v, float &nx, float &
     nx = sr * c; ny = sr * s; nz = ct;
 }
 
-// New electron produced by an ionising collision.
-struct Child {
-    double x, y, z, t, e, vx, vy, vz;
-    uint64_t uid;
-};
+// Store the birth record of a new electron in queue slot s: position and
+// time are the parent's at the ionising collision (read from the parent),
+// energy, velocity and id from the child record.
+template <class E, class C>
+__device__ __forceinline__ void store_birth(const RunParams &p, int64_t s, const E &parent,
+                                            const C &c)
+{
+    parent.position(p.x0[s], p.y0[s], p.z0[s], p.t0[s]);
+    p.e0[s] = (double)c.e;
+    p.bvx[s] = (double)c.vx; p.bvy[s] = (double)c.vy; p.bvz[s] = (double)c.vz;
+    p.uid[s] = c.uid;
+    p.aval[s] = parent.aval;
+    p.status[s] = 0;
+}
+
+// Below-threshold test of an inelastic level in FP64 from the FP32 velocity.
+// Kept out of line so that the compiler cannot hoist this rare test (it is
+// reached only inside the FP32 margin) into every flight: FP64 instructions
+// issue at 1/64 of the FP32 rate on GB300.
+static __device__ __noinline__ bool below_threshold64(float vx, float vy, float vz, double thr)
+{
+    const double e64 = ((double)vx * vx + (double)vy * vy + (double)vz * vz) * kInvTwoAccel;
+    return e64 < thr;
+}
+
+// The FP64 time-limit decision of a flight that ends near t_max: x = the
+// flight time, truncated to reach t_max exactly if T + ot + dt > t_max;
+// y = 1 if truncated.  Out of line for the same reason: nvcc turns a short
+// rarely-taken branch into predicated code that issues on every flight.
+static __device__ __noinline__ float2 time_cut64(double T, float ot, float dt, double t_max)
+{
+    if (T + (double)(ot + dt) > t_max)
+        return make_float2(fmaxf((float)((t_max - T) - (double)ot), 0.0f), 1.0f);
+    return make_float2(dt, 0.0f);
+}
+
+// FP64 boundary test of the position X + o (same role as above: only
+// reached when the FP32 pre-test falls inside its margin).
+template <int FK>
+static __device__ __noinline__ int boundary_confirm64(double X, double Y, double Z, float ox,
+                                                      float oy, float oz, double gap,
+                                                      double wire_r2, double tube_r2,
+                                                      double lo0, double lo1, double lo2,
+                                                      double hi0, double hi1, double hi2)
+{
+    const double x = X + (double)ox, y = Y + (double)oy, z = Z + (double)oz;
+    if (FK == GT_FIELD_PLATE) {
+        if (z >= gap) return GT_ST_ANODE;
+        if (z < 0.0) return GT_ST_CATHODE;
+    } else if (FK == GT_FIELD_COAX) {
+        const double r2 = x * x + y * y;
+        if (r2 <= wire_r2) return GT_ST_WIRE;
+        if (r2 >= tube_r2) return GT_ST_TUBE;
+    } else if (FK == GT_FIELD_GRID) {
+        const double r2 = x * x + y * y;
+        if (wire_r2 > 0.0 && r2 <= wire_r2) return GT_ST_WIRE;
+        if (x < lo0 || x > hi0 || y < lo1 || y > hi1 || z < lo2 || z > hi2)
+            return GT_ST_OUT_OF_MAP;
+    }
+    return 0;
+}
 
 // ============================================================ FP64 electron
 struct Fp64Electron {
+    static constexpr bool kTwoPhase = false;
+    // New electron produced by an ionising collision (the parent supplies
+    // its position and time).
+    struct ChildT {
+        double e, vx, vy, vz;
+        uint64_t uid;
+    };
+
     double x, y, z, t, vx, vy, vz;
     double plate_e;
     uint32_t nf, nreal, nnull;
@@ -441,6 +506,11 @@ struct Fp64Electron {
     int aval;
     uint64_t uid;
     int64_t slot;
+
+    __device__ __forceinline__ void position(double &ox_, double &oy_, double &oz_, double &ot_) const
+    {
+        ox_ = x; oy_ = y; oz_ = z; ot_ = t;
+    }
 
     template <int FK>
     __device__ void load_birth(const RunParams &p, int64_t s)
@@ -462,8 +532,10 @@ struct Fp64Electron {
         return status ? EV_RETIRE : EV_NONE;
     }
 
+    // One flight and its collision (Fig. 2: "Find E field and add random
+    // time step", "Collision?", "ionisation or attachment?").
     template <int FK>
-    __device__ __forceinline__ int fly(const RunParams &p, const Tables &tb, Child &ch)
+    __device__ __forceinline__ int fly(const RunParams &p, const Tables &tb, ChildT &ch)
     {
         if (nf == 0xFFFFFFFFu) {
             status = GT_ST_FLIGHT_LIMIT;
@@ -528,7 +600,7 @@ struct Fp64Electron {
                 double sx, sy, sz;
                 isotropic64(u01d(w2.y), u01d(w2.z), sx, sy, sz);
                 const double ss = sqrt(kTwoAccel * es);
-                ch.x = x; ch.y = y; ch.z = z; ch.t = t; ch.e = es;
+                ch.e = es;
                 ch.vx = ss * sx; ch.vy = ss * sy; ch.vz = ss * sz;
                 ch.uid = child_uid(uid, flight);
                 ev = EV_CHILD;
@@ -539,7 +611,7 @@ struct Fp64Electron {
         ++nreal;
         if (p.coll_limit && nreal >= p.coll_limit) {
             status = GT_ST_COLL_LIMIT;
-            return ev == EV_CHILD ? (EV_CHILD | EV_RETIRE) : EV_RETIRE;
+            return ev | EV_RETIRE;
         }
         return ev;
     }
@@ -577,19 +649,39 @@ struct Fp64Electron {
 };
 
 // ===================================================== mixed-precision electron
+// The step is split in two so that a warp can handle its lanes' real
+// collisions together: advance() makes one free flight and the null test
+// against the interpolated total rate; a lane that meets a real collision
+// keeps its random words (`pending`) until collide() selects the level and
+// scatters.  Each electron still takes exactly the sequence
+// flight, collision, flight, ... with the same random numbers.
 struct MixedElectron {
+    static constexpr bool kTwoPhase = true;
+    struct ChildT {
+        float e, vx, vy, vz;
+        uint64_t uid;
+    };
+
     double X, Y, Z, T;       // FP64 absolute position and time at the last flush
     float ox, oy, oz, ot;    // FP32 offsets since the last flush
     float vx, vy, vz;        // FP32 velocity
     float px, py, pz;        // FP32 copy of (X, Y, Z) for field and pre-tests
     float zhi, zlo, tlim;    // pre-test limits for the offsets (see flush)
     float plate_e;
+    float pR;                // pending collision: R = u1 nu_max
+    uint32_t pw2, pw3;       // pending collision: direction words
     uint32_t nf, nreal, nnull;
     int status;
     int aval;
-    bool timed;
+    bool timed, pending;
     uint64_t uid;
     int64_t slot;
+
+    __device__ __forceinline__ void position(double &x_, double &y_, double &z_, double &t_) const
+    {
+        x_ = X + (double)ox; y_ = Y + (double)oy; z_ = Z + (double)oz;
+        t_ = T + (double)ot;
+    }
 
     // Fold the FP32 offsets into the FP64 state and refresh the FP32
     // pre-test limits: an offset beyond a limit is re-tested in FP64.
@@ -598,9 +690,12 @@ struct MixedElectron {
     {
         X += (double)ox; Y += (double)oy; Z += (double)oz; T += (double)ot;
         ox = oy = oz = ot = 0.f;
-        px = (float)X; py = (float)Y; pz = (float)Z;
+        if (FK == GT_FIELD_COAX || FK == GT_FIELD_GRID) {
+            px = (float)X; py = (float)Y;
+        }
+        if (FK == GT_FIELD_GRID) pz = (float)Z;
         if (FK == GT_FIELD_PLATE) {
-            const float hi = (float)(p.field.gap - Z), lo = (float)(-Z);
+            const float hi = (float)(p.field.gap - Z), lo = -(float)Z;
             zhi = hi - (fabsf(hi) * 1e-6f + 1e-12f);
             zlo = lo + (fabsf(lo) * 1e-6f + 1e-12f);
         }
@@ -623,7 +718,7 @@ struct MixedElectron {
         plate_e = (float)(p.aval_field ? p.aval_field[aval] : p.field.e0);
         nf = nreal = nnull = 0;
         status = 0;
-        timed = false;
+        timed = pending = false;
         ox = oy = oz = ot = 0.f;
         flush<FK>(p);
     }
@@ -658,24 +753,28 @@ struct MixedElectron {
             }
         }
         if (!maybe) return 0;
-        return boundary64<FK>(p.field, X + (double)ox, Y + (double)oy, Z + (double)oz);
+        const DevField &f = p.field;
+        return boundary_confirm64<FK>(X, Y, Z, ox, oy, oz, f.gap, f.wire_r2, f.tube_r2,
+                                      f.origin[0], f.origin[1], f.origin[2], f.hi[0], f.hi[1],
+                                      f.hi[2]);
     }
 
+    // One free flight and the real/null decision (Fig. 2 "Find E field and
+    // add random time step", "Collision?").  Returns EV_RETIRE or EV_NONE;
+    // sets `pending` for a real collision.
     template <int FK>
-    __device__ __forceinline__ int fly(const RunParams &p, const Tables &tb, Child &ch)
+    __device__ __forceinline__ int advance(const RunParams &p, const Tables &tb)
     {
         if (nf == 0xFFFFFFFFu) {
             status = GT_ST_FLIGHT_LIMIT;
             return EV_RETIRE;
         }
-        const uint32_t flight = nf;
-        const uint4 w = draw(p.seed, aval, uid, flight, 0u);
+        const uint4 w = draw(p.seed, aval, uid, nf, 0u);
         float dt = -__logf(u01f(w.x)) * p.gas.inv_nu_max_f;
         if (ot + dt >= tlim) {  // near the time limit: decide in FP64
-            if (T + (double)(ot + dt) > p.t_max) {
-                dt = fmaxf((float)((p.t_max - T) - (double)ot), 0.0f);
-                timed = true;
-            }
+            const float2 c = time_cut64(T, ot, dt, p.t_max);
+            dt = c.x;
+            timed = c.y != 0.0f;
         }
         float ex, ey, ez;
         field32<FK>(p.field, plate_e, px + ox, py + oy, pz + oz, ex, ey, ez);
@@ -691,7 +790,7 @@ struct MixedElectron {
             lorentz_step<float>(p.field.w_f, ax, ay, az, dt, vx, vy, vz, dx, dy, dz);
         }
         ox += dx; oy += dy; oz += dz; ot += dt;
-        nf = flight + 1u;
+        ++nf;
         const int st = boundary<FK>(p);
         if (st) {
             status = st;
@@ -701,34 +800,56 @@ struct MixedElectron {
             status = GT_ST_TIME;
             return EV_RETIRE;
         }
+        // null test against the interpolated total rate
+        const float eps = (vx * vx + vy * vy + vz * vz) * kInvTwoAccelF;
+        const float R = u01f(w.y) * p.gas.nu_max_f;
+        const float xk = eps * p.gas.inv_d_eps_f;
+        const float tk = __fadd_rd(fminf(xk, p.gas.lastk_f), 8388608.0f);
+        const int k = __float_as_int(tk) - 0x4B000000;
+        const float f = fminf(xk, p.gas.last_x_f) - (tk - 8388608.0f);
+        const int L = p.gas.n_levels;
+        const float *c0 = tb.cum32 + k * tb.stride32 + (L - 1);
+        const float top = fmaf(f, c0[tb.stride32] - c0[0], c0[0]);
+        if (R < top) {
+            pending = true;
+            pR = R;
+            pw2 = w.z;
+            pw3 = w.w;
+        } else {
+            ++nnull;
+        }
+        return EV_NONE;
+    }
+
+    // The pending real collision (Fig. 2 "Collision is ionisation or
+    // attachment?"): level selection, threshold guard, isotropic scattering.
+    template <int FK>
+    __device__ __forceinline__ int collide(const RunParams &p, const Tables &tb, ChildT &ch)
+    {
+        pending = false;
         const float eps = (vx * vx + vy * vy + vz * vz) * kInvTwoAccelF;
         int lvl = select_level32(tb.cum32, tb.stride32, p.gas.n_levels, p.gas.lastk_f,
-                                 p.gas.last_x_f, p.gas.inv_d_eps_f, eps,
-                                 u01f(w.y) * p.gas.nu_max_f);
-        if (lvl >= 0 && tb.type[lvl] != GT_LEVEL_ELASTIC) {
+                                 p.gas.last_x_f, p.gas.inv_d_eps_f, eps, pR);
+        if (lvl < 0) lvl = p.gas.n_levels - 1;  // R was below the total rate
+        const int type = tb.type[lvl];
+        if (type != GT_LEVEL_ELASTIC) {
             const float th = tb.thr_f[lvl];
-            if (eps < th * (1.0f - 1e-6f)) {
-                lvl = -1;
-            } else if (eps < th * (1.0f + 1e-6f)) {  // within the margin: FP64 test
-                const double e64 = ((double)vx * vx + (double)vy * vy + (double)vz * vz) *
-                                   kInvTwoAccel;
-                if (e64 < tb.thr[lvl]) lvl = -1;
+            if (eps < th * (1.0f + 1e-6f)) {
+                if (eps < th * (1.0f - 1e-6f) || below_threshold64(vx, vy, vz, tb.thr[lvl])) {
+                    ++nnull;
+                    return EV_NONE;
+                }
             }
-        }
-        if (lvl < 0) {
-            ++nnull;
-            return EV_NONE;
         }
         tb.tally[lvl * blockDim.x + threadIdx.x] += 1u;
         float nx, ny, nz;
-        isotropic32(u01f(w.z), u01f(w.w), nx, ny, nz);
+        isotropic32(u01f(pw2), u01f(pw3), nx, ny, nz);
         float sp;
         int ev = EV_NONE;
-        const int type = tb.type[lvl];
         if (type == GT_LEVEL_ELASTIC) {
             // scale the speed itself: |v'| = |v| sqrt(1 - recoil (1 - cos chi));
             // a round trip through the energy would multiply by
-            // (2a)_f32 * (1/2a)_f32 != 1 at every collision and drift
+            // (2a)_f32 * (1/2a)_f32 != 1 at every collision and drift.
             // (cos chi only enters multiplied by recoil ~ 1e-5, so the
             // hardware rsqrt is accurate enough there)
             const float v2 = vx * vx + vy * vy + vz * vz;
@@ -737,16 +858,15 @@ struct MixedElectron {
         } else {
             float eps_new = fmaxf(eps - tb.thr_f[lvl], 0.0f);
             if (type == GT_LEVEL_IONISATION) {
+                const uint32_t flight = nf - 1u;
                 const uint4 w2 = draw(p.seed, aval, uid, flight, 1u);
                 const float es = u01f(w2.x) * eps_new;
                 eps_new = eps_new - es;
                 float sx, sy, sz;
                 isotropic32(u01f(w2.y), u01f(w2.z), sx, sy, sz);
                 const float ss = sqrtf(kTwoAccelF * es);
-                ch.x = X + (double)ox; ch.y = Y + (double)oy; ch.z = Z + (double)oz;
-                ch.t = T + (double)ot;
-                ch.e = (double)es;
-                ch.vx = (double)(ss * sx); ch.vy = (double)(ss * sy); ch.vz = (double)(ss * sz);
+                ch.e = es;
+                ch.vx = ss * sx; ch.vy = ss * sy; ch.vz = ss * sz;
                 ch.uid = child_uid(uid, flight);
                 ev = EV_CHILD;
             }
@@ -756,9 +876,18 @@ struct MixedElectron {
         ++nreal;
         if (p.coll_limit && nreal >= p.coll_limit) {
             status = GT_ST_COLL_LIMIT;
-            return ev == EV_CHILD ? (EV_CHILD | EV_RETIRE) : EV_RETIRE;
+            return ev | EV_RETIRE;
         }
         return ev;
+    }
+
+    // Flight and collision in one call (plain mode).
+    template <int FK>
+    __device__ __forceinline__ int fly(const RunParams &p, const Tables &tb, ChildT &ch)
+    {
+        const int ev = advance<FK>(p, tb);
+        if (ev || !pending) return ev;
+        return collide<FK>(p, tb, ch);
     }
 
     template <int FK>
@@ -795,7 +924,7 @@ struct MixedElectron {
         plate_e = (float)(p.aval_field ? p.aval_field[aval] : p.field.e0);
         nnull = 0;
         status = 0;
-        timed = false;
+        timed = pending = false;
         ox = oy = oz = ot = 0.f;
         flush<FK>(p);
     }

@@ -130,26 +130,17 @@ __device__ __forceinline__ void finish(const RunParams &p, const Tables &tb, con
     atomicAdd(&bs.nul, (unsigned long long)e.nnull);
 }
 
-// Write the birth record of a new electron into queue slot s.
-__device__ __forceinline__ void store_birth(const RunParams &p, int64_t s, const Child &c, int aval)
-{
-    p.x0[s] = c.x; p.y0[s] = c.y; p.z0[s] = c.z; p.t0[s] = c.t; p.e0[s] = c.e;
-    p.bvx[s] = c.vx; p.bvy[s] = c.vy; p.bvz[s] = c.vz;
-    p.uid[s] = c.uid;
-    p.aval[s] = aval;
-    p.status[s] = 0;
-}
-
 // Warp-collective append of the lanes' new electrons to the queue: ballot,
 // one atomic on the tail per warp, each lane's slot = base + its rank.
 // Returns the number of this lane's electrons dropped for lack of capacity
 // (they count as finished so that the queue can drain).
-__device__ __forceinline__ int push_children(const RunParams &p, bool want, const Child &ch,
-                                             int aval, int lane)
+template <class E>
+__device__ __forceinline__ int push_children(const RunParams &p, bool want, const E &parent,
+                                             const typename E::ChildT &ch, int lane)
 {
     bool ok = want;
     if (want && p.size_limit) {
-        const unsigned long long old = atomicAdd(p.created + aval, 1ull);
+        const unsigned long long old = atomicAdd(p.created + parent.aval, 1ull);
         if (old >= p.size_limit) {
             ok = false;
             atomicAdd(&p.hdr->dropped, 1ull);
@@ -168,7 +159,7 @@ __device__ __forceinline__ int push_children(const RunParams &p, bool want, cons
         atomicOr(&p.hdr->error, ERR_OVERFLOW);
         return 1;
     }
-    store_birth(p, (int64_t)s, ch, aval);
+    store_birth(p, (int64_t)s, parent, ch);
     __threadfence();
     st_release_u32(p.ready + s, 1u);
     return 0;
@@ -181,7 +172,7 @@ __global__ void __launch_bounds__(MAXT) k_batched(const RunParams p)
     __shared__ BlockState bs;
     const Tables tb = stage_tables<SMEM_TABLE>(p, smem, bs);
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
-    const int K = p.flights_per_round;
+    const int K = p.refill_period;
 
     E e;
     bool has = false;
@@ -251,17 +242,45 @@ __global__ void __launch_bounds__(MAXT) k_batched(const RunParams p)
             continue;
         }
 
-        // K flights per electron between refills
-        for (int k = 0; k < K; ++k) {
-            Child ch;
-            int ev = EV_NONE;
-            if (has) ev = e.template fly<FK>(p, tb, ch);
-            if (__any_sync(FULL, ev & EV_CHILD))
-                retired += push_children(p, (ev & EV_CHILD) != 0, ch, e.aval, lane);
-            if (ev & EV_RETIRE) {
-                finish(p, tb, e, bs);
-                has = false;
-                ++retired;
+        if constexpr (E::kTwoPhase) {
+            // K collision rounds between refills.  In each, lanes without a
+            // pending collision fly (at most M flights) until they meet a
+            // real one; then the warp applies its lanes' collisions together.
+            const int M = p.flights_per_phase;
+            for (int k = 0; k < K; ++k) {
+                for (int mm = 0; mm < M; ++mm) {
+                    const bool go = has && !e.pending;
+                    if (!__any_sync(FULL, go)) break;
+                    if (go && (e.template advance<FK>(p, tb) & EV_RETIRE)) {
+                        finish(p, tb, e, bs);
+                        has = false;
+                        ++retired;
+                    }
+                }
+                typename E::ChildT ch;
+                int ev = EV_NONE;
+                if (has && e.pending) ev = e.template collide<FK>(p, tb, ch);
+                if (__any_sync(FULL, ev & EV_CHILD))
+                    retired += push_children(p, (ev & EV_CHILD) != 0, e, ch, lane);
+                if (ev & EV_RETIRE) {
+                    finish(p, tb, e, bs);
+                    has = false;
+                    ++retired;
+                }
+            }
+        } else {
+            // K flights per electron between refills
+            for (int k = 0; k < K; ++k) {
+                typename E::ChildT ch;
+                int ev = EV_NONE;
+                if (has) ev = e.template fly<FK>(p, tb, ch);
+                if (__any_sync(FULL, ev & EV_CHILD))
+                    retired += push_children(p, (ev & EV_CHILD) != 0, e, ch, lane);
+                if (ev & EV_RETIRE) {
+                    finish(p, tb, e, bs);
+                    has = false;
+                    ++retired;
+                }
             }
         }
         if (has) e.template round_end<FK>(p);
@@ -297,7 +316,7 @@ __global__ void __launch_bounds__(MAXT)
     E e;
     e.template restore<FK>(p, cur, i, aval);
     const uint32_t nf0 = e.nf, nr0 = e.nreal;
-    Child ch;
+    typename E::ChildT ch;
     int ev = EV_NONE;
     if (e.nf == 0u) ev = e.template check_start<FK>(p);
     unsigned long long k = 0;
@@ -313,11 +332,11 @@ __global__ void __launch_bounds__(MAXT)
     if (ev & EV_CHILD) {
         const unsigned long long s = atomicAdd(&p.hdr->tail, 1ull);
         if (s < (unsigned long long)p.capacity) {
-            store_birth(p, (int64_t)s, ch, aval);
+            store_birth(p, (int64_t)s, e, ch);
             p.ready[s] = 1u;
             const unsigned long long j = atomicAdd(&p.hdr->n_new[parity], 1ull);
-            fresh.x[j] = ch.x; fresh.y[j] = ch.y; fresh.z[j] = ch.z; fresh.t[j] = ch.t;
-            fresh.vx[j] = ch.vx; fresh.vy[j] = ch.vy; fresh.vz[j] = ch.vz;
+            e.position(fresh.x[j], fresh.y[j], fresh.z[j], fresh.t[j]);
+            fresh.vx[j] = (double)ch.vx; fresh.vy[j] = (double)ch.vy; fresh.vz[j] = (double)ch.vz;
             fresh.nf[j] = 0u; fresh.nreal[j] = 0u; fresh.uid[j] = ch.uid;
             fresh.slot[j] = (int64_t)s;
         } else {

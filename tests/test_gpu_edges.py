@@ -115,15 +115,17 @@ def test_autotune_picks_and_remembers_a_shape(av):
     p = av.primaries_device(w.primaries)
     opt = A.RunOptions(seed=11, t_max=w.t_max, precision=A.GT_MIXED)
     best, pts = av.autotune(p, opt, capacity=2_000_000)
-    assert len(pts) == 16 and best["real_per_ms"] == max(q["real_per_ms"] for q in pts)
-    assert best["block"] in (512, 640, 768, 1024) and best["flights_per_round"] in (8, 16, 32, 64)
+    assert len(pts) == 36 and best["real_per_ms"] == max(q["real_per_ms"] for q in pts)
+    assert best["block"] in (512, 768, 1024) and best["refill_period"] in (2, 4, 8, 16)
+    assert best["flights_per_phase"] in (4, 6, 8)
     st = av.run(p, opt, capacity=2_000_000)
-    assert st["block"] == best["block"] and st["flights_per_round"] == best["flights_per_round"]
+    assert st["block"] == best["block"] and st["refill_period"] == best["refill_period"]
+    assert st["flights_per_phase"] == best["flights_per_phase"]
     # the shape does not change the physics: same electrons, same tallies
     _, a = run_gpu(av, w, seed=11, precision=A.GT_FP64, capacity=2_000_000, block=128,
-                   flights_per_round=8, t_max=0.3)
+                   refill_period=8, t_max=0.3)
     _, b = run_gpu(av, w, seed=11, precision=A.GT_FP64, capacity=2_000_000, block=512,
-                   flights_per_round=64, t_max=0.3)
+                   refill_period=64, t_max=0.3)
     assert np.array_equal(np.sort(a["uid"]), np.sort(b["uid"]))
     assert np.array_equal(a["tallies"], b["tallies"])
     w = W.plate(n_avalanches=8, seed=0)
