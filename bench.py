@@ -32,12 +32,22 @@ METRIC = "electron-collisions/sec on 1 GB300 (batched mixed vs plain FP64) at ma
 UNIT = "electron-collisions/s"
 WORKLOAD = "plate_batched_4096"
 
-# Warp instructions per flight of the transport step, measured with ncu
-# (smsp__inst_executed.sum / warp-flights) on the straight-line calibration
-# run described in the design notes; None until measured.
-INST_PER_WARP_FLIGHT = None
+# Roofline of the batched transport kernel (bound: instruction issue of the
+# SM's ALU/FMA pipes).  Algorithmic work per flight = lane instructions of
+# the straight-line step: ncu smsp__thread_inst_executed.sum / flights on
+# `bench.py --calibrate --steps 1 --block 1024 --refill-period 16
+# --flights-per-phase 4` (profiles/k_batched_mixed_plate_batched_4096.md).
+# Lanes switched off by divergence are not counted, so divergence, stalls
+# and queue work all show as lost efficiency.
+LANE_INST_PER_FLIGHT = 245.4
 SM_COUNT = 152
-ISSUE_PER_SM_PER_CLK = 4
+ISSUE_PER_SM_PER_CLK = 4       # warp schedulers per SM, one instruction each per clock
+LANES_PER_WARP = 32
+# DRAM bytes per electron of the batched kernel (ncu dram__bytes_read.sum +
+# dram__bytes_write.sum on the 256-avalanche case, divided by its
+# electrons; traffic grows with electrons, so it is scaled to a launch by
+# the electrons the launch stores).  None once the kernel has changed.
+DRAM_BYTES_PER_ELECTRON = 216.2
 
 
 # ---------------------------------------------------------------- sharding
@@ -182,12 +192,13 @@ def run_ours(args) -> None:
     av.set_field(w.field)
     prim_dev = av.primaries_device(w.primaries)
     opt = A.RunOptions(seed=seed, t_max=w.t_max, precision=A.GT_MIXED, mode=A.GT_BATCHED,
-                       block=args.block, refill_period=args.refill_period)
+                       block=args.block, refill_period=args.refill_period,
+                       flights_per_phase=args.flights_per_phase)
     cap = args.capacity
     stream = torch.cuda.current_stream(dev)
     flush = torch.empty(256 * 1024 * 1024, dtype=torch.uint8, device=dev)  # > 129 MB L2
     tune = None
-    if not args.no_autotune and not (args.block or args.refill_period):
+    if not args.no_autotune and not (args.block or args.refill_period or args.flights_per_phase):
         # launch shape chosen by the library's autotuner on a sample of the
         # workload (outside the timed region); later runs use it
         sample = w.primaries.subset(list(range(min(args.tune_avalanches, args.avalanches))))
@@ -288,19 +299,20 @@ def run_ours(args) -> None:
     kms = statistics.mean(kernel_ms)
     fl_per_launch = flights / len(kernel_ms)
     peak_clk = clk.get("sm_max_mhz") or 2070.0
-    peak = SM_COUNT * ISSUE_PER_SM_PER_CLK * peak_clk * 1e6 / 1e9  # G warp-inst/s
-    if INST_PER_WARP_FLIGHT:
-        achieved = INST_PER_WARP_FLIGHT * fl_per_launch / 32.0 / (kms / 1e3) / 1e9
-        roof = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "Gwarp-inst/s",
-                "frac": achieved / peak, "traffic": None,
-                "kernel": "k_batched<MixedElectron,PLATE>", "kernel_ms": kms,
-                "flights_per_launch": fl_per_launch,
-                "inst_per_warp_flight": INST_PER_WARP_FLIGHT,
-                "peak_note": "152 SMs x 4 issue/clk x max SM clock"}
-    else:
-        roof = {"bound": "alu", "achieved": None, "peak": peak, "unit": "Gwarp-inst/s",
-                "frac": None, "traffic": None, "kernel_ms": kms,
-                "flights_per_launch": fl_per_launch}
+    # G lane-instructions/s: SMs x schedulers x lanes x max SM clock
+    peak = SM_COUNT * ISSUE_PER_SM_PER_CLK * LANES_PER_WARP * peak_clk * 1e6 / 1e9
+    achieved = LANE_INST_PER_FLIGHT * fl_per_launch / (kms / 1e3) / 1e9
+    electrons_per_launch = statistics.mean(s["n_endpoints"] for s in stats)
+    roof = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "Glane-inst/s",
+            "frac": achieved / peak,
+            "traffic": (DRAM_BYTES_PER_ELECTRON * electrons_per_launch
+                        if DRAM_BYTES_PER_ELECTRON else None),
+            "traffic_unit": "bytes per launch (ncu, scaled from the 256-avalanche capture)",
+            "kernel": "k_batched<MixedElectron, PLATE, smem table>", "kernel_ms": kms,
+            "flights_per_launch": fl_per_launch,
+            "lane_inst_per_flight": LANE_INST_PER_FLIGHT,
+            "peak_note": "152 SMs x 4 schedulers x 32 lanes x max SM clock (measured max)",
+            "clock_frac": (clk.get("sm_mhz") or peak_clk) / peak_clk}
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": t_max_rank * 1e3 / args.steps,
@@ -334,17 +346,19 @@ def run_ours(args) -> None:
 
 # ------------------------------------------------------------- calibration
 def calibration_workload(n_electrons: int, coll_limit: int = 1000):
-    """Straight-line flights for the instruction count per flight: the
-    argon-like table with its ionisation rate set to zero (same 12-level
-    selection, no secondaries), a uniform 40 kV/cm field with no boundary,
-    one electron per thread, each stopped after `coll_limit` real
-    collisions."""
+    """Straight-line flights for the instruction count per flight, run by the
+    same kernel instantiation as the benchmark (plate field): the argon-like
+    table with its ionisation rate set to zero (same 12-level selection, no
+    secondaries), 40 kV/cm, an anode too far away to reach, one electron per
+    thread from mid-gap, each stopped after `coll_limit` real collisions."""
     from paper_2509_15377_gb300 import workloads as W
     g = W.argon_like_gas()
     g.rate = g.rate.copy()
     g.rate[:, -1] = 0.0
     w = W.drift_model(n_electrons=n_electrons, n_coll=coll_limit, e_field=40_000.0, seed=0)
     w.gas = g
+    w.field = W.Field(W.PLATE, e0=40_000.0, gap=1.0e3)
+    w.primaries.z[:] = 500.0
     return w
 
 
@@ -354,13 +368,14 @@ def run_calibration(args) -> None:
     __graft_entry__.build()
     from paper_2509_15377_gb300 import avalanche as A
     av = A.Avalanche(0)
-    threads = SM_COUNT * 512
+    threads = SM_COUNT * (args.block or 1024)
     w = calibration_workload(threads)
     av.set_gas(w.gas)
     av.set_field(w.field)
     prim = av.primaries_device(w.primaries)
     opt = A.RunOptions(seed=0, coll_limit=w.coll_limit, precision=A.GT_MIXED, mode=A.GT_BATCHED,
-                       block=args.block, refill_period=args.refill_period)
+                       block=args.block, refill_period=args.refill_period,
+                       flights_per_phase=args.flights_per_phase)
     for _ in range(max(1, args.steps)):
         st = av.run(prim, opt, threads, allow=(A.GT_OK,))
     torch.cuda.synchronize()
@@ -414,6 +429,7 @@ def parse(argv=None):
     ap.add_argument("--capacity", type=int, default=100_000_000)
     ap.add_argument("--block", type=int, default=0)
     ap.add_argument("--refill-period", type=int, default=0)
+    ap.add_argument("--flights-per-phase", type=int, default=0)
     ap.add_argument("--cpu-avalanches", type=int, default=64)
     ap.add_argument("--plain-avalanches", type=int, default=32)
     ap.add_argument("--no-cpu-baseline", action="store_true")
