@@ -255,6 +255,37 @@ int gt_workspace_bytes(gt_ctx *ctx, const gt_run *run, int64_t capacity, size_t 
 int avalanche_run(gt_ctx *ctx, const gt_run *run, const gt_endpoints *out, void *workspace,
                   size_t workspace_bytes, void *stream, gt_stats *stats);
 
+/* ---- the batched run without a caller work space ----------------------
+ * avalanche_run_static runs exactly like avalanche_run in GT_BATCHED mode,
+ * but its scratch memory (queue flags, birth velocities, run header,
+ * per-avalanche counters) is a fixed array inside the library, so the call
+ * itself allocates nothing: no cudaMalloc, no cudaFree, no host heap.  It
+ * is for callers that cannot allocate device memory where they run
+ * avalanches: code living inside a framework whose memory manager owns the
+ * GPU's memory, or a loop that cannot accept the device synchronisation an
+ * allocation or a free may cause.  The paper has no counterpart.
+ *
+ * Limits: out->capacity <= GT_STATIC_MAX_ELECTRONS and n_avalanches <=
+ * GT_STATIC_MAX_AVALANCHES, else GT_ERR_WORKSPACE; primaries must be in
+ * device memory (primaries_on_device = 1) and mode GT_BATCHED, else
+ * GT_ERR_ARG.  The caller still provides the primaries and every output
+ * array, as for avalanche_run.
+ *
+ * The array (GT_STATIC_SCRATCH_BYTES) is held by every GPU that loads the
+ * library, until the process exits.  The first call on a device looks up the
+ * array's device address for that device (cudaGetSymbolAddress), which may
+ * load the library's device code; make that first call before any stream
+ * capture.  All calls on a device share the one array: calls whose runs
+ * overlap on the GPU (other streams, other contexts, other threads) race
+ * and corrupt each other; serialise them.  Each call clears what must start
+ * at zero, so the contents left by the previous call do not matter. */
+#define GT_STATIC_MAX_ELECTRONS (1 << 18)
+#define GT_STATIC_MAX_AVALANCHES 16384
+#define GT_STATIC_SCRATCH_BYTES 7471616 /* ~7.1 MiB */
+
+int avalanche_run_static(gt_ctx *ctx, const gt_run *run, const gt_endpoints *out, void *stream,
+                         gt_stats *stats);
+
 /* ---- autotuning of the batched launch shape ---------------------------
  * The batched kernel's throughput depends on the threads per CTA (more
  * resident warps against fewer registers each) and on the flights per

@@ -98,7 +98,8 @@ class gt_tune_point(C.Structure):
 
 EXPORTS = ("gt_abi_version", "gt_strerror", "gt_abi_sizes", "gt_last_cuda_error", "gt_create",
            "gt_destroy", "gas_table_upload", "gt_gas_nu_max", "field_setup",
-           "gt_workspace_bytes", "avalanche_run", "gt_autotune", "avalanche_observables")
+           "gt_workspace_bytes", "avalanche_run", "avalanche_run_static", "gt_autotune",
+           "avalanche_observables")
 
 _lib = None
 
@@ -127,6 +128,8 @@ def load(path: str = LIB_PATH):
                            C.POINTER(gt_stats)], C.c_int),
         "avalanche_observables": ([vp, C.POINTER(gt_endpoints), i64, i32, vp, i32, i32,
                                    C.c_double, vp, vp], C.c_int),
+        "avalanche_run_static": ([vp, C.POINTER(gt_run), C.POINTER(gt_endpoints), vp,
+                                  C.POINTER(gt_stats)], C.c_int),
         "gt_autotune": ([vp, C.POINTER(gt_run), C.POINTER(gt_endpoints), vp, sz, vp,
                          C.POINTER(gt_tune_point), i32, C.POINTER(i32),
                          C.POINTER(gt_tune_point)], C.c_int),
@@ -209,6 +212,22 @@ def avalanche_run(ctx, run: gt_run, out: gt_endpoints, workspace_ptr: int, works
     rc = load().avalanche_run(ctx, C.byref(run), C.byref(out), workspace_ptr, workspace_nbytes,
                               stream_ptr, C.byref(st))
     _check(rc, "avalanche_run", ctx, allow)
+    st.status = rc
+    return st
+
+
+GT_STATIC_MAX_ELECTRONS = 1 << 18
+GT_STATIC_MAX_AVALANCHES = 16384
+
+
+def avalanche_run_static(ctx, run: gt_run, out: gt_endpoints, stream_ptr: int,
+                         allow=PARTIAL_OK) -> gt_stats:
+    """The batched run with the library's fixed internal scratch: allocates
+    nothing (for callers that cannot allocate device memory at this point);
+    limits GT_STATIC_MAX_ELECTRONS slots and GT_STATIC_MAX_AVALANCHES."""
+    st = gt_stats()
+    rc = load().avalanche_run_static(ctx, C.byref(run), C.byref(out), stream_ptr, C.byref(st))
+    _check(rc, "avalanche_run_static", ctx, allow)
     st.status = rc
     return st
 

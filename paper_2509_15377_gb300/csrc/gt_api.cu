@@ -139,6 +139,8 @@ bool finite_pos(double x) { return std::isfinite(x) && x > 0.0; }
 
 }  // namespace
 
+int gt::context_device(const gt_ctx *ctx) { return ctx ? ctx->device : -1; }
+
 extern "C" {
 
 int gt_abi_version(void) { return GT_ABI_VERSION; }

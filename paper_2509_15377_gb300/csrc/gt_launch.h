@@ -6,7 +6,12 @@
 
 #include "gt_device.cuh"
 
+struct gt_ctx;
+
 namespace gt {
+
+// Device index of a context (gt_api.cu), -1 for NULL.
+int context_device(const gt_ctx *ctx);
 
 // Static shared memory of the transport kernels stays below this; the
 // dynamic part (tallies and table) may use the rest of a CTA's opt-in size.
