@@ -13,6 +13,7 @@ Prints one JSON line on rank 0.  Under torchrun every rank runs its own
 from __future__ import annotations
 
 import argparse
+import dataclasses
 import json
 import math
 import os
@@ -36,10 +37,11 @@ WORKLOAD = "plate_batched_4096"
 # SM's ALU/FMA pipes).  Algorithmic work per flight = lane instructions of
 # the straight-line step: ncu smsp__thread_inst_executed.sum / flights on
 # `bench.py --calibrate --steps 1 --block 1024 --refill-period 16
-# --flights-per-phase 4` (profiles/k_batched_mixed_plate_batched_4096.md).
-# Lanes switched off by divergence are not counted, so divergence, stalls
-# and queue work all show as lost efficiency.
-LANE_INST_PER_FLIGHT = 245.4
+# --flights-per-phase 4` with the default banded majorant
+# (profiles/k_batched_mixed_plate_batched_4096.md).  Lanes switched off by
+# divergence are not counted, so divergence, stalls and queue work all show
+# as lost efficiency.
+LANE_INST_PER_FLIGHT = 485.0
 SM_COUNT = 152
 ISSUE_PER_SM_PER_CLK = 4       # warp schedulers per SM, one instruction each per clock
 LANES_PER_WARP = 32
@@ -47,7 +49,7 @@ LANES_PER_WARP = 32
 # dram__bytes_write.sum on the 256-avalanche case, divided by its
 # electrons; traffic grows with electrons, so it is scaled to a launch by
 # the electrons the launch stores).  None once the kernel has changed.
-DRAM_BYTES_PER_ELECTRON = 216.2
+DRAM_BYTES_PER_ELECTRON = 208.0
 
 
 # ---------------------------------------------------------------- sharding
@@ -145,20 +147,23 @@ class ClockSampler:
 
 
 # ------------------------------------------------------------ CPU baseline
-def oracle_baseline(w, seed: int, n_aval: int) -> dict:
+def oracle_baseline(w, seed: int, n_aval: int, args) -> dict:
     """The FP64 oracle as it stands on the host cores, on the first n_aval
-    avalanches of the workload (a bounded sample)."""
+    avalanches of the workload (a bounded sample), with the same majorant
+    as the GPU run."""
     import oracle
     sub = w.primaries.subset(list(range(n_aval)))
     threads = oracle.default_threads()
     t0 = time.perf_counter()
-    o = oracle.run(w.gas, w.field, sub, seed=seed, t_max=w.t_max, n_threads=threads)
+    o = oracle.run(w.gas, w.field, sub, seed=seed, t_max=w.t_max, n_threads=threads,
+                   majorant=int(args.majorant == "banded"), window=args.window,
+                   band_width=w.gas.band_width)
     dt = time.perf_counter() - t0
     L = w.gas.n_levels
     real = int(o["tallies"][:, :L].sum())
     return {"value": real / dt, "unit": UNIT, "cores": threads, "kind": "oracle",
             "sample": f"avalanches 0..{n_aval - 1} of {w.primaries.n_avalanches} "
-                      f"({real:.3g} real collisions in {dt:.1f} s)",
+                      f"({real:.3g} real collisions in {dt:.1f} s, {args.majorant} majorant)",
             "seconds": dt, "real_collisions": real}
 
 
@@ -185,15 +190,17 @@ def run_ours(args) -> None:
 
     cpu = None
     if rank == 0 and ws == 1 and not args.no_cpu_baseline:
-        cpu = oracle_baseline(w, seed, args.cpu_avalanches)
+        cpu = oracle_baseline(w, seed, args.cpu_avalanches, args)
 
     av = A.Avalanche(local)
     av.set_gas(w.gas)
     av.set_field(w.field)
     prim_dev = av.primaries_device(w.primaries)
+    majorant = A.GT_MAJORANT_BANDED if args.majorant == "banded" else A.GT_MAJORANT_GLOBAL
     opt = A.RunOptions(seed=seed, t_max=w.t_max, precision=A.GT_MIXED, mode=A.GT_BATCHED,
                        block=args.block, refill_period=args.refill_period,
-                       flights_per_phase=args.flights_per_phase)
+                       flights_per_phase=args.flights_per_phase, majorant=majorant,
+                       majorant_window=args.window)
     cap = args.capacity
     stream = torch.cuda.current_stream(dev)
     flush = torch.empty(256 * 1024 * 1024, dtype=torch.uint8, device=dev)  # > 129 MB L2
@@ -268,30 +275,53 @@ def run_ours(args) -> None:
     d2h = h_elec.numel() * 8 + h_tal.numel() * 8 + 256
 
     # plain FP64 GPU path (one avalanche per launch sequence) on a sample
+    # the same batched mixed run with the global majorant (one nu_max), for
+    # the gain of the banded majorant alone
+    other = None
+    if rank == 0 and not args.no_plain:
+        o_opt = dataclasses.replace(
+            opt, majorant=A.GT_MAJORANT_GLOBAL if majorant == A.GT_MAJORANT_BANDED
+            else A.GT_MAJORANT_BANDED)
+        o_real, o_ms = 0, 0.0
+        for _ in range(2):
+            flush.fill_(1)
+            o_st = av.run(prim_dev, o_opt, cap, stream=stream, allow=(A.GT_OK,))
+            o_real += o_st["real_collisions"]
+            o_ms += o_st["transport_ms"]
+        other = {"majorant": "global" if o_opt.majorant == A.GT_MAJORANT_GLOBAL else "banded",
+                 "value_kernel_time": o_real / (o_ms / 1e3), "unit": UNIT,
+                 "flights_per_real": o_st["flights"] / max(o_st["real_collisions"], 1)}
+
+    # plain FP64 GPU path (the paper's structure: one avalanche at a time, one
+    # launch per generation) on a sample, with both majorants
     plain = None
     if rank == 0 and not args.no_plain:
         sub = w.primaries.subset(list(range(args.plain_avalanches)))
         psub = av.primaries_device(sub)
-        popt = A.RunOptions(seed=seed, t_max=w.t_max, precision=A.GT_FP64, mode=A.GT_PLAIN)
-        torch.cuda.synchronize()
-        t0 = time.perf_counter()
-        pst = av.run(psub, popt, cap, stream=stream, allow=(A.GT_OK,))
-        torch.cuda.synchronize()
-        pdt = time.perf_counter() - t0
-        pobs = av.observables(pst["n_endpoints"], sub, collect_status=W.ANODE,
-                              drift_status=W.ANODE, gap=w.field.gap)
+        plain = {"sample": f"avalanches 0..{args.plain_avalanches - 1}", "unit": UNIT}
+        for name, mj in (("global", A.GT_MAJORANT_GLOBAL), ("banded", A.GT_MAJORANT_BANDED)):
+            popt = A.RunOptions(seed=seed, t_max=w.t_max, precision=A.GT_FP64, mode=A.GT_PLAIN,
+                                majorant=mj, majorant_window=args.window)
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            pst = av.run(psub, popt, cap, stream=stream, allow=(A.GT_OK,))
+            torch.cuda.synchronize()
+            pdt = time.perf_counter() - t0
+            plain["value_" + name] = pst["real_collisions"] / pdt
+            if mj == majorant:
+                # like for like: the speedup compares runs with the same majorant
+                pobs = av.observables(pst["n_endpoints"], sub, collect_status=W.ANODE,
+                                      drift_status=W.ANODE, gap=w.field.gap)
+                plain.update(value=plain["value_" + name], majorant=name,
+                             launches=pst["launches"], generations=pst["iterations"])
         # the mixed batched run restricted to the same avalanches, for the gain match
         st_m = av.run(psub, opt, cap, stream=stream, allow=(A.GT_OK,))
         mobs = av.observables(st_m["n_endpoints"], sub, collect_status=W.ANODE,
                               drift_status=W.ANODE, gap=w.field.gap)
         se = math.hypot(pobs[1], mobs[1])
-        plain = {"value": pst["real_collisions"] / pdt, "unit": UNIT,
-                 "sample": f"avalanches 0..{args.plain_avalanches - 1}",
-                 "launches": pst["launches"], "generations": pst["iterations"],
-                 "gain_fp64_plain": pobs[0], "gain_mixed_batched": mobs[0],
-                 "gain_sigma": se,
-                 "matched_gain_3sigma": bool(abs(pobs[0] - mobs[0]) <= 3 * se),
-                 "vd_fp64_plain": pobs[3], "vd_mixed_batched": mobs[3]}
+        plain.update(gain_fp64_plain=pobs[0], gain_mixed_batched=mobs[0], gain_sigma=se,
+                     matched_gain_3sigma=bool(abs(pobs[0] - mobs[0]) <= 3 * se),
+                     vd_fp64_plain=pobs[3], vd_mixed_batched=mobs[3])
 
     if rank != 0:
         av.close()
@@ -331,6 +361,9 @@ def run_ours(args) -> None:
         "electrons_per_step": stats[-1]["n_endpoints"],
         "observables": {"gain": obs[0], "gain_se": obs[1], "vd_cm_per_ns": obs[3],
                         "dt_cm2_per_ns": obs[4], "dl_cm2_per_ns": obs[5]},
+        "majorant": args.majorant,
+        "flights_per_real": flights / max(real, 1),
+        "other_majorant": other,
         "plain_fp64": plain,
         "speedup_vs_plain_fp64": (value / plain["value"]) if plain else None,
         "roofline": roof,
@@ -375,7 +408,10 @@ def run_calibration(args) -> None:
     prim = av.primaries_device(w.primaries)
     opt = A.RunOptions(seed=0, coll_limit=w.coll_limit, precision=A.GT_MIXED, mode=A.GT_BATCHED,
                        block=args.block, refill_period=args.refill_period,
-                       flights_per_phase=args.flights_per_phase)
+                       flights_per_phase=args.flights_per_phase,
+                       majorant=(A.GT_MAJORANT_BANDED if args.majorant == "banded"
+                                 else A.GT_MAJORANT_GLOBAL),
+                       majorant_window=args.window)
     for _ in range(max(1, args.steps)):
         st = av.run(prim, opt, threads, allow=(A.GT_OK,))
     torch.cuda.synchronize()
@@ -398,12 +434,12 @@ def run_reference(args) -> None:
     oracle.build()
     w = W.plate_batched(n_avalanches=args.avalanches, seed=0)
     for _ in range(args.warmup):
-        oracle_baseline(w, 0, max(1, args.cpu_avalanches // 8))
+        oracle_baseline(w, 0, max(1, args.cpu_avalanches // 8), args)
     real = 0
     secs = 0.0
     res = None
     for _ in range(args.steps):
-        res = oracle_baseline(w, 0, args.cpu_avalanches)
+        res = oracle_baseline(w, 0, args.cpu_avalanches, args)
         real += res["real_collisions"]
         secs += res["seconds"]
     value = real / secs
@@ -435,6 +471,8 @@ def parse(argv=None):
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-plain", action="store_true")
     ap.add_argument("--no-autotune", action="store_true")
+    ap.add_argument("--majorant", default="banded", choices=["banded", "global"])
+    ap.add_argument("--window", type=float, default=2.0)
     ap.add_argument("--tune-avalanches", type=int, default=1024)
     ap.add_argument("--calibrate", action="store_true",
                     help="run the straight-line calibration workload (for ncu)")

@@ -96,7 +96,10 @@ typedef struct gt_ctx gt_ctx;
  * rate[k * n_levels + j] is the collision rate of level j at the node energy
  * k * d_eps (1/ns, >= 0); between nodes the rates are interpolated linearly,
  * beyond the last node the last node is used.  nu_max <= 0 selects
- * (1 + 1e-6) * max_k sum_j rate; a given nu_max must be >= that maximum. */
+ * (1 + 1e-6) * max_k sum_j rate; a given nu_max must be >= that maximum.
+ * The upload also tabulates, per energy band, the largest total rate (the
+ * band's largest node value: rates are linear between nodes), for runs with
+ * the banded majorant. */
 typedef struct {
     int32_t n_levels;          /* 1..GT_MAX_LEVELS */
     int32_t n_nodes;           /* >= 2 */
@@ -106,6 +109,8 @@ typedef struct {
     const double *rate;        /* host [n_nodes * n_levels] 1/ns */
     double recoil;             /* 2 m / M for elastic recoil loss, in [0, 0.5) */
     double nu_max;             /* 1/ns */
+    double band_width;         /* eV per energy band of the banded majorant,
+                                  rounded to whole nodes; 0 = 1 eV */
 } gt_gas;
 
 /* ---- field and geometry (Fig. 2 "Find E field"; Sec. 3.1 field maps) -- */
@@ -158,7 +163,25 @@ typedef struct {
                                          meets a real collision, then the warp
                                          applies its lanes' collisions together;
                                          0 = default */
+    int32_t majorant;                 /* GT_MAJORANT_GLOBAL / GT_MAJORANT_BANDED */
+    int32_t pad;
+    double majorant_window;           /* banded: window factor c, 0 = 2 */
 } gt_run;
+
+/* Majorant of the null-collision flights.
+ * GLOBAL: dt = -ln(u)/nu_max with one nu_max for all energies (Skullerud).
+ * BANDED: per flight, with tau = c / (largest rate of the band holding the
+ * current energy), the energy can change by at most
+ * D = |E| (|v| tau + a tau^2 / 2) during tau (the field's work bound; B
+ * does no work), so the largest rate over the bands covering
+ * [eps - D, eps + D] bounds the true rate along the whole flight; dt is drawn
+ * with that bound, and a flight longer than tau stops at tau without a
+ * collision test (a memoryless restart).  Both are exact; BANDED needs
+ * several times fewer flights per real collision when the rates vary with
+ * energy.  Flight counts include the stopped flights; null tallies count
+ * only rejected collision tests. */
+#define GT_MAJORANT_GLOBAL 0
+#define GT_MAJORANT_BANDED 1
 
 /* Fault injection for tests: reserve one queue slot that is never filled,
  * so every waiting worker eventually gives up after spin_limit_ms and the

@@ -123,6 +123,9 @@ typedef struct {
     double t_max;                    /* ns; <= 0 means none */
     uint32_t coll_limit;             /* real collisions; 0 means none */
     int32_t n_threads;
+    int32_t majorant;                /* 0: one global nu_max; 1: banded (below) */
+    double window;                   /* banded: flight window = window / band rate */
+    double band_width;               /* banded: eV per energy band (whole nodes) */
 } or_run_args;
 
 /* ------------------------------------------------ Philox4x32-10
@@ -304,6 +307,9 @@ typedef struct {
     int type[64];
     double thr[64];
     double *cum; /* [N][L]: running sum over levels 0..j of the rate */
+    double top;  /* largest total rate over the nodes */
+    int band_nodes, B; /* banded majorant: nodes per band, number of bands */
+    double *bmax;      /* [B]: largest total rate over the band's nodes */
 } or_table;
 
 static int table_build(const or_gas *g, or_table *t)
@@ -329,11 +335,91 @@ static int table_build(const or_gas *g, or_table *t)
         if (s > top) top = s;
     }
     t->nu_max = g->nu_max > 0.0 ? g->nu_max : top * (1.0 + 1e-6);
-    if (t->nu_max < top) {
+    t->band_nodes = 0;
+    t->B = 0;
+    t->bmax = NULL;
+    t->top = top;
+    if (!(t->nu_max > 0.0) || t->nu_max < top) {
         free(t->cum);
         return -1;
     }
     return 0;
+}
+
+/* Energy bands for the banded majorant: band b spans the nodes
+ * b*n .. (b+1)*n (n = band_width / d_eps, at least 1); since the rates are
+ * linear between nodes, the largest total rate over the band's energies is
+ * the largest node value.  Energies beyond the last node belong to the
+ * last band (their rate is the last node's).  A band whose rates are all
+ * zero gets the bound top * 2^-40 instead, so that its window stays
+ * finite (any positive bound of a zero rate is exact). */
+static int bands_build(or_table *t, double band_width)
+{
+    int n = (int)floor(band_width / t->d_eps + 0.5);
+    if (n < 1) n = 1;
+    int B = (t->N - 1 + n - 1) / n;
+    if (B < 1) B = 1;
+    t->bmax = (double *)malloc(sizeof(double) * (size_t)B);
+    if (!t->bmax) return -1;
+    for (int b = 0; b < B; ++b) {
+        double m = 0.0;
+        for (int k = b * n; k <= (b + 1) * n && k < t->N; ++k) {
+            double c = t->cum[(int64_t)k * t->L + t->L - 1];
+            if (c > m) m = c;
+        }
+        t->bmax[b] = m > 0.0 ? m : ldexp(t->top, -40);
+    }
+    t->band_nodes = n;
+    t->B = B;
+    return 0;
+}
+
+static int band_of(const or_table *t, double eps)
+{
+    double x = eps / (t->band_nodes * t->d_eps);
+    if (!(x > 0.0)) return 0;
+    if (x >= (double)t->B) return t->B - 1;
+    int b = (int)floor(x);
+    return b < t->B ? b : t->B - 1;
+}
+
+/* Banded majorant for a flight that starts with energy eps0 and speed
+ * `speed` in a field of magnitude Em (V/cm): over a window of
+ * tau = window / (rate of the current band) the energy can change by at
+ * most D = Em (speed tau + a Em tau^2 / 2) (the field's work along the
+ * largest displacement), so the largest rate of the bands covering
+ * [eps0 - D, eps0 + D] bounds the true rate along the flight.  Returns
+ * that rate and sets *tau. */
+static double banded_majorant(const or_table *tb, double eps0, double speed, double Em,
+                              double window, double *tau)
+{
+    double w = window / tb->bmax[band_of(tb, eps0)];
+    double D = Em * (speed * w + 0.5 * (OR_ACCEL_PER_VCM * Em) * w * w);
+    int lo = band_of(tb, eps0 - D), hi = band_of(tb, eps0 + D);
+    double nu = 0.0;
+    for (int b = lo; b <= hi; ++b)
+        if (tb->bmax[b] > nu) nu = tb->bmax[b];
+    *tau = w;
+    return nu;
+}
+
+/* Test hook: the banded majorant above for a given gas and band width.
+ * Returns the rate (1/ns), or a negative value for a bad table. */
+double or_majorant(const or_gas *g, double band_width, double eps0, double speed, double Em,
+                   double window, double *tau_out)
+{
+    or_table t;
+    if (table_build(g, &t)) return -1.0;
+    if (bands_build(&t, band_width)) {
+        free(t.cum);
+        return -1.0;
+    }
+    double tau = 0.0;
+    double nu = banded_majorant(&t, eps0, speed, Em, window, &tau);
+    if (tau_out) *tau_out = tau;
+    free(t.cum);
+    free(t.bmax);
+    return nu;
 }
 
 /* Cumulative rates at energy eps by linear interpolation between nodes;
@@ -355,12 +441,13 @@ static void table_interp(const or_table *t, double eps, double *c)
     for (int j = 0; j < t->L; ++j) c[j] = c0[j] + f * (c1[j] - c0[j]);
 }
 
-/* Real or null collision (Fig. 2 "Collision?"): level index, or -1 for null. */
-static int table_select(const or_table *t, double eps, double u1)
+/* Real or null collision (Fig. 2 "Collision?") for a flight drawn with the
+ * majorant nu: level index, or -1 for null. */
+static int table_select(const or_table *t, double eps, double u1, double nu)
 {
     double c[64];
     table_interp(t, eps, c);
-    double R = u1 * t->nu_max;
+    double R = u1 * nu;
     for (int j = 0; j < t->L; ++j) {
         if (R < c[j]) {
             if (t->type[j] != OR_ELASTIC && eps < t->thr[j]) return -1;
@@ -375,7 +462,7 @@ int or_select(const or_gas *g, double eps, double u1, double *nu_max_out)
 {
     or_table t;
     if (table_build(g, &t)) return -2;
-    int j = table_select(&t, eps, u1);
+    int j = table_select(&t, eps, u1, t.nu_max);
     if (nu_max_out) *nu_max_out = t.nu_max;
     free(t.cum);
     return j;
@@ -486,8 +573,24 @@ static void transport_electron(const or_table *tb, const or_field *f, const or_r
         or_field_eval(f, plate_e, r, E);
         double acc[3] = {-OR_ACCEL_PER_VCM * E[0], -OR_ACCEL_PER_VCM * E[1],
                          -OR_ACCEL_PER_VCM * E[2]};
-        /* null-collision free flight */
-        double dt = -log(u[0]) / tb->nu_max;
+        /* null-collision free flight.  With the banded majorant a flight
+         * longer than the window tau stops at tau without a collision test
+         * (memoryless restart). */
+        double nu = tb->nu_max;
+        double dt;
+        int pseudo = 0;
+        if (a->majorant == 1) {
+            double tau;
+            nu = banded_majorant(tb, kinetic_energy(v), sqrt(dot3(v, v)), sqrt(dot3(E, E)),
+                                 a->window, &tau);
+            dt = -log(u[0]) / nu;
+            if (dt >= tau) {
+                dt = tau;
+                pseudo = 1;
+            }
+        } else {
+            dt = -log(u[0]) / nu;
+        }
         int timed = 0;
         if (a->t_max > 0.0 && t + dt > a->t_max) {
             dt = a->t_max - t;
@@ -506,8 +609,9 @@ static void transport_electron(const or_table *tb, const or_field *f, const or_r
             status = OR_TIME;
             break;
         }
+        if (pseudo) continue; /* window ended before a collision */
         double eps = kinetic_energy(v);
-        int lvl = table_select(tb, eps, u[1]);
+        int lvl = table_select(tb, eps, u[1], nu);
         if (lvl < 0) {
             o->tally[tb->L] += 1;
             continue;
@@ -641,12 +745,18 @@ int or_run(const or_gas *g, const or_field *f, const or_run_args *a, or_result *
         if (a->aval[p] < 0 || a->aval[p] >= a->n_avalanches) return -3;
     or_table tb;
     if (table_build(g, &tb)) return -2;
+    if (a->majorant == 1) {
+        if (!(a->window > 0.0) || !(a->band_width > 0.0) || bands_build(&tb, a->band_width)) {
+            free(tb.cum);
+            return -3;
+        }
+    }
     int32_t A = a->n_avalanches;
     int64_t *first = (int64_t *)calloc((size_t)A + 1, sizeof(int64_t));
     int64_t *order = (int64_t *)malloc(sizeof(int64_t) * (size_t)(a->n_primaries + 1));
     or_aval_out *out = (or_aval_out *)calloc((size_t)A + 1, sizeof(or_aval_out));
     if (!first || !order || !out) {
-        free(first); free(order); free(out); free(tb.cum);
+        free(first); free(order); free(out); free(tb.cum); free(tb.bmax);
         return -1;
     }
     for (int64_t p = 0; p < a->n_primaries; ++p) first[a->aval[p] + 1] += 1;
@@ -654,7 +764,7 @@ int or_run(const or_gas *g, const or_field *f, const or_run_args *a, or_result *
     {
         int64_t *fill = (int64_t *)malloc(sizeof(int64_t) * ((size_t)A + 1));
         if (!fill) {
-            free(first); free(order); free(out); free(tb.cum);
+            free(first); free(order); free(out); free(tb.cum); free(tb.bmax);
             return -1;
         }
         memcpy(fill, first, sizeof(int64_t) * ((size_t)A + 1));
@@ -690,7 +800,7 @@ int or_run(const or_gas *g, const or_field *f, const or_run_args *a, or_result *
             free(out[k].ep);
             free(out[k].tally);
         }
-        free(out); free(R); free(tb.cum);
+        free(out); free(R); free(tb.cum); free(tb.bmax);
         return -1;
     }
     R->n_aval = A;
@@ -698,6 +808,7 @@ int or_run(const or_gas *g, const or_field *f, const or_run_args *a, or_result *
     R->out = out;
     R->total = total;
     free(tb.cum);
+    free(tb.bmax);
     *res = R;
     return 0;
 }

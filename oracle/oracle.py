@@ -24,7 +24,7 @@ _lock = threading.Lock()
 _lib = None
 
 __all__ = ["build", "philox4x32_10", "splitmix64_mix", "child_uid", "flight", "elastic", "field_eval",
-           "boundary", "select", "run", "default_threads"]
+           "boundary", "select", "majorant", "run", "default_threads"]
 
 
 def build(force: bool = False) -> str:
@@ -58,7 +58,8 @@ class _Run(C.Structure):
                 ("e", C.c_void_p), ("dx", C.c_void_p), ("dy", C.c_void_p), ("dz", C.c_void_p),
                 ("aval", C.c_void_p), ("uid", C.c_void_p), ("aval_field", C.c_void_p),
                 ("seed", C.c_uint64), ("t_max", C.c_double), ("coll_limit", C.c_uint32),
-                ("n_threads", C.c_int32)]
+                ("n_threads", C.c_int32), ("majorant", C.c_int32), ("window", C.c_double),
+                ("band_width", C.c_double)]
 
 
 def _load():
@@ -84,6 +85,9 @@ def _load():
             lib.or_select.argtypes = [C.POINTER(_Gas), C.c_double, C.c_double,
                                       C.POINTER(C.c_double)]
             lib.or_select.restype = C.c_int
+            lib.or_majorant.argtypes = [C.POINTER(_Gas)] + [C.c_double] * 5 + [
+                C.POINTER(C.c_double)]
+            lib.or_majorant.restype = C.c_double
             lib.or_run.argtypes = [C.POINTER(_Gas), C.POINTER(_Field), C.POINTER(_Run),
                                    C.POINTER(C.c_void_p)]
             lib.or_run.restype = C.c_int
@@ -199,10 +203,27 @@ def select(gas, eps: float, u1: float):
     return j, nm.value
 
 
+def majorant(gas, band_width: float, eps0: float, speed: float, e_mag: float,
+             window: float):
+    """Banded majorant (1/ns) and window tau (ns) of a flight starting with
+    energy eps0 (eV) and speed (cm/ns) in a field of e_mag V/cm."""
+    keep = []
+    g = _gas_struct(gas, keep)
+    tau = C.c_double(0.0)
+    nu = _load().or_majorant(C.byref(g), float(band_width), float(eps0), float(speed),
+                             float(e_mag), float(window), C.byref(tau))
+    if nu < 0.0:
+        raise ValueError("bad gas table")
+    return nu, tau.value
+
+
 # -------------------------------------------------------------------- run
 def run(gas, field, prim, seed: int = 0, t_max: float = 0.0, coll_limit: int = 0,
-        n_threads: int | None = None) -> dict:
-    """Transport every avalanche of `prim` and return a dict of arrays:
+        n_threads: int | None = None, majorant: int = 0, window: float = 2.0,
+        band_width: float = 1.0) -> dict:
+    """Transport every avalanche of `prim` and return a dict of arrays
+    (majorant 0: one global nu_max; 1: the banded majorant with flight
+    window `window` / band rate and bands of `band_width` eV):
     x0..e0 (start), x1..e1 (end), status, aval, uid, n_flight, ledger [n, 4]
     (field work, inelastic loss, recoil loss, secondary share; eV),
     electrons [n_avalanches], tallies [n_avalanches, L+1] (real collisions
@@ -232,6 +253,9 @@ def run(gas, field, prim, seed: int = 0, t_max: float = 0.0, coll_limit: int = 0
     ra.t_max = t_max
     ra.coll_limit = coll_limit
     ra.n_threads = n_threads or default_threads()
+    ra.majorant = majorant
+    ra.window = window
+    ra.band_width = band_width
     handle = C.c_void_p()
     rc = lib.or_run(C.byref(g), C.byref(f), C.byref(ra), C.byref(handle))
     if rc != 0:

@@ -28,6 +28,7 @@ GT_ERR_UNSUPPORTED = -8
 GT_FP64, GT_MIXED = 0, 1
 GT_BATCHED, GT_PLAIN = 0, 1
 GT_DEBUG_UNFILLED_SLOT = 1
+GT_MAJORANT_GLOBAL, GT_MAJORANT_BANDED = 0, 1
 GT_OBS_COUNT = 8
 PARTIAL_OK = (GT_OK, GT_ERR_QUEUE_OVERFLOW, GT_ERR_TIMEOUT)
 
@@ -42,7 +43,7 @@ class GtError(RuntimeError):
 class gt_gas(C.Structure):
     _fields_ = [("n_levels", C.c_int32), ("n_nodes", C.c_int32), ("d_eps", C.c_double),
                 ("level_type", C.c_void_p), ("threshold", C.c_void_p), ("rate", C.c_void_p),
-                ("recoil", C.c_double), ("nu_max", C.c_double)]
+                ("recoil", C.c_double), ("nu_max", C.c_double), ("band_width", C.c_double)]
 
 
 class gt_field(C.Structure):
@@ -63,7 +64,8 @@ class gt_run(C.Structure):
                 ("refill_period", C.c_int32), ("grid", C.c_int32),
                 ("size_limit", C.c_uint64), ("spin_limit_ms", C.c_double),
                 ("time_limit_ms", C.c_double), ("debug_flags", C.c_int32),
-                ("flights_per_phase", C.c_int32)]
+                ("flights_per_phase", C.c_int32), ("majorant", C.c_int32), ("pad", C.c_int32),
+                ("majorant_window", C.c_double)]
 
 
 _EP_ARRAYS = ("x0", "y0", "z0", "t0", "e0", "x1", "y1", "z1", "t1", "e1", "status", "aval",
@@ -175,7 +177,7 @@ def gas_table_upload(ctx, gas: W.Gas) -> None:
     th = np.ascontiguousarray(gas.threshold, np.float64)
     rt = np.ascontiguousarray(gas.rate, np.float64)
     g = gt_gas(rt.shape[1], rt.shape[0], gas.d_eps, lt.ctypes.data, th.ctypes.data,
-               rt.ctypes.data, gas.recoil, gas.nu_max)
+               rt.ctypes.data, gas.recoil, gas.nu_max, getattr(gas, "band_width", 0.0))
     _check(load().gas_table_upload(ctx, C.byref(g)), "gas_table_upload", ctx)
 
 
@@ -263,6 +265,8 @@ class RunOptions:
     refill_period: int = 0
     flights_per_phase: int = 0
     grid: int = 0
+    majorant: int = 0          # GT_MAJORANT_GLOBAL / GT_MAJORANT_BANDED
+    majorant_window: float = 0.0
     size_limit: int = 0
     spin_limit_ms: float = 0.0
     time_limit_ms: float = 0.0
@@ -394,6 +398,8 @@ class Avalanche:
         r.block = opt.block
         r.refill_period = opt.refill_period
         r.flights_per_phase = opt.flights_per_phase
+        r.majorant = opt.majorant
+        r.majorant_window = opt.majorant_window
         r.grid = opt.grid
         r.size_limit = opt.size_limit
         r.spin_limit_ms = opt.spin_limit_ms

@@ -25,6 +25,8 @@ struct gt_ctx {
     DevField field{};
     double *d_cum64 = nullptr;
     float *d_cum32 = nullptr;
+    double *d_band64 = nullptr;
+    float *d_band32 = nullptr;
     cudaEvent_t ev0 = nullptr, ev1 = nullptr;
     Header *h_hdr = nullptr;  // pinned copy of the work-space header
     unsigned long long *d_obs_counts = nullptr;
@@ -211,6 +213,8 @@ int gt_destroy(gt_ctx *ctx)
         DeviceGuard g(ctx->device);
         if (ctx->d_cum64) cudaFree(ctx->d_cum64);
         if (ctx->d_cum32) cudaFree(ctx->d_cum32);
+        if (ctx->d_band64) cudaFree(ctx->d_band64);
+        if (ctx->d_band32) cudaFree(ctx->d_band32);
         if (ctx->d_obs_counts) cudaFree(ctx->d_obs_counts);
         if (ctx->d_obs_partials) cudaFree(ctx->d_obs_partials);
         if (ctx->ev0) cudaEventDestroy(ctx->ev0);
@@ -253,18 +257,56 @@ int gas_table_upload(gt_ctx *ctx, const gt_gas *g)
     std::vector<float> cum32(cum.size());
     for (size_t i = 0; i < cum.size(); ++i) cum32[i] = (float)cum[i];
 
+    // Banded majorant: band b spans nodes b*n .. (b+1)*n; its bound is the
+    // largest node value of the total rate (linear between nodes), or
+    // top * 2^-40 where that is zero, so every window stays finite.  Range
+    // maxima over 2^j consecutive bands, j = 0..J, make any band range two
+    // lookups.
+    if (!(g->band_width >= 0.0) || !std::isfinite(g->band_width)) return GT_ERR_ARG;
+    const double bw = g->band_width > 0.0 ? g->band_width : 1.0;
+    const int bn = std::max(1, (int)std::floor(bw / g->d_eps + 0.5));
+    const int B = std::max(1, (N - 1 + bn - 1) / bn);
+    int J = 0;
+    while ((2 << J) <= B) ++J;
+    std::vector<double> band((size_t)(J + 1) * B);
+    for (int b = 0; b < B; ++b) {
+        double m = 0.0;
+        for (int k = b * bn; k <= (b + 1) * bn && k < N; ++k)
+            m = std::max(m, cum[(size_t)k * L + L - 1]);
+        band[b] = m > 0.0 ? m : std::ldexp(top, -40);
+    }
+    for (int j = 1; j <= J; ++j)
+        for (int b = 0; b < B; ++b) {
+            const int o = b + (1 << (j - 1));
+            band[(size_t)j * B + b] = o < B ? std::max(band[(size_t)(j - 1) * B + b],
+                                                       band[(size_t)(j - 1) * B + o])
+                                            : band[(size_t)(j - 1) * B + b];
+        }
+    std::vector<float> band32(band.size());
+    for (size_t i = 0; i < band.size(); ++i) band32[i] = (float)band[i];
+
     DeviceGuard dg(ctx->device);
     if (!dg.ok) return GT_ERR_CUDA;
     if (ctx->d_cum64) cudaFree(ctx->d_cum64);
     if (ctx->d_cum32) cudaFree(ctx->d_cum32);
+    if (ctx->d_band64) cudaFree(ctx->d_band64);
+    if (ctx->d_band32) cudaFree(ctx->d_band32);
     ctx->d_cum64 = nullptr;
     ctx->d_cum32 = nullptr;
+    ctx->d_band64 = nullptr;
+    ctx->d_band32 = nullptr;
     ctx->has_gas = false;
     GT_CUDA(ctx, cudaMalloc((void **)&ctx->d_cum64, sizeof(double) * cum.size()));
     GT_CUDA(ctx, cudaMalloc((void **)&ctx->d_cum32, sizeof(float) * cum.size()));
+    GT_CUDA(ctx, cudaMalloc((void **)&ctx->d_band64, sizeof(double) * band.size()));
+    GT_CUDA(ctx, cudaMalloc((void **)&ctx->d_band32, sizeof(float) * band.size()));
     GT_CUDA(ctx, cudaMemcpy(ctx->d_cum64, cum.data(), sizeof(double) * cum.size(),
                             cudaMemcpyHostToDevice));
     GT_CUDA(ctx, cudaMemcpy(ctx->d_cum32, cum32.data(), sizeof(float) * cum.size(),
+                            cudaMemcpyHostToDevice));
+    GT_CUDA(ctx, cudaMemcpy(ctx->d_band64, band.data(), sizeof(double) * band.size(),
+                            cudaMemcpyHostToDevice));
+    GT_CUDA(ctx, cudaMemcpy(ctx->d_band32, band32.data(), sizeof(float) * band.size(),
                             cudaMemcpyHostToDevice));
     DevGas &d = ctx->gas;
     d = DevGas{};
@@ -283,6 +325,13 @@ int gas_table_upload(gt_ctx *ctx, const gt_gas *g)
     d.lastk_f = (float)(N - 2);
     d.cum64 = ctx->d_cum64;
     d.cum32 = ctx->d_cum32;
+    d.n_bands = B;
+    d.band_levels = J + 1;
+    d.inv_band_width = 1.0 / (bn * g->d_eps);
+    d.inv_band_width_f = (float)d.inv_band_width;
+    d.last_band_f = (float)(B - 1);
+    d.band64 = ctx->d_band64;
+    d.band32 = ctx->d_band32;
     for (int j = 0; j < L; ++j) {
         d.type[j] = g->level_type[j];
         d.thr[j] = g->threshold[j];
@@ -389,6 +438,9 @@ static int validate_run(gt_ctx *ctx, const gt_run *r, const gt_endpoints *o, voi
     if (!std::isfinite(r->t_max)) return GT_ERR_ARG;
     if (r->block < 0 || r->refill_period < 0 || r->grid < 0 || r->flights_per_phase < 0)
         return GT_ERR_ARG;
+    if ((r->majorant != GT_MAJORANT_GLOBAL && r->majorant != GT_MAJORANT_BANDED) ||
+        !(r->majorant_window >= 0.0) || !std::isfinite(r->majorant_window))
+        return GT_ERR_ARG;
     if (r->block && (r->block % 32 != 0 ||
                      r->block > (r->precision == GT_FP64 ? max_block_fp64() : max_block_mixed())))
         return GT_ERR_ARG;
@@ -465,6 +517,9 @@ int avalanche_run(gt_ctx *ctx, const gt_run *r, const gt_endpoints *o, void *ws,
                                            : (tuned_k > 0 ? tuned_k : (prec_i ? 8 : 32));
     p.flights_per_phase = r->flights_per_phase > 0 ? r->flights_per_phase
                                                    : (tuned_m > 0 ? tuned_m : 6);
+    p.majorant = r->majorant;
+    p.window = r->majorant_window > 0.0 ? r->majorant_window : 2.0;
+    p.window_f = (float)p.window;
     p.size_limit = r->size_limit;
     p.spin_limit_ns = (long long)((r->spin_limit_ms > 0 ? r->spin_limit_ms : 60000.0) * 1e6);
     p.time_limit_ns = (long long)((r->time_limit_ms > 0 ? r->time_limit_ms : 600000.0) * 1e6);
@@ -524,10 +579,11 @@ int avalanche_run(gt_ctx *ctx, const gt_run *r, const gt_endpoints *o, void *ws,
     const int block = r->block ? r->block
                                : (r->mode == GT_BATCHED && tuned_b > 0 ? tuned_b
                                                                        : default_block(r->precision));
-    const size_t smem_tab = shared_bytes(L, ctx->gas.n_nodes, block, true);
+    const int band_entries = ctx->gas.n_bands * ctx->gas.band_levels;
+    const size_t smem_tab = shared_bytes(L, ctx->gas.n_nodes, block, true, band_entries);
     const size_t smem_cap = ctx->smem_optin - kStaticSmemReserve;
     const bool smem_table = !fp64 && smem_tab <= smem_cap;
-    const size_t smem = shared_bytes(L, ctx->gas.n_nodes, block, smem_table);
+    const size_t smem = shared_bytes(L, ctx->gas.n_nodes, block, smem_table, band_entries);
     if (smem > smem_cap) return GT_ERR_UNSUPPORTED;
     int iterations = 0, grid = 0;
     unsigned host_err = 0;  // aborts decided on the host (plain mode)
@@ -596,9 +652,9 @@ int avalanche_run(gt_ctx *ctx, const gt_run *r, const gt_endpoints *o, void *ws,
                 pa.parity = parity;
                 pa.aval = a;
                 GT_CUDA(ctx, fp64 ? launch_plain_fp64(p, pa, std::min(block, 128),
-                                                      shared_bytes(L, ctx->gas.n_nodes, std::min(block, 128), false), s)
+                                                      shared_bytes(L, ctx->gas.n_nodes, std::min(block, 128), false, band_entries), s)
                                   : launch_plain_mixed(p, pa, smem_table, std::min(block, 128),
-                                                       shared_bytes(L, ctx->gas.n_nodes, std::min(block, 128), smem_table), s));
+                                                       shared_bytes(L, ctx->gas.n_nodes, std::min(block, 128), smem_table, band_entries), s));
                 GT_CUDA(ctx, launch_plain_compact(p, pa, s));
                 launches += 2;
                 GT_CUDA(ctx, cudaMemcpyAsync(ctx->h_hdr, p.hdr, sizeof(Header),

@@ -40,6 +40,14 @@ struct DevGas {
     float last_x_f, lastk_f;  // n_nodes - 1 and n_nodes - 2 as floats
     const double *cum64;  // [n_nodes][n_levels] running sums over levels
     const float *cum32;
+    // Banded majorant: band b covers nodes [b n, (b+1) n]; bandmax tables
+    // hold range maxima, level j, entry b = max over bands b .. b + 2^j - 1
+    // (a sparse table: the maximum over any band range is two lookups).
+    int n_bands, band_levels;
+    double inv_band_width;       // 1 / (n d_eps)
+    float inv_band_width_f, last_band_f;
+    const double *band64;        // [band_levels][n_bands]
+    const float *band32;
     int32_t type[GT_MAX_LEVELS];
     double thr[GT_MAX_LEVELS];
 };
@@ -110,6 +118,9 @@ struct RunParams {
     uint32_t coll_limit;
     int refill_period;  // batched: collision rounds between queue refills
     int flights_per_phase;  // batched mixed: flights before a warp's collisions
+    int majorant;           // GT_MAJORANT_GLOBAL / GT_MAJORANT_BANDED
+    double window;          // banded: window factor c
+    float window_f;
     uint64_t size_limit;
     long long spin_limit_ns, time_limit_ns;
     int n_avalanches;
@@ -200,6 +211,7 @@ __device__ __forceinline__ uint64_t child_uid(uint64_t parent, uint32_t flight)
 // Per-CTA view of the gas constants; the FP32 cumulative table is staged
 // into shared memory when it fits (mixed precision).
 struct Tables {
+    const float *band32;    // shared: banded-majorant range maxima (FP32)
     const float *cum32;     // shared or global, rows of `stride32` floats
     const double *cum64;    // global (read-only path), rows of n_levels
     const int *type;        // shared [L]
@@ -398,6 +410,32 @@ __device__ __forceinline__ int select_level32(const float *cum, int stride, int 
     return pos;
 }
 
+// ---------------------------------------------------- banded majorant
+// Band of an energy: floor(eps / band width), clamped to the band range.
+__device__ __forceinline__ int band_index64(const DevGas &g, double eps)
+{
+    const double x = eps * g.inv_band_width;
+    if (!(x > 0.0)) return 0;
+    if (x >= (double)g.n_bands) return g.n_bands - 1;
+    const int b = (int)floor(x);
+    return b < g.n_bands ? b : g.n_bands - 1;
+}
+
+__device__ __forceinline__ int band_index32(const DevGas &g, float eps)
+{
+    const float x = fminf(fmaxf(eps * g.inv_band_width_f, 0.0f), g.last_band_f);
+    return __float_as_int(__fadd_rd(x, 8388608.0f)) - 0x4B000000;
+}
+
+// Largest rate over bands lo..hi from the sparse table (two lookups).
+template <typename T>
+__device__ __forceinline__ T band_range_max(const T *bt, int n_bands, int lo, int hi)
+{
+    const int j = 31 - __clz(hi - lo + 1);
+    const T a = bt[j * n_bands + lo], b = bt[j * n_bands + hi - (1 << j) + 1];
+    return a > b ? a : b;
+}
+
 // Isotropic unit vector from two uniforms: cos(theta) = 1 - 2 u, phi = 2 pi v.
 __device__ __forceinline__ void isotropic64(double u, double v, double &nx, double &ny,
                                             double &nz)
@@ -546,7 +584,25 @@ struct Fp64Electron {
         double ex, ey, ez;
         field64<FK>(p.field, plate_e, x, y, z, ex, ey, ez);
         const double ax = -kAccel * ex, ay = -kAccel * ey, az = -kAccel * ez;
-        double dt = -log(u01d(w.x)) * p.gas.inv_nu_max;
+        double nu = p.gas.nu_max, dt;
+        bool pseudo = false;
+        if (p.majorant == GT_MAJORANT_BANDED) {
+            // the rate bound over the energies reachable within the window
+            const double eps0 = (vx * vx + vy * vy + vz * vz) * kInvTwoAccel;
+            const double Em = sqrt(ex * ex + ey * ey + ez * ez);
+            const double tau = p.window / __ldg(p.gas.band64 + band_index64(p.gas, eps0));
+            const double D = Em * (sqrt(vx * vx + vy * vy + vz * vz) * tau +
+                                   0.5 * (kAccel * Em) * tau * tau);
+            nu = band_range_max(p.gas.band64, p.gas.n_bands, band_index64(p.gas, eps0 - D),
+                                band_index64(p.gas, eps0 + D));
+            dt = -log(u01d(w.x)) / nu;
+            if (dt >= tau) {
+                dt = tau;
+                pseudo = true;
+            }
+        } else {
+            dt = -log(u01d(w.x)) * p.gas.inv_nu_max;
+        }
         bool timed = false;
         if (p.t_max > 0.0 && t + dt > p.t_max) {
             dt = p.t_max - t;
@@ -573,9 +629,10 @@ struct Fp64Electron {
             status = GT_ST_TIME;
             return EV_RETIRE;
         }
+        if (pseudo) return EV_NONE;  // the window ended before a collision
         const double eps = (vx * vx + vy * vy + vz * vz) * kInvTwoAccel;
         int lvl = select_level<double, double>(tb.cum64, p.gas.n_levels, p.gas.n_nodes,
-                                                p.gas.inv_d_eps, eps, u01d(w.y) * p.gas.nu_max);
+                                                p.gas.inv_d_eps, eps, u01d(w.y) * nu);
         if (lvl >= 0 && tb.type[lvl] != GT_LEVEL_ELASTIC && eps < tb.thr[lvl]) lvl = -1;
         if (lvl < 0) {
             ++nnull;
@@ -770,15 +827,34 @@ struct MixedElectron {
             return EV_RETIRE;
         }
         const uint4 w = draw(p.seed, aval, uid, nf, 0u);
-        float dt = -__logf(u01f(w.x)) * p.gas.inv_nu_max_f;
+        float ex, ey, ez;
+        field32<FK>(p.field, plate_e, px + ox, py + oy, pz + oz, ex, ey, ez);
+        const float ax = -kAccelF * ex, ay = -kAccelF * ey, az = -kAccelF * ez;
+        float nu = p.gas.nu_max_f, dt;
+        bool pseudo = false;
+        if (p.majorant == GT_MAJORANT_BANDED) {
+            // the rate bound over the energies reachable within the window
+            // (D widened by 1e-5 against FP32 rounding)
+            const float v2 = vx * vx + vy * vy + vz * vz;
+            const float eps0 = v2 * kInvTwoAccelF;
+            const float Em = FK == GT_FIELD_PLATE ? fabsf(plate_e) : sqrtf(ex * ex + ey * ey + ez * ez);
+            const float tau = __fdividef(p.window_f, tb.band32[band_index32(p.gas, eps0)]);
+            const float D = Em * fmaf(0.5f * kAccelF * Em * tau, tau, sqrtf(v2) * tau) * 1.00001f;
+            nu = band_range_max(tb.band32, p.gas.n_bands, band_index32(p.gas, eps0 - D),
+                                band_index32(p.gas, eps0 + D));
+            dt = -__fdividef(__logf(u01f(w.x)), nu);
+            if (dt >= tau) {
+                dt = tau;
+                pseudo = true;
+            }
+        } else {
+            dt = -__logf(u01f(w.x)) * p.gas.inv_nu_max_f;
+        }
         if (ot + dt >= tlim) {  // near the time limit: decide in FP64
             const float2 c = time_cut64(T, ot, dt, p.t_max);
             dt = c.x;
             timed = c.y != 0.0f;
         }
-        float ex, ey, ez;
-        field32<FK>(p.field, plate_e, px + ox, py + oy, pz + oz, ex, ey, ez);
-        const float ax = -kAccelF * ex, ay = -kAccelF * ey, az = -kAccelF * ez;
         float dx, dy, dz;
         if (!p.field.has_b) {
             const float h = 0.5f * dt;
@@ -800,9 +876,10 @@ struct MixedElectron {
             status = GT_ST_TIME;
             return EV_RETIRE;
         }
+        if (pseudo) return EV_NONE;  // the window ended before a collision
         // null test against the interpolated total rate
         const float eps = (vx * vx + vy * vy + vz * vz) * kInvTwoAccelF;
-        const float R = u01f(w.y) * p.gas.nu_max_f;
+        const float R = u01f(w.y) * nu;
         const float xk = eps * p.gas.inv_d_eps_f;
         const float tk = __fadd_rd(fminf(xk, p.gas.lastk_f), 8388608.0f);
         const int k = __float_as_int(tk) - 0x4B000000;

@@ -25,12 +25,16 @@ constexpr unsigned FULL = 0xFFFFFFFFu;
 // rows of a warp's random energies start on all 32 banks.
 __host__ __device__ inline int smem_stride(int n_levels) { return n_levels | 1; }
 
-// Dynamic shared memory: the per-thread collision tallies [L][blockDim] and
-// (optionally) the FP32 cumulative table with an odd row stride.
-__host__ __device__ inline size_t shared_bytes(int n_levels, int n_nodes, int block, bool table)
+// Dynamic shared memory: the per-thread collision tallies [L][blockDim], the
+// banded-majorant range-max table, and (optionally) the FP32 cumulative
+// table with an odd row stride.
+__host__ __device__ inline size_t align16(size_t b) { return (b + 15) & ~(size_t)15; }
+
+__host__ __device__ inline size_t shared_bytes(int n_levels, int n_nodes, int block, bool table,
+                                               int band_entries)
 {
-    size_t b = (size_t)n_levels * block * sizeof(uint32_t);
-    b = (b + 15) & ~(size_t)15;
+    size_t b = align16((size_t)n_levels * block * sizeof(uint32_t));
+    b += align16((size_t)band_entries * sizeof(float));
     if (table) b += (size_t)smem_stride(n_levels) * n_nodes * sizeof(float);
     return b;
 }
@@ -51,9 +55,11 @@ __device__ __forceinline__ Tables stage_tables(const RunParams &p, unsigned char
     __shared__ int s_type[GT_MAX_LEVELS];
     const int L = p.gas.n_levels;
     uint32_t *s_tally = reinterpret_cast<uint32_t *>(smem);
-    size_t off = (size_t)L * blockDim.x * sizeof(uint32_t);
-    off = (off + 15) & ~(size_t)15;
-    float *s_cum = reinterpret_cast<float *>(smem + off);
+    const int nb = p.gas.n_bands * p.gas.band_levels;
+    const size_t off_band = align16((size_t)L * blockDim.x * sizeof(uint32_t));
+    float *s_band = reinterpret_cast<float *>(smem + off_band);
+    float *s_cum = reinterpret_cast<float *>(smem + off_band + align16((size_t)nb * sizeof(float)));
+    for (int i = threadIdx.x; i < nb; i += blockDim.x) s_band[i] = p.gas.band32[i];
     for (int i = threadIdx.x; i < L; i += blockDim.x) {
         s_thr[i] = p.gas.thr[i];
         s_thr_f[i] = (float)p.gas.thr[i];
@@ -77,6 +83,7 @@ __device__ __forceinline__ Tables stage_tables(const RunParams &p, unsigned char
     }
     __syncthreads();
     Tables tb;
+    tb.band32 = s_band;
     tb.cum32 = SMEM_TABLE ? s_cum : p.gas.cum32;
     tb.stride32 = SMEM_TABLE ? S : L;
     tb.cum64 = p.gas.cum64;

@@ -51,6 +51,7 @@ class Gas:
     d_eps: float             # eV
     recoil: float = 0.0      # 2m/M (elastic recoil loss), 0 = no loss
     nu_max: float = 0.0      # 1/ns, 0 = derived by the consumer
+    band_width: float = 1.0  # eV per energy band of the banded majorant
 
     @property
     def n_levels(self) -> int:

@@ -61,3 +61,20 @@ def within_sigma(value, expect, se, k=3.0):
 def geometric_cdf(k, p):
     """P(N <= k) for N ~ Geometric(p) on {1, 2, ...}."""
     return 1.0 - (1.0 - p) ** np.asarray(k, float)
+
+
+def ramp_first_collision_survival(t, eps0, cos_a, e_vcm, c):
+    """P(no real collision before t) for an electron starting with energy
+    eps0 (eV) at angle acos(cos_a) to its acceleration a = (e/m)|E| in a
+    gas whose total rate is nu(eps) = c * eps (1/ns per eV), with no
+    magnetic field.
+
+    v(s) = v0 + a s, so eps(s) = |v(s)|^2 / (2 a_1) with a_1 the acceleration
+    per V/cm, and the survival is exp(-int_0^t c eps(s) ds) with
+    int_0^t |v0 + a s|^2 ds = |v0|^2 t + (v0.a) t^2 + |a|^2 t^3 / 3."""
+    a1 = ACCEL_PER_VCM
+    a = a1 * e_vcm
+    v0 = np.sqrt(speed_sq(np.asarray(eps0, float)))
+    t = np.asarray(t, float)
+    integral = v0 * v0 * t + v0 * a * np.asarray(cos_a, float) * t * t + a * a * t ** 3 / 3.0
+    return np.exp(-c * integral / (2.0 * a1))

@@ -374,3 +374,155 @@ def test_plate_subset_reproduces_avalanches(plate_run):
         ia, ib = np.argsort(o["uid"][a]), np.argsort(s["uid"][b])
         for c in ("x1", "y1", "z1", "t1", "e1", "status", "uid"):
             assert np.array_equal(o[c][a][ia], s[c][b][ib])
+
+
+# ------------------------------------------------------- banded majorant
+def test_banded_majorant_drift_closed_form():
+    """The banded majorant is exact: on the constant-rate gas the drift
+    velocity and the energy ledger are unchanged."""
+    w = W.drift_model(n_electrons=20000, n_coll=3000, seed=21)
+    w.gas = W.model_gas(1000.0, exact_nu_max=False)  # nu_max above the rate: nulls exist
+    o = oracle.run(w.gas, w.field, w.primaries, seed=21, coll_limit=3000, majorant=1,
+                   window=2.0, band_width=50.0)
+    dz, dt = o["z1"] - o["z0"], o["t1"] - o["t0"]
+    vd = P.drift_velocity(1000.0, 1000.0)
+    se = np.std(dz - vd * dt) / math.sqrt(len(dz)) / dt.mean()
+    assert P.within_sigma(dz.mean() / dt.mean(), vd, se)
+    assert np.allclose(o["e1"], o["e0"] + 1000.0 * dz, rtol=1e-9, atol=1e-9)
+
+
+def test_banded_majorant_yule():
+    nu_i, T, n_av = 10.0, 0.5, 1500
+    w = W.drift_model(n_electrons=n_av, n_coll=0, e_field=100.0, seed=23)
+    w.gas = W.model_gas(1000.0, nu_ion=nu_i, ion_threshold=0.0, exact_nu_max=False)
+    o = oracle.run(w.gas, w.field, w.primaries, seed=23, t_max=T, majorant=1, window=1.5,
+                   band_width=100.0)
+    n = o["electrons"].astype(float)
+    assert P.within_sigma(n.mean(), math.exp(nu_i * T), n.std() / math.sqrt(n_av))
+
+
+def test_banded_majorant_matches_global_in_distribution():
+    """Same physics, different random-number use: the argon plate with the
+    banded majorant has the same gain distribution, arrival times and
+    collision mix as with the global nu_max (two-sample KS, 3 sigma), in far
+    fewer flights."""
+    from scipy import stats
+    n = 160
+    w = W.plate(n_avalanches=n, e_field=35_000.0, seed=3)
+    g = oracle.run(w.gas, w.field, w.primaries, seed=3, t_max=w.t_max)
+    b = oracle.run(w.gas, w.field, w.primaries, seed=4, t_max=w.t_max, majorant=1,
+                   window=2.0, band_width=1.0)
+    ga = np.bincount(g["aval"][g["status"] == W.ANODE], minlength=n).astype(float)
+    gb = np.bincount(b["aval"][b["status"] == W.ANODE], minlength=n).astype(float)
+    se = math.sqrt(ga.var() / n + gb.var() / n)
+    assert abs(ga.mean() - gb.mean()) < 3 * se
+    assert stats.ks_2samp(np.log1p(ga), np.log1p(gb)).pvalue > 0.01
+    L = w.gas.n_levels
+    fa = g["tallies"][:, :L].sum(0) / g["tallies"][:, :L].sum()
+    fb = b["tallies"][:, :L].sum(0) / b["tallies"][:, :L].sum()
+    assert np.allclose(fa, fb, atol=0.01)  # share of each level among real collisions
+    ta = np.array([g["t1"][(g["aval"] == i) & (g["status"] == W.ANODE)].mean()
+                   for i in range(n) if ga[i] > 0])
+    tb = np.array([b["t1"][(b["aval"] == i) & (b["status"] == W.ANODE)].mean()
+                   for i in range(n) if gb[i] > 0])
+    assert stats.ks_2samp(ta, tb).pvalue > 0.01
+    # real collisions per flight rise several-fold
+    ra = g["tallies"][:, :L].sum() / g["n_flight"].astype(np.int64).sum()
+    rb = b["tallies"][:, :L].sum() / b["n_flight"].astype(np.int64).sum()
+    assert rb > 3 * ra
+
+
+@pytest.mark.parametrize("gas_name", ["argon_like", "ramp", "ramp_above_5eV"])
+def test_banded_majorant_bounds_the_rate_along_every_flight(gas_name):
+    """Thinning is exact only if the majorant is never below the true rate
+    on the flight.  For random starts (energy, angle to the acceleration,
+    field, window, band width) the exact no-B trajectory v0 + a t gives the
+    energy range reached over [0, tau]; the largest tabulated total rate on
+    that range (its ends and every node inside, since the table is linear
+    between nodes) must not exceed the majorant.  The window itself is
+    window / (largest node rate of the start band)."""
+    if gas_name == "argon_like":
+        gas = W.argon_like_gas()
+    else:
+        eps = np.arange(1001, dtype=np.float64) * 0.1
+        if gas_name == "ramp_above_5eV":  # zero-rate bands below 5 eV
+            eps = np.maximum(eps - 5.0, 0.0)
+        gas = W.Gas(np.array([W.ELASTIC], np.int32), np.zeros(1), (34.0 * eps)[:, None], 0.1)
+    nodes = np.arange(gas.n_nodes) * gas.d_eps
+    total = gas.rate.sum(axis=1)
+    rng = np.random.default_rng(41)
+    worst = 0.0
+    for _ in range(3000):
+        bw = rng.choice([0.05, 0.25, 1.0, 5.0])
+        window = rng.choice([0.5, 2.0, 4.0])
+        eps0 = rng.choice([0.0, rng.uniform(0.0, 5.0), rng.uniform(0.0, 60.0)])
+        cos_a = rng.uniform(-1.0, 1.0)
+        e_mag = rng.uniform(0.0, 6.0e4)
+        s0 = math.sqrt(P.speed_sq(eps0))
+        nu_w, tau = oracle.majorant(gas, bw, eps0, s0, e_mag, window)
+        n = max(1, int(math.floor(bw / gas.d_eps + 0.5)))
+        b0 = min(int(eps0 / (n * gas.d_eps)), (gas.n_nodes - 2) // n)
+        bound = total[b0 * n:(b0 + 1) * n + 1].max()
+        bound = bound if bound > 0.0 else total.max() * 2.0 ** -40
+        assert tau == pytest.approx(window / bound, rel=1e-12)
+        assert math.isfinite(nu_w) and nu_w > 0.0
+        a = P.ACCEL_PER_VCM * e_mag
+        # |v(t)|^2 = s0^2 + 2 s0 a cos t + a^2 t^2 is convex in t
+        ends = [0.0, tau]
+        if a > 0.0 and 0.0 < -s0 * cos_a / a < tau:
+            ends.append(-s0 * cos_a / a)
+        v2 = [s0 * s0 + 2.0 * s0 * a * cos_a * t + a * a * t * t for t in ends]
+        e_lo = min(v2) / (2.0 * P.ACCEL_PER_VCM)
+        e_hi = max(v2) / (2.0 * P.ACCEL_PER_VCM)
+        inside = total[(nodes >= e_lo) & (nodes <= e_hi)]
+        true_max = max(np.interp(e_lo, nodes, total), np.interp(e_hi, nodes, total),
+                       inside.max() if inside.size else 0.0)
+        assert true_max <= nu_w * (1.0 + 1e-12), (gas_name, bw, window, eps0, cos_a, e_mag)
+        worst = max(worst, true_max / nu_w)
+    assert worst > 0.9  # the bound is attained closely somewhere (not vacuous)
+
+
+def ramp_workload(n, seed, band_width):
+    """Rate linear in energy, nu = c * eps, 0-100 eV (exact under linear
+    interpolation), E = 10 kV/cm, one real collision per electron, isotropic
+    directions; a quarter of the electrons start at rest (the energy reach
+    of a flight is then the acceleration term alone), the rest with
+    U(0, 20) eV."""
+    c, n_nodes, d_eps = 34.0, 1001, 0.1
+    eps = np.arange(n_nodes, dtype=np.float64) * d_eps
+    gas = W.Gas(np.array([W.ELASTIC], np.int32), np.zeros(1), (c * eps)[:, None], d_eps,
+                0.0, 0.0, band_width)
+    w = W.drift_model(n_electrons=n, n_coll=1, e_field=1.0e4, seed=seed)
+    w.gas = gas
+    e0 = np.random.default_rng(seed + 1).uniform(0.0, 20.0, n)
+    e0[: n // 4] = 0.0
+    w.primaries.e[:] = e0
+    return w, c
+
+
+def ramp_pit(o, w, c):
+    """Probability integral transform of each electron's first-collision
+    time under the closed-form survival: uniform on (0, 1) when exact."""
+    p = w.primaries
+    cos_a = p.dz[o["uid"].astype(np.int64)]  # acceleration is along +z (E along -z)
+    s = P.ramp_first_collision_survival(o["t1"] - o["t0"], o["e0"], cos_a,
+                                        w.field.e0, c)
+    return 1.0 - s
+
+
+@pytest.mark.parametrize("majorant,band_width,window",
+                         [(0, 1.0, 2.0), (1, 1.0, 2.0), (1, 5.0, 2.0), (1, 0.1, 0.5)])
+def test_ramp_first_collision_closed_form(majorant, band_width, window):
+    """A rising rate is where a majorant can fail: the electron gains energy
+    during the flight, so a bound taken at the start energy, or without
+    the drift or the acceleration term of the energy reach, falls below
+    the rate along the path and delays the collisions.  The first real
+    collision times follow the closed-form survival exactly (KS of the
+    probability integral transform against the uniform law)."""
+    from scipy import stats
+    w, c = ramp_workload(40000, 31, band_width)
+    o = oracle.run(w.gas, w.field, w.primaries, seed=31, coll_limit=1, majorant=majorant,
+                   window=window, band_width=band_width)
+    assert np.all(o["status"] == W.COLL_LIMIT)
+    u = ramp_pit(o, w, c)
+    assert stats.kstest(u, "uniform").pvalue > 0.01
