@@ -433,13 +433,14 @@ def run_reference(args) -> None:
     import oracle
     oracle.build()
     w = W.plate_batched(n_avalanches=args.avalanches, seed=0)
+    per_step = max(1, args.cpu_avalanches // 2)
     for _ in range(args.warmup):
-        oracle_baseline(w, 0, max(1, args.cpu_avalanches // 8), args)
+        oracle_baseline(w, 0, max(1, per_step // 8), args)
     real = 0
     secs = 0.0
     res = None
     for _ in range(args.steps):
-        res = oracle_baseline(w, 0, args.cpu_avalanches, args)
+        res = oracle_baseline(w, 0, per_step, args)
         real += res["real_collisions"]
         secs += res["seconds"]
     value = real / secs
@@ -466,7 +467,9 @@ def parse(argv=None):
     ap.add_argument("--block", type=int, default=0)
     ap.add_argument("--refill-period", type=int, default=0)
     ap.add_argument("--flights-per-phase", type=int, default=0)
-    ap.add_argument("--cpu-avalanches", type=int, default=64)
+    # the oracle's sample: ~10-15 s of CPU work on 16 Arm cores (banded majorant);
+    # the reference arm takes half of it per step
+    ap.add_argument("--cpu-avalanches", type=int, default=512)
     ap.add_argument("--plain-avalanches", type=int, default=32)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-plain", action="store_true")
