@@ -36,12 +36,12 @@ WORKLOAD = "plate_batched_4096"
 # Roofline of the batched transport kernel (bound: instruction issue of the
 # SM's ALU/FMA pipes).  Algorithmic work per flight = lane instructions of
 # the straight-line step: ncu smsp__thread_inst_executed.sum / flights on
-# `bench.py --calibrate --steps 1 --block 1024 --refill-period 16
-# --flights-per-phase 4` with the default banded majorant
+# `bench.py --calibrate --steps 1 --block 1024 --refill-period 32
+# --flights-per-phase 1` with the default banded majorant
 # (profiles/k_batched_mixed_plate_batched_4096.md).  Lanes switched off by
 # divergence are not counted, so divergence, stalls and queue work all show
 # as lost efficiency.
-LANE_INST_PER_FLIGHT = 485.0
+LANE_INST_PER_FLIGHT = 470.3
 SM_COUNT = 152
 ISSUE_PER_SM_PER_CLK = 4       # warp schedulers per SM, one instruction each per clock
 LANES_PER_WARP = 32
@@ -49,7 +49,7 @@ LANES_PER_WARP = 32
 # dram__bytes_write.sum on the 256-avalanche case, divided by its
 # electrons; traffic grows with electrons, so it is scaled to a launch by
 # the electrons the launch stores).  None once the kernel has changed.
-DRAM_BYTES_PER_ELECTRON = 208.0
+DRAM_BYTES_PER_ELECTRON = None
 
 
 # ---------------------------------------------------------------- sharding

@@ -162,7 +162,8 @@ typedef struct {
                                          lane fly up to this many flights until it
                                          meets a real collision, then the warp
                                          applies its lanes' collisions together;
-                                         0 = default */
+                                         0 = default (1 with the banded majorant,
+                                         6 with the global one) */
     int32_t majorant;                 /* GT_MAJORANT_GLOBAL / GT_MAJORANT_BANDED */
     int32_t pad;
     double majorant_window;           /* banded: window factor c, 0 = 2 */
@@ -315,10 +316,12 @@ int avalanche_run_static(gt_ctx *ctx, const gt_run *run, const gt_endpoints *out
  * round (fewer queue refills and FP64 flushes against lanes idling after
  * their electron finishes).  gt_autotune runs `run` in GT_BATCHED mode once
  * per candidate shape (after one warm-up run) and measures real collisions
- * per millisecond of transport kernel time (CUDA events).  The fastest
- * shape is remembered by the context for the run's precision and field
- * kind, and used by later runs that leave block / refill_period /
- * flights_per_phase at 0.
+ * per millisecond of transport kernel time (CUDA events).  Candidates:
+ * MIXED 512/768/1024 threads x refill period 4/8/16/32 x flights per
+ * phase 1/2/4/6 (48); FP64 128/256/512 threads x refill period 8/16/32/64
+ * (12).  The fastest shape is remembered by the context for the run's
+ * precision, field kind and majorant, and used by later runs that leave
+ * block / refill_period / flights_per_phase at 0.
  * points (may be NULL) receives up to max_points measurements, *n_points
  * their number; *best the chosen shape.  Errors as avalanche_run; a
  * candidate that fails is skipped. */

@@ -34,9 +34,10 @@ struct gt_ctx {
     double *d_obs_partials = nullptr;
     size_t obs_partials_cap = 0;
     // autotuned batched launch shape per [precision][field kind] (0 = none)
-    int tuned_block[2][4] = {{0}};
-    int tuned_k[2][4] = {{0}};
-    int tuned_m[2][4] = {{0}};
+    // autotuned launch shapes per [precision][field kind][majorant]
+    int tuned_block[2][4][2] = {};
+    int tuned_k[2][4][2] = {};
+    int tuned_m[2][4][2] = {};
     char last_error[256] = {0};
 };
 
@@ -511,12 +512,15 @@ int avalanche_run(gt_ctx *ctx, const gt_run *r, const gt_endpoints *o, void *ws,
     p.t_max = r->t_max > 0.0 ? r->t_max : 0.0;
     p.coll_limit = r->coll_limit;
     const int prec_i = r->precision == GT_FP64 ? 0 : 1;
-    const int tuned_k = ctx->tuned_k[prec_i][ctx->field.kind & 3];
-    const int tuned_m = ctx->tuned_m[prec_i][ctx->field.kind & 3];
+    const int maj_i = r->majorant == GT_MAJORANT_BANDED ? 1 : 0;
+    const int tuned_k = ctx->tuned_k[prec_i][ctx->field.kind & 3][maj_i];
+    const int tuned_m = ctx->tuned_m[prec_i][ctx->field.kind & 3][maj_i];
     p.refill_period = r->refill_period > 0 ? r->refill_period
-                                           : (tuned_k > 0 ? tuned_k : (prec_i ? 8 : 32));
+                                           : (tuned_k > 0 ? tuned_k : (prec_i ? 16 : 32));
+    // most banded flights end in a real collision, so a round flies once;
+    // with one global nu_max most are null and a round flies several times
     p.flights_per_phase = r->flights_per_phase > 0 ? r->flights_per_phase
-                                                   : (tuned_m > 0 ? tuned_m : 6);
+                                                   : (tuned_m > 0 ? tuned_m : (maj_i ? 1 : 6));
     p.majorant = r->majorant;
     p.window = r->majorant_window > 0.0 ? r->majorant_window : 2.0;
     p.window_f = (float)p.window;
@@ -575,7 +579,7 @@ int avalanche_run(gt_ctx *ctx, const gt_run *r, const gt_endpoints *o, void *ws,
     ++launches;
 
     const bool fp64 = r->precision == GT_FP64;
-    const int tuned_b = ctx->tuned_block[prec_i][ctx->field.kind & 3];
+    const int tuned_b = ctx->tuned_block[prec_i][ctx->field.kind & 3][maj_i];
     const int block = r->block ? r->block
                                : (r->mode == GT_BATCHED && tuned_b > 0 ? tuned_b
                                                                        : default_block(r->precision));
@@ -718,14 +722,14 @@ int gt_autotune(gt_ctx *ctx, const gt_run *run, const gt_endpoints *out, void *w
     // candidate shapes: threads per CTA x refill period (x flights per phase)
     static const int blocks_mixed[] = {512, 768, 1024};
     static const int blocks_fp64[] = {128, 256, 512};
-    static const int ks_mixed[] = {2, 4, 8, 16};
+    static const int ks_mixed[] = {4, 8, 16, 32};
     static const int ks_fp64[] = {8, 16, 32, 64};
-    static const int ms_mixed[] = {4, 6, 8};
+    static const int ms_mixed[] = {1, 2, 4, 6};
     static const int ms_fp64[] = {1};
     const int *blocks = fp64 ? blocks_fp64 : blocks_mixed;
     const int *ks = fp64 ? ks_fp64 : ks_mixed;
     const int *ms = fp64 ? ms_fp64 : ms_mixed;
-    const int nb = 3, nk = 4, nm = fp64 ? 1 : 3;
+    const int nb = 3, nk = 4, nm = fp64 ? 1 : 4;
     gt_stats st{};
     r.block = blocks[0];
     r.refill_period = ks[1];
@@ -756,10 +760,10 @@ int gt_autotune(gt_ctx *ctx, const gt_run *run, const gt_endpoints *out, void *w
     }
     if (n_points) *n_points = n;
     if (top.block == 0) return GT_ERR_UNSUPPORTED;
-    const int pi = fp64 ? 0 : 1;
-    ctx->tuned_block[pi][ctx->field.kind & 3] = top.block;
-    ctx->tuned_k[pi][ctx->field.kind & 3] = top.refill_period;
-    ctx->tuned_m[pi][ctx->field.kind & 3] = top.flights_per_phase;
+    const int pi = fp64 ? 0 : 1, mi = r.majorant == GT_MAJORANT_BANDED ? 1 : 0;
+    ctx->tuned_block[pi][ctx->field.kind & 3][mi] = top.block;
+    ctx->tuned_k[pi][ctx->field.kind & 3][mi] = top.refill_period;
+    ctx->tuned_m[pi][ctx->field.kind & 3][mi] = top.flights_per_phase;
     *best = top;
     return GT_OK;
 }
