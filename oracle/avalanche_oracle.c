@@ -383,21 +383,48 @@ static int band_of(const or_table *t, double eps)
     return b < t->B ? b : t->B - 1;
 }
 
-/* Banded majorant for a flight that starts with energy eps0 and speed
- * `speed` in a field of magnitude Em (V/cm): over a window of
- * tau = window / (rate of the current band) the energy can change by at
- * most D = Em (speed tau + a Em tau^2 / 2) (the field's work along the
- * largest displacement), so the largest rate of the bands covering
- * [eps0 - D, eps0 + D] bounds the true rate along the flight.  Returns
- * that rate and sets *tau. */
-static double banded_majorant(const or_table *tb, double eps0, double speed, double Em,
+/* Banded majorant of one flight with velocity v in the held field E.
+ * The window is tau = window / (bound of the current band).  Within it the
+ * energy stays in a range [lo, hi]:
+ *   no magnetic field: the flight is v + a t, so the energy is
+ *     eps(t) = eps0 + g(t),  g(t) = -(v.E) t + (a1 |E|^2 / 2) t^2
+ *   (the field's work, a convex parabola in t): hi = eps0 + max(g(tau), 0);
+ *   lo = eps0 when v.E <= 0 (g rises from 0), else the vertex value
+ *   eps0 - (v.E) t* / 2 at t* = (v.E) / (a1 |E|^2) if t* < tau, or
+ *   eps0 + g(tau);
+ *   with a magnetic field: |dv/dt| <= a1 |E| along the flight, so the
+ *   displacement stays below |v| tau + a1 |E| tau^2 / 2 and
+ *   [lo, hi] = eps0 -+ |E| (|v| tau + a1 |E| tau^2 / 2).
+ * The majorant is the largest bound of the bands covering [lo, hi]; it
+ * bounds the true rate along the flight because the table is linear
+ * between nodes.  Returns it and sets *tau. */
+static double kinetic_energy(const double v[3]);
+
+static double banded_majorant(const or_table *tb, const double v[3], const double E[3], int has_b,
                               double window, double *tau)
 {
+    double eps0 = kinetic_energy(v);
     double w = window / tb->bmax[band_of(tb, eps0)];
-    double D = Em * (speed * w + 0.5 * (OR_ACCEL_PER_VCM * Em) * w * w);
-    int lo = band_of(tb, eps0 - D), hi = band_of(tb, eps0 + D);
+    double lo, hi;
+    if (!has_b) {
+        double vE = dot3(v, E), E2 = dot3(E, E);
+        double gw = -vE * w + 0.5 * OR_ACCEL_PER_VCM * E2 * w * w;
+        hi = eps0 + (gw > 0.0 ? gw : 0.0);
+        if (vE <= 0.0) {
+            lo = eps0;
+        } else {
+            double ts = vE / (OR_ACCEL_PER_VCM * E2);
+            lo = ts < w ? eps0 - 0.5 * vE * ts : eps0 + gw;
+        }
+    } else {
+        double Em = sqrt(dot3(E, E));
+        double D = Em * (sqrt(dot3(v, v)) * w + 0.5 * (OR_ACCEL_PER_VCM * Em) * w * w);
+        lo = eps0 - D;
+        hi = eps0 + D;
+    }
+    int b0 = band_of(tb, lo), b1 = band_of(tb, hi);
     double nu = 0.0;
-    for (int b = lo; b <= hi; ++b)
+    for (int b = b0; b <= b1; ++b)
         if (tb->bmax[b] > nu) nu = tb->bmax[b];
     *tau = w;
     return nu;
@@ -405,8 +432,8 @@ static double banded_majorant(const or_table *tb, double eps0, double speed, dou
 
 /* Test hook: the banded majorant above for a given gas and band width.
  * Returns the rate (1/ns), or a negative value for a bad table. */
-double or_majorant(const or_gas *g, double band_width, double eps0, double speed, double Em,
-                   double window, double *tau_out)
+double or_majorant(const or_gas *g, double band_width, const double v[3], const double E[3],
+                   int has_b, double window, double *tau_out)
 {
     or_table t;
     if (table_build(g, &t)) return -1.0;
@@ -415,7 +442,7 @@ double or_majorant(const or_gas *g, double band_width, double eps0, double speed
         return -1.0;
     }
     double tau = 0.0;
-    double nu = banded_majorant(&t, eps0, speed, Em, window, &tau);
+    double nu = banded_majorant(&t, v, E, has_b, window, &tau);
     if (tau_out) *tau_out = tau;
     free(t.cum);
     free(t.bmax);
@@ -559,6 +586,7 @@ static void transport_electron(const or_table *tb, const or_field *f, const or_r
     double work = 0.0, inel = 0.0, recoil = 0.0, share = 0.0;
     double w[3] = {-OR_OMEGA_PER_T * f->b[0], -OR_OMEGA_PER_T * f->b[1],
                    -OR_OMEGA_PER_T * f->b[2]}; /* electron: q = -e */
+    const int has_b = f->b[0] != 0.0 || f->b[1] != 0.0 || f->b[2] != 0.0;
     int status = or_boundary(f, r);
     while (status == 0) {
         if (n_flight == 0xFFFFFFFFu) {
@@ -581,8 +609,7 @@ static void transport_electron(const or_table *tb, const or_field *f, const or_r
         int pseudo = 0;
         if (a->majorant == 1) {
             double tau;
-            nu = banded_majorant(tb, kinetic_energy(v), sqrt(dot3(v, v)), sqrt(dot3(E, E)),
-                                 a->window, &tau);
+            nu = banded_majorant(tb, v, E, has_b, a->window, &tau);
             dt = -log(u[0]) / nu;
             if (dt >= tau) {
                 dt = tau;

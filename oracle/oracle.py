@@ -85,8 +85,9 @@ def _load():
             lib.or_select.argtypes = [C.POINTER(_Gas), C.c_double, C.c_double,
                                       C.POINTER(C.c_double)]
             lib.or_select.restype = C.c_int
-            lib.or_majorant.argtypes = [C.POINTER(_Gas)] + [C.c_double] * 5 + [
-                C.POINTER(C.c_double)]
+            lib.or_majorant.argtypes = [C.POINTER(_Gas), C.c_double, C.POINTER(C.c_double),
+                                        C.POINTER(C.c_double), C.c_int, C.c_double,
+                                        C.POINTER(C.c_double)]
             lib.or_majorant.restype = C.c_double
             lib.or_run.argtypes = [C.POINTER(_Gas), C.POINTER(_Field), C.POINTER(_Run),
                                    C.POINTER(C.c_void_p)]
@@ -203,15 +204,17 @@ def select(gas, eps: float, u1: float):
     return j, nm.value
 
 
-def majorant(gas, band_width: float, eps0: float, speed: float, e_mag: float,
-             window: float):
-    """Banded majorant (1/ns) and window tau (ns) of a flight starting with
-    energy eps0 (eV) and speed (cm/ns) in a field of e_mag V/cm."""
+def majorant(gas, band_width: float, v, e_field, has_b: bool, window: float):
+    """Banded majorant (1/ns) and window tau (ns) of a flight with velocity
+    v (cm/ns) in the held field e_field (V/cm); has_b selects the bound for
+    a flight that also turns in a magnetic field."""
     keep = []
     g = _gas_struct(gas, keep)
+    vv = (C.c_double * 3)(*[float(x) for x in v])
+    ee = (C.c_double * 3)(*[float(x) for x in e_field])
     tau = C.c_double(0.0)
-    nu = _load().or_majorant(C.byref(g), float(band_width), float(eps0), float(speed),
-                             float(e_mag), float(window), C.byref(tau))
+    nu = _load().or_majorant(C.byref(g), float(band_width), vv, ee, int(bool(has_b)),
+                             float(window), C.byref(tau))
     if nu < 0.0:
         raise ValueError("bad gas table")
     return nu, tau.value

@@ -436,6 +436,64 @@ __device__ __forceinline__ T band_range_max(const T *bt, int n_bands, int lo, in
     return a > b ? a : b;
 }
 
+// Energy range [lo, hi] of a flight within the window tau in the held field
+// E.  Without B the flight is v + a t and the energy eps0 + g(t) with
+// g(t) = -(v.E) t + (a1 |E|^2 / 2) t^2, a convex parabola: hi is its larger
+// end, lo its vertex (t* = v.E / (a1 |E|^2) when inside the window) or its
+// smaller end.  With B, |dv/dt| <= a1 |E| bounds the displacement, and the
+// range is eps0 -+ |E| (|v| tau + a1 |E| tau^2 / 2).
+__device__ __forceinline__ void reach64(int has_b, double eps0, double vx, double vy, double vz,
+                                        double ex, double ey, double ez, double tau, double &lo,
+                                        double &hi)
+{
+    if (!has_b) {
+        const double vE = vx * ex + vy * ey + vz * ez, E2 = ex * ex + ey * ey + ez * ez;
+        const double gw = -vE * tau + 0.5 * kAccel * E2 * tau * tau;
+        hi = eps0 + (gw > 0.0 ? gw : 0.0);
+        if (vE <= 0.0) {
+            lo = eps0;
+        } else {
+            const double ts = vE / (kAccel * E2);
+            lo = ts < tau ? eps0 - 0.5 * vE * ts : eps0 + gw;
+        }
+    } else {
+        const double Em = sqrt(ex * ex + ey * ey + ez * ez);
+        const double D = Em * (sqrt(vx * vx + vy * vy + vz * vz) * tau +
+                               0.5 * (kAccel * Em) * tau * tau);
+        lo = eps0 - D;
+        hi = eps0 + D;
+    }
+}
+
+// FP32 version, widened by 1e-5 of the energies involved against rounding.
+template <int FK>
+__device__ __forceinline__ void reach32(int has_b, float eps0, float vx, float vy, float vz,
+                                        float ex, float ey, float ez, float plate_e, float tau,
+                                        float &lo, float &hi)
+{
+    if (!has_b) {
+        const float vE = FK == GT_FIELD_PLATE ? -vz * plate_e : fmaf(vx, ex, fmaf(vy, ey, vz * ez));
+        const float E2 = FK == GT_FIELD_PLATE ? plate_e * plate_e
+                                              : fmaf(ex, ex, fmaf(ey, ey, ez * ez));
+        const float q = 0.5f * kAccelF * E2 * tau * tau;  // the acceleration term of g(tau)
+        const float gw = fmaf(-vE, tau, q);
+        const float margin = 1e-5f * (eps0 + fabsf(vE) * tau + q);
+        hi = eps0 + fmaxf(gw, 0.0f) + margin;
+        float l = eps0;
+        if (vE > 0.0f) {
+            const float ts = __fdividef(vE, kAccelF * E2);
+            l = ts < tau ? fmaf(-0.5f * vE, ts, eps0) : eps0 + gw;
+        }
+        lo = l - margin;
+    } else {
+        const float Em = sqrtf(ex * ex + ey * ey + ez * ez);
+        const float D = Em * fmaf(0.5f * kAccelF * Em * tau, tau,
+                                  sqrtf(vx * vx + vy * vy + vz * vz) * tau) * 1.00001f;
+        lo = eps0 - D;
+        hi = eps0 + D;
+    }
+}
+
 // Isotropic unit vector from two uniforms: cos(theta) = 1 - 2 u, phi = 2 pi v.
 __device__ __forceinline__ void isotropic64(double u, double v, double &nx, double &ny,
                                             double &nz)
@@ -589,12 +647,11 @@ struct Fp64Electron {
         if (p.majorant == GT_MAJORANT_BANDED) {
             // the rate bound over the energies reachable within the window
             const double eps0 = (vx * vx + vy * vy + vz * vz) * kInvTwoAccel;
-            const double Em = sqrt(ex * ex + ey * ey + ez * ez);
             const double tau = p.window / __ldg(p.gas.band64 + band_index64(p.gas, eps0));
-            const double D = Em * (sqrt(vx * vx + vy * vy + vz * vz) * tau +
-                                   0.5 * (kAccel * Em) * tau * tau);
-            nu = band_range_max(p.gas.band64, p.gas.n_bands, band_index64(p.gas, eps0 - D),
-                                band_index64(p.gas, eps0 + D));
+            double lo, hi;
+            reach64(p.field.has_b, eps0, vx, vy, vz, ex, ey, ez, tau, lo, hi);
+            nu = band_range_max(p.gas.band64, p.gas.n_bands, band_index64(p.gas, lo),
+                                band_index64(p.gas, hi));
             dt = -log(u01d(w.x)) / nu;
             if (dt >= tau) {
                 dt = tau;
@@ -834,14 +891,12 @@ struct MixedElectron {
         bool pseudo = false;
         if (p.majorant == GT_MAJORANT_BANDED) {
             // the rate bound over the energies reachable within the window
-            // (D widened by 1e-5 against FP32 rounding)
-            const float v2 = vx * vx + vy * vy + vz * vz;
-            const float eps0 = v2 * kInvTwoAccelF;
-            const float Em = FK == GT_FIELD_PLATE ? fabsf(plate_e) : sqrtf(ex * ex + ey * ey + ez * ez);
+            const float eps0 = (vx * vx + vy * vy + vz * vz) * kInvTwoAccelF;
             const float tau = __fdividef(p.window_f, tb.band32[band_index32(p.gas, eps0)]);
-            const float D = Em * fmaf(0.5f * kAccelF * Em * tau, tau, sqrtf(v2) * tau) * 1.00001f;
-            nu = band_range_max(tb.band32, p.gas.n_bands, band_index32(p.gas, eps0 - D),
-                                band_index32(p.gas, eps0 + D));
+            float lo, hi;
+            reach32<FK>(p.field.has_b, eps0, vx, vy, vz, ex, ey, ez, plate_e, tau, lo, hi);
+            nu = band_range_max(tb.band32, p.gas.n_bands, band_index32(p.gas, lo),
+                                band_index32(p.gas, hi));
             dt = -__fdividef(__logf(u01f(w.x)), nu);
             if (dt >= tau) {
                 dt = tau;

@@ -432,7 +432,7 @@ def test_banded_majorant_matches_global_in_distribution():
     assert rb > 3 * ra
 
 
-@pytest.mark.parametrize("gas_name", ["argon_like", "ramp", "ramp_above_5eV"])
+@pytest.mark.parametrize("gas_name", ["argon_like", "ramp", "ramp_above_5eV", "v_shape"])
 def test_banded_majorant_bounds_the_rate_along_every_flight(gas_name):
     """Thinning is exact only if the majorant is never below the true rate
     on the flight.  For random starts (energy, angle to the acceleration,
@@ -447,6 +447,8 @@ def test_banded_majorant_bounds_the_rate_along_every_flight(gas_name):
         eps = np.arange(1001, dtype=np.float64) * 0.1
         if gas_name == "ramp_above_5eV":  # zero-rate bands below 5 eV
             eps = np.maximum(eps - 5.0, 0.0)
+        if gas_name == "v_shape":  # falling below 20 eV: the lower end of the range counts
+            eps = np.abs(eps - 20.0)
         gas = W.Gas(np.array([W.ELASTIC], np.int32), np.zeros(1), (34.0 * eps)[:, None], 0.1)
     nodes = np.arange(gas.n_nodes) * gas.d_eps
     total = gas.rate.sum(axis=1)
@@ -456,10 +458,14 @@ def test_banded_majorant_bounds_the_rate_along_every_flight(gas_name):
         bw = rng.choice([0.05, 0.25, 1.0, 5.0])
         window = rng.choice([0.5, 2.0, 4.0])
         eps0 = rng.choice([0.0, rng.uniform(0.0, 5.0), rng.uniform(0.0, 60.0)])
-        cos_a = rng.uniform(-1.0, 1.0)
-        e_mag = rng.uniform(0.0, 6.0e4)
+        e_mag = rng.choice([0.0, rng.uniform(0.0, 6.0e4)], p=[0.05, 0.95])
         s0 = math.sqrt(P.speed_sq(eps0))
-        nu_w, tau = oracle.majorant(gas, bw, eps0, s0, e_mag, window)
+        n_v, n_e = rng.normal(size=3), rng.normal(size=3)
+        v = s0 * n_v / np.linalg.norm(n_v)
+        e_vec = e_mag * n_e / np.linalg.norm(n_e)
+        # angle between the velocity and the acceleration -(e/m) E
+        cos_a = -float(np.dot(n_v, n_e)) / (np.linalg.norm(n_v) * np.linalg.norm(n_e))
+        nu_w, tau = oracle.majorant(gas, bw, v, e_vec, False, window)
         n = max(1, int(math.floor(bw / gas.d_eps + 0.5)))
         b0 = min(int(eps0 / (n * gas.d_eps)), (gas.n_nodes - 2) // n)
         bound = total[b0 * n:(b0 + 1) * n + 1].max()
@@ -480,6 +486,32 @@ def test_banded_majorant_bounds_the_rate_along_every_flight(gas_name):
         assert true_max <= nu_w * (1.0 + 1e-12), (gas_name, bw, window, eps0, cos_a, e_mag)
         worst = max(worst, true_max / nu_w)
     assert worst > 0.9  # the bound is attained closely somewhere (not vacuous)
+
+
+def test_banded_majorant_bounds_the_rate_with_magnetic_field():
+    """With B the flight turns; the majorant must still cover the tabulated
+    rate at every point of the trajectory within the window, here sampled
+    50 times along an RK4 integration of the Lorentz force."""
+    gas = W.argon_like_gas()
+    nodes = np.arange(gas.n_nodes) * gas.d_eps
+    total = gas.rate.sum(axis=1)
+    rng = np.random.default_rng(43)
+    for _ in range(60):
+        eps0 = rng.uniform(0.0, 30.0)
+        e_vec = rng.normal(size=3)
+        e_vec *= rng.uniform(1.0e3, 6.0e4) / np.linalg.norm(e_vec)
+        b_vec = rng.normal(size=3)
+        b_vec *= rng.uniform(0.1, 4.0) / np.linalg.norm(b_vec)
+        n_v = rng.normal(size=3)
+        v = math.sqrt(P.speed_sq(eps0)) * n_v / np.linalg.norm(n_v)
+        nu_w, tau = oracle.majorant(gas, 1.0, v, e_vec, True, 2.0)
+        a = -P.ACCEL_PER_VCM * e_vec
+        w = -P.OMEGA_PER_T * b_vec
+        r, u = np.zeros(3), v.copy()
+        for _ in range(50):
+            r, u = _rk4(r, u, a, w, tau / 50, n=20)
+            eps = float(np.dot(u, u)) / (2.0 * P.ACCEL_PER_VCM)
+            assert np.interp(eps, nodes, total) <= nu_w * (1.0 + 1e-12)
 
 
 def ramp_workload(n, seed, band_width):
