@@ -41,7 +41,7 @@ WORKLOAD = "plate_batched_4096"
 # (profiles/k_batched_mixed_plate_batched_4096.md).  Lanes switched off by
 # divergence are not counted, so divergence, stalls and queue work all show
 # as lost efficiency.
-LANE_INST_PER_FLIGHT = 470.3
+LANE_INST_PER_FLIGHT = 485.3
 SM_COUNT = 152
 ISSUE_PER_SM_PER_CLK = 4       # warp schedulers per SM, one instruction each per clock
 LANES_PER_WARP = 32

@@ -218,6 +218,7 @@ struct Tables {
     const double *thr;      // shared [L]
     const float *thr_f;     // shared [L]
     uint32_t *tally;        // shared [L][blockDim]: real collisions per level
+    double *base;           // shared [4][blockDim]: FP64 position/time bases (mixed)
     int stride32;           // odd in shared memory: rows start on every bank
 };
 
@@ -410,6 +411,25 @@ __device__ __forceinline__ int select_level32(const float *cum, int stride, int 
     return pos;
 }
 
+// Level of a real collision whose R = u1 nu is known to lie below the total
+// rate at fraction f of the table interval starting at row c0 (stride
+// `stride`): the first level whose running sum exceeds R, by a branch-free
+// binary search over the levels below the last.
+__device__ __forceinline__ int select_below_total32(const float *c0, int stride, int L, float f,
+                                                    float Rv)
+{
+    const float *c1 = c0 + stride;
+    const int m = L - 1;
+    int pos = 0;
+    if (m > 0) {
+        for (int step = 1 << (31 - __clz(m)); step > 0; step >>= 1) {
+            const int j = pos + step - 1;
+            if (j < m && fmaf(f, c1[j] - c0[j], c0[j]) <= Rv) pos += step;
+        }
+    }
+    return pos;
+}
+
 // ---------------------------------------------------- banded majorant
 // Band of an energy: floor(eps / band width), clamped to the band range.
 __device__ __forceinline__ int band_index64(const DevGas &g, double eps)
@@ -530,7 +550,7 @@ template <class E, class C>
 __device__ __forceinline__ void store_birth(const RunParams &p, int64_t s, const E &parent,
                                             const C &c)
 {
-    parent.position(p.x0[s], p.y0[s], p.z0[s], p.t0[s]);
+    parent.position(p, p.x0[s], p.y0[s], p.z0[s], p.t0[s]);
     p.e0[s] = (double)c.e;
     p.bvx[s] = (double)c.vx; p.bvy[s] = (double)c.vy; p.bvz[s] = (double)c.vz;
     p.uid[s] = c.uid;
@@ -549,26 +569,30 @@ static __device__ __noinline__ bool below_threshold64(float vx, float vy, float 
 }
 
 // The FP64 time-limit decision of a flight that ends near t_max: x = the
-// flight time, truncated to reach t_max exactly if T + ot + dt > t_max;
-// y = 1 if truncated.  Out of line for the same reason: nvcc turns a short
-// rarely-taken branch into predicated code that issues on every flight.
-static __device__ __noinline__ float2 time_cut64(double T, float ot, float dt, double t_max)
+// flight time, truncated to reach t_max exactly if T + ot + dt > t_max
+// (T = *t_base); y = 1 if truncated.  Out of line for the same reason: nvcc
+// turns a short rarely-taken branch into predicated code that issues on
+// every flight.
+static __device__ __noinline__ float2 time_cut64(const double *t_base, float ot, float dt,
+                                                 double t_max)
 {
+    const double T = *t_base;
     if (T + (double)(ot + dt) > t_max)
         return make_float2(fmaxf((float)((t_max - T) - (double)ot), 0.0f), 1.0f);
     return make_float2(dt, 0.0f);
 }
 
-// FP64 boundary test of the position X + o (same role as above: only
+// FP64 boundary test of the position base + o (same role as above: only
 // reached when the FP32 pre-test falls inside its margin).
 template <int FK>
-static __device__ __noinline__ int boundary_confirm64(double X, double Y, double Z, float ox,
-                                                      float oy, float oz, double gap,
-                                                      double wire_r2, double tube_r2,
-                                                      double lo0, double lo1, double lo2,
-                                                      double hi0, double hi1, double hi2)
+static __device__ __noinline__ int boundary_confirm64(const double *xb, const double *yb,
+                                                      const double *zb, float ox, float oy,
+                                                      float oz, double gap, double wire_r2,
+                                                      double tube_r2, double lo0, double lo1,
+                                                      double lo2, double hi0, double hi1,
+                                                      double hi2)
 {
-    const double x = X + (double)ox, y = Y + (double)oy, z = Z + (double)oz;
+    const double x = *xb + (double)ox, y = *yb + (double)oy, z = *zb + (double)oz;
     if (FK == GT_FIELD_PLATE) {
         if (z >= gap) return GT_ST_ANODE;
         if (z < 0.0) return GT_ST_CATHODE;
@@ -597,13 +621,16 @@ struct Fp64Electron {
 
     double x, y, z, t, vx, vy, vz;
     double plate_e;
+
+    __device__ __forceinline__ void bind(const Tables &) {}
     uint32_t nf, nreal, nnull;
     int status;
     int aval;
     uint64_t uid;
     int64_t slot;
 
-    __device__ __forceinline__ void position(double &ox_, double &oy_, double &oz_, double &ot_) const
+    __device__ __forceinline__ void position(const RunParams &, double &ox_, double &oy_,
+                                             double &oz_, double &ot_) const
     {
         ox_ = x; oy_ = y; oz_ = z; ot_ = t;
     }
@@ -766,35 +793,49 @@ struct Fp64Electron {
 // The step is split in two so that a warp can handle its lanes' real
 // collisions together: advance() makes one free flight and the null test
 // against the interpolated total rate; a lane that meets a real collision
-// keeps its random words (`pending`) until collide() selects the level and
-// scatters.  Each electron still takes exactly the sequence
-// flight, collision, flight, ... with the same random numbers.
+// keeps its random words and table position (a Pending record, local to
+// one collision round) until collide() selects the level and scatters.
+// Each electron still takes exactly the sequence flight, collision,
+// flight, ... with the same random numbers.
 struct MixedElectron {
     static constexpr bool kTwoPhase = true;
     struct ChildT {
         float e, vx, vy, vz;
         uint64_t uid;
     };
+    struct Pending {
+        float R;          // u1 * majorant
+        float eps, f;     // energy at the collision, fraction within table interval k
+        int k;
+        uint32_t w2, w3;  // direction words
+        bool real;
+    };
 
-    double X, Y, Z, T;       // FP64 absolute position and time at the last flush
+    // The FP64 absolute position and time at the last flush live in the
+    // thread's shared-memory slot (b[0], b[S], b[2S], b[3S], S = blockDim),
+    // not in registers: they are read only at flushes, ionisations and the
+    // rare FP64 confirmations.
+    double *b;
     float ox, oy, oz, ot;    // FP32 offsets since the last flush
     float vx, vy, vz;        // FP32 velocity
     float px, py, pz;        // FP32 copy of (X, Y, Z) for field and pre-tests
     float zhi, zlo, tlim;    // pre-test limits for the offsets (see flush)
     float plate_e;
-    float pR;                // pending collision: R = u1 nu_max
-    uint32_t pw2, pw3;       // pending collision: direction words
     uint32_t nf, nreal, nnull;
     int status;
     int aval;
-    bool timed, pending;
+    bool timed;
     uint64_t uid;
     int64_t slot;
 
-    __device__ __forceinline__ void position(double &x_, double &y_, double &z_, double &t_) const
+    __device__ __forceinline__ void bind(const Tables &tb) { b = tb.base + threadIdx.x; }
+
+    __device__ __forceinline__ void position(const RunParams &, double &x_, double &y_,
+                                             double &z_, double &t_) const
     {
-        x_ = X + (double)ox; y_ = Y + (double)oy; z_ = Z + (double)oz;
-        t_ = T + (double)ot;
+        const unsigned S = blockDim.x;
+        x_ = b[0] + (double)ox; y_ = b[S] + (double)oy;
+        z_ = b[2 * S] + (double)oz; t_ = b[3 * S] + (double)ot;
     }
 
     // Fold the FP32 offsets into the FP64 state and refresh the FP32
@@ -802,7 +843,18 @@ struct MixedElectron {
     template <int FK>
     __device__ __forceinline__ void flush(const RunParams &p)
     {
-        X += (double)ox; Y += (double)oy; Z += (double)oz; T += (double)ot;
+        const unsigned S = blockDim.x;
+        set_base<FK>(p, b[0] + (double)ox, b[S] + (double)oy, b[2 * S] + (double)oz,
+                     b[3 * S] + (double)ot);
+    }
+
+    // New FP64 base (X, Y, Z, T) with zero offsets, and the pre-test limits.
+    template <int FK>
+    __device__ __forceinline__ void set_base(const RunParams &p, double X, double Y, double Z,
+                                             double T)
+    {
+        const unsigned S = blockDim.x;
+        b[0] = X; b[S] = Y; b[2 * S] = Z; b[3 * S] = T;
         ox = oy = oz = ot = 0.f;
         if (FK == GT_FIELD_COAX || FK == GT_FIELD_GRID) {
             px = (float)X; py = (float)Y;
@@ -825,22 +877,20 @@ struct MixedElectron {
     __device__ void load_birth(const RunParams &p, int64_t s)
     {
         slot = s;
-        X = p.x0[s]; Y = p.y0[s]; Z = p.z0[s]; T = p.t0[s];
         vx = (float)p.bvx[s]; vy = (float)p.bvy[s]; vz = (float)p.bvz[s];
         uid = p.uid[s];
         aval = p.aval[s];
         plate_e = (float)(p.aval_field ? p.aval_field[aval] : p.field.e0);
         nf = nreal = nnull = 0;
         status = 0;
-        timed = pending = false;
-        ox = oy = oz = ot = 0.f;
-        flush<FK>(p);
+        timed = false;
+        set_base<FK>(p, p.x0[s], p.y0[s], p.z0[s], p.t0[s]);
     }
 
     template <int FK>
     __device__ __forceinline__ int check_start(const RunParams &p)
     {
-        status = boundary64<FK>(p.field, X, Y, Z);
+        status = boundary64<FK>(p.field, p.x0[slot], p.y0[slot], p.z0[slot]);
         return status ? EV_RETIRE : EV_NONE;
     }
 
@@ -868,17 +918,19 @@ struct MixedElectron {
         }
         if (!maybe) return 0;
         const DevField &f = p.field;
-        return boundary_confirm64<FK>(X, Y, Z, ox, oy, oz, f.gap, f.wire_r2, f.tube_r2,
-                                      f.origin[0], f.origin[1], f.origin[2], f.hi[0], f.hi[1],
-                                      f.hi[2]);
+        const unsigned S = blockDim.x;
+        return boundary_confirm64<FK>(b, b + S, b + 2 * S, ox, oy, oz, f.gap, f.wire_r2,
+                                      f.tube_r2, f.origin[0], f.origin[1], f.origin[2], f.hi[0],
+                                      f.hi[1], f.hi[2]);
     }
 
     // One free flight and the real/null decision (Fig. 2 "Find E field and
     // add random time step", "Collision?").  Returns EV_RETIRE or EV_NONE;
-    // sets `pending` for a real collision.
+    // fills `pd` (pd.real) for a real collision.
     template <int FK>
-    __device__ __forceinline__ int advance(const RunParams &p, const Tables &tb)
+    __device__ __forceinline__ int advance(const RunParams &p, const Tables &tb, Pending &pd)
     {
+        pd.real = false;
         if (nf == 0xFFFFFFFFu) {
             status = GT_ST_FLIGHT_LIMIT;
             return EV_RETIRE;
@@ -906,7 +958,7 @@ struct MixedElectron {
             dt = -__logf(u01f(w.x)) * p.gas.inv_nu_max_f;
         }
         if (ot + dt >= tlim) {  // near the time limit: decide in FP64
-            const float2 c = time_cut64(T, ot, dt, p.t_max);
+            const float2 c = time_cut64(b + 3 * blockDim.x, ot, dt, p.t_max);
             dt = c.x;
             timed = c.y != 0.0f;
         }
@@ -943,10 +995,13 @@ struct MixedElectron {
         const float *c0 = tb.cum32 + k * tb.stride32 + (L - 1);
         const float top = fmaf(f, c0[tb.stride32] - c0[0], c0[0]);
         if (R < top) {
-            pending = true;
-            pR = R;
-            pw2 = w.z;
-            pw3 = w.w;
+            pd.real = true;
+            pd.R = R;
+            pd.eps = eps;
+            pd.k = k;
+            pd.f = f;
+            pd.w2 = w.z;
+            pd.w3 = w.w;
         } else {
             ++nnull;
         }
@@ -956,13 +1011,13 @@ struct MixedElectron {
     // The pending real collision (Fig. 2 "Collision is ionisation or
     // attachment?"): level selection, threshold guard, isotropic scattering.
     template <int FK>
-    __device__ __forceinline__ int collide(const RunParams &p, const Tables &tb, ChildT &ch)
+    __device__ __forceinline__ int collide(const RunParams &p, const Tables &tb, Pending &pd,
+                                           ChildT &ch)
     {
-        pending = false;
-        const float eps = (vx * vx + vy * vy + vz * vz) * kInvTwoAccelF;
-        int lvl = select_level32(tb.cum32, tb.stride32, p.gas.n_levels, p.gas.lastk_f,
-                                 p.gas.last_x_f, p.gas.inv_d_eps_f, eps, pR);
-        if (lvl < 0) lvl = p.gas.n_levels - 1;  // R was below the total rate
+        pd.real = false;
+        const float eps = pd.eps;
+        const int lvl = select_below_total32(tb.cum32 + pd.k * tb.stride32, tb.stride32,
+                                             p.gas.n_levels, pd.f, pd.R);
         const int type = tb.type[lvl];
         if (type != GT_LEVEL_ELASTIC) {
             const float th = tb.thr_f[lvl];
@@ -975,7 +1030,7 @@ struct MixedElectron {
         }
         tb.tally[lvl * blockDim.x + threadIdx.x] += 1u;
         float nx, ny, nz;
-        isotropic32(u01f(pw2), u01f(pw3), nx, ny, nz);
+        isotropic32(u01f(pd.w2), u01f(pd.w3), nx, ny, nz);
         float sp;
         int ev = EV_NONE;
         if (type == GT_LEVEL_ELASTIC) {
@@ -1017,9 +1072,10 @@ struct MixedElectron {
     template <int FK>
     __device__ __forceinline__ int fly(const RunParams &p, const Tables &tb, ChildT &ch)
     {
-        const int ev = advance<FK>(p, tb);
-        if (ev || !pending) return ev;
-        return collide<FK>(p, tb, ch);
+        Pending pd;
+        const int ev = advance<FK>(p, tb, pd);
+        if (ev || !pd.real) return ev;
+        return collide<FK>(p, tb, pd, ch);
     }
 
     template <int FK>
@@ -1030,8 +1086,10 @@ struct MixedElectron {
 
     __device__ void write_end(const RunParams &p) const
     {
-        p.x1[slot] = X + (double)ox; p.y1[slot] = Y + (double)oy; p.z1[slot] = Z + (double)oz;
-        p.t1[slot] = timed ? p.t_max : T + (double)ot;
+        double x, y, z, t;
+        position(p, x, y, z, t);
+        p.x1[slot] = x; p.y1[slot] = y; p.z1[slot] = z;
+        p.t1[slot] = timed ? p.t_max : t;
         p.e1[slot] = ((double)vx * vx + (double)vy * vy + (double)vz * vz) * kInvTwoAccel;
         p.status[slot] = status;
         p.nflight[slot] = nf;
@@ -1040,8 +1098,7 @@ struct MixedElectron {
     template <int FK>
     __device__ void save(const RunParams &p, const Stack &s, int64_t i)
     {
-        flush<FK>(p);
-        s.x[i] = X; s.y[i] = Y; s.z[i] = Z; s.t[i] = T;
+        position(p, s.x[i], s.y[i], s.z[i], s.t[i]);
         s.vx[i] = vx; s.vy[i] = vy; s.vz[i] = vz;
         s.nf[i] = nf; s.nreal[i] = nreal; s.uid[i] = uid; s.slot[i] = slot;
     }
@@ -1049,16 +1106,14 @@ struct MixedElectron {
     template <int FK>
     __device__ void restore(const RunParams &p, const Stack &s, int64_t i, int av)
     {
-        X = s.x[i]; Y = s.y[i]; Z = s.z[i]; T = s.t[i];
         vx = (float)s.vx[i]; vy = (float)s.vy[i]; vz = (float)s.vz[i];
         nf = s.nf[i]; nreal = s.nreal[i]; uid = s.uid[i]; slot = s.slot[i];
         aval = av;
         plate_e = (float)(p.aval_field ? p.aval_field[aval] : p.field.e0);
         nnull = 0;
         status = 0;
-        timed = pending = false;
-        ox = oy = oz = ot = 0.f;
-        flush<FK>(p);
+        timed = false;
+        set_base<FK>(p, s.x[i], s.y[i], s.z[i], s.t[i]);
     }
 };
 

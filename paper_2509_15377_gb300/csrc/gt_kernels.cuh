@@ -25,15 +25,17 @@ constexpr unsigned FULL = 0xFFFFFFFFu;
 // rows of a warp's random energies start on all 32 banks.
 __host__ __device__ inline int smem_stride(int n_levels) { return n_levels | 1; }
 
-// Dynamic shared memory: the per-thread collision tallies [L][blockDim], the
-// banded-majorant range-max table, and (optionally) the FP32 cumulative
-// table with an odd row stride.
+// Dynamic shared memory: the per-thread FP64 position/time bases
+// [4][blockDim] (mixed precision), the per-thread collision tallies
+// [L][blockDim], the banded-majorant range-max table, and (optionally) the
+// FP32 cumulative table with an odd row stride.
 __host__ __device__ inline size_t align16(size_t b) { return (b + 15) & ~(size_t)15; }
 
 __host__ __device__ inline size_t shared_bytes(int n_levels, int n_nodes, int block, bool table,
                                                int band_entries)
 {
-    size_t b = align16((size_t)n_levels * block * sizeof(uint32_t));
+    size_t b = (size_t)4 * block * sizeof(double);
+    b += align16((size_t)n_levels * block * sizeof(uint32_t));
     b += align16((size_t)band_entries * sizeof(float));
     if (table) b += (size_t)smem_stride(n_levels) * n_nodes * sizeof(float);
     return b;
@@ -54,9 +56,11 @@ __device__ __forceinline__ Tables stage_tables(const RunParams &p, unsigned char
     __shared__ float s_thr_f[GT_MAX_LEVELS];
     __shared__ int s_type[GT_MAX_LEVELS];
     const int L = p.gas.n_levels;
-    uint32_t *s_tally = reinterpret_cast<uint32_t *>(smem);
+    double *s_base = reinterpret_cast<double *>(smem);
+    const size_t off_tally = (size_t)4 * blockDim.x * sizeof(double);
+    uint32_t *s_tally = reinterpret_cast<uint32_t *>(smem + off_tally);
     const int nb = p.gas.n_bands * p.gas.band_levels;
-    const size_t off_band = align16((size_t)L * blockDim.x * sizeof(uint32_t));
+    const size_t off_band = off_tally + align16((size_t)L * blockDim.x * sizeof(uint32_t));
     float *s_band = reinterpret_cast<float *>(smem + off_band);
     float *s_cum = reinterpret_cast<float *>(smem + off_band + align16((size_t)nb * sizeof(float)));
     for (int i = threadIdx.x; i < nb; i += blockDim.x) s_band[i] = p.gas.band32[i];
@@ -91,6 +95,7 @@ __device__ __forceinline__ Tables stage_tables(const RunParams &p, unsigned char
     tb.thr = s_thr;
     tb.thr_f = s_thr_f;
     tb.tally = s_tally;
+    tb.base = s_base;
     return tb;
 }
 
@@ -172,7 +177,7 @@ __device__ __forceinline__ int push_children(const RunParams &p, bool want, cons
     return 0;
 }
 
-template <class E, int FK, bool SMEM_TABLE, int MAXT>
+template <class E, int FK, bool SMEM_TABLE, int MAXT, int MP = 0>
 __global__ void __launch_bounds__(MAXT) k_batched(const RunParams p)
 {
     extern __shared__ __align__(16) unsigned char smem[];
@@ -182,6 +187,7 @@ __global__ void __launch_bounds__(MAXT) k_batched(const RunParams p)
     const int K = p.refill_period;
 
     E e;
+    e.bind(tb);
     bool has = false;
     long long ticket = -1;
 
@@ -253,12 +259,15 @@ __global__ void __launch_bounds__(MAXT) k_batched(const RunParams p)
             // K collision rounds between refills.  In each, lanes without a
             // pending collision fly (at most M flights) until they meet a
             // real one; then the warp applies its lanes' collisions together.
-            const int M = p.flights_per_phase;
+            // MP = 1 builds the one-flight round (M = 1) at compile time.
+            const int M = MP ? MP : p.flights_per_phase;
             for (int k = 0; k < K; ++k) {
+                typename E::Pending pd;
+                pd.real = false;
                 for (int mm = 0; mm < M; ++mm) {
-                    const bool go = has && !e.pending;
-                    if (!__any_sync(FULL, go)) break;
-                    if (go && (e.template advance<FK>(p, tb) & EV_RETIRE)) {
+                    const bool go = has && !pd.real;
+                    if (MP != 1 && !__any_sync(FULL, go)) break;
+                    if (go && (e.template advance<FK>(p, tb, pd) & EV_RETIRE)) {
                         finish(p, tb, e, bs);
                         has = false;
                         ++retired;
@@ -266,7 +275,7 @@ __global__ void __launch_bounds__(MAXT) k_batched(const RunParams p)
                 }
                 typename E::ChildT ch;
                 int ev = EV_NONE;
-                if (has && e.pending) ev = e.template collide<FK>(p, tb, ch);
+                if (pd.real) ev = e.template collide<FK>(p, tb, pd, ch);
                 if (__any_sync(FULL, ev & EV_CHILD))
                     retired += push_children(p, (ev & EV_CHILD) != 0, e, ch, lane);
                 if (ev & EV_RETIRE) {
@@ -321,6 +330,7 @@ __global__ void __launch_bounds__(MAXT)
     if (i >= n_active) return;
 
     E e;
+    e.bind(tb);
     e.template restore<FK>(p, cur, i, aval);
     const uint32_t nf0 = e.nf, nr0 = e.nreal;
     typename E::ChildT ch;
@@ -342,7 +352,7 @@ __global__ void __launch_bounds__(MAXT)
             store_birth(p, (int64_t)s, e, ch);
             p.ready[s] = 1u;
             const unsigned long long j = atomicAdd(&p.hdr->n_new[parity], 1ull);
-            e.position(fresh.x[j], fresh.y[j], fresh.z[j], fresh.t[j]);
+            e.position(p, fresh.x[j], fresh.y[j], fresh.z[j], fresh.t[j]);
             fresh.vx[j] = (double)ch.vx; fresh.vy[j] = (double)ch.vy; fresh.vz[j] = (double)ch.vz;
             fresh.nf[j] = 0u; fresh.nreal[j] = 0u; fresh.uid[j] = ch.uid;
             fresh.slot[j] = (int64_t)s;

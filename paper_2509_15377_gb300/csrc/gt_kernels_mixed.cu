@@ -15,7 +15,10 @@ constexpr int kPlainThreadsMixed = 512;
 template <int FK, bool TAB, int MAXT>
 static cudaError_t batched_t(const RunParams &p, int grid, int block, size_t smem, cudaStream_t s)
 {
-    k_batched<MixedElectron, FK, TAB, MAXT><<<grid, block, smem, s>>>(p);
+    if (p.flights_per_phase == 1)
+        k_batched<MixedElectron, FK, TAB, MAXT, 1><<<grid, block, smem, s>>>(p);
+    else
+        k_batched<MixedElectron, FK, TAB, MAXT, 0><<<grid, block, smem, s>>>(p);
     return cudaGetLastError();
 }
 
@@ -75,16 +78,25 @@ cudaError_t launch_plain_mixed(const RunParams &p, const PlainArgs &a, bool smem
     return smem_table ? plain_fk<true>(p, a, block, smem, s) : plain_fk<false>(p, a, block, smem, s);
 }
 
+template <int FK, bool TAB, int MP>
+static cudaError_t configure_mp(size_t max_smem)
+{
+    cudaError_t e;
+    if ((e = allow_dynamic_smem(k_batched<MixedElectron, FK, TAB, 512, MP>, max_smem)) !=
+        cudaSuccess)
+        return e;
+    if ((e = allow_dynamic_smem(k_batched<MixedElectron, FK, TAB, 768, MP>, max_smem)) !=
+        cudaSuccess)
+        return e;
+    return allow_dynamic_smem(k_batched<MixedElectron, FK, TAB, 1024, MP>, max_smem);
+}
+
 template <int FK, bool TAB>
 static cudaError_t configure_one(size_t max_smem)
 {
     cudaError_t e;
-    if ((e = allow_dynamic_smem(k_batched<MixedElectron, FK, TAB, 512>, max_smem)) != cudaSuccess)
-        return e;
-    if ((e = allow_dynamic_smem(k_batched<MixedElectron, FK, TAB, 768>, max_smem)) != cudaSuccess)
-        return e;
-    if ((e = allow_dynamic_smem(k_batched<MixedElectron, FK, TAB, 1024>, max_smem)) != cudaSuccess)
-        return e;
+    if ((e = configure_mp<FK, TAB, 0>(max_smem)) != cudaSuccess) return e;
+    if ((e = configure_mp<FK, TAB, 1>(max_smem)) != cudaSuccess) return e;
     return allow_dynamic_smem(k_plain_transport<MixedElectron, FK, TAB, kPlainThreadsMixed>,
                               max_smem);
 }
