@@ -83,10 +83,12 @@ enum {
     OR_OUT_OF_MAP = 5,   /* grid: outside the map box */
     OR_TIME = 6,         /* time limit reached */
     OR_COLL_LIMIT = 7,   /* real-collision limit reached */
-    OR_FLIGHT_LIMIT = 8  /* 2^32-1 flights (counter exhausted) */
+    OR_FLIGHT_LIMIT = 8, /* 2^32-1 flights (counter exhausted) */
+    OR_ATTACHED = 9      /* captured by an attachment collision */
 };
 
-enum { OR_ELASTIC = 0, OR_EXCITATION = 1, OR_IONISATION = 2 };
+/* level types: Fig. 2 "Collision is ionisation or attachment?" */
+enum { OR_ELASTIC = 0, OR_EXCITATION = 1, OR_IONISATION = 2, OR_ATTACHMENT = 3 };
 enum { OR_UNIFORM = 0, OR_PLATE = 1, OR_COAX = 2, OR_GRID = 3 };
 
 typedef struct {
@@ -98,6 +100,9 @@ typedef struct {
     const double *rate;        /* [n_nodes][n_levels], 1/ns */
     double recoil;             /* 2m/M for elastic recoil loss; 0 = none */
     double nu_max;             /* 1/ns; 0 = (1+1e-6) * max total rate */
+    const double *xi0;         /* [n_levels] constant anisotropy, or NULL (all 0) */
+    const double *screen;      /* [n_levels] screening energy (eV), or NULL (all 0) */
+    double split_w;            /* ionisation sharing width (eV); 0 = uniform split */
 } or_gas;
 
 typedef struct {
@@ -306,6 +311,8 @@ typedef struct {
     double d_eps, nu_max, recoil;
     int type[64];
     double thr[64];
+    double xi0[64], screen[64]; /* angular model per level (see level_xi) */
+    double split_w;
     double *cum; /* [N][L]: running sum over levels 0..j of the rate */
     double top;  /* largest total rate over the nodes */
     int band_nodes, B; /* banded majorant: nodes per band, number of bands */
@@ -322,7 +329,13 @@ static int table_build(const or_gas *g, or_table *t)
     for (int j = 0; j < t->L; ++j) {
         t->type[j] = g->level_type[j];
         t->thr[j] = g->threshold[j];
+        t->xi0[j] = g->xi0 ? g->xi0[j] : 0.0;
+        t->screen[j] = g->screen ? g->screen[j] : 0.0;
+        if (t->type[j] < OR_ELASTIC || t->type[j] > OR_ATTACHMENT) return -1;
+        if (!(t->xi0[j] > -1.0 && t->xi0[j] < 1.0) || !(t->screen[j] >= 0.0)) return -1;
     }
+    t->split_w = g->split_w;
+    if (!(t->split_w >= 0.0)) return -1;
     t->cum = (double *)malloc(sizeof(double) * (size_t)t->N * t->L);
     if (!t->cum) return -1;
     double top = 0.0;
@@ -559,20 +572,89 @@ static void isotropic(double u_cos, double u_phi, double n[3])
     n[2] = ct;
 }
 
-/* Elastic collision on a heavy target at rest: isotropic new direction n
- * from (u_cos, u_phi); the energy is scaled by 1 - recoil*(1 - cos chi),
- * chi the lab deflection angle and recoil = 2m/M (first order in m/M of
- * the two-body kinematics).  Writes the new velocity. */
-void or_elastic(double recoil, const double v[3], double u_cos, double u_phi, double v_out[3])
+/* Anisotropy of level j at energy eps: the constant xi0 when the level's
+ * screening energy is 0, else eps / (eps + screen) (the screened-Coulomb
+ * form, forward-peaked at high energy). */
+static double level_xi(const or_table *t, int j, double eps)
+{
+    if (t->screen[j] > 0.0) return eps / (eps + t->screen[j]);
+    return t->xi0[j];
+}
+
+/* New unit direction of a scattered electron with incident velocity v.
+ * xi = 0: isotropic in the lab frame (cos theta = 1 - 2 u_cos, phi = 2 pi
+ * u_phi).  Otherwise the deflection chi from the incident direction has the
+ * screened-Coulomb density p(mu) = (1 - xi^2) / (2 (1 - xi mu)^2) in
+ * mu = cos chi (Okhrimovskyy, Bogaerts, Gijbels, Phys. Rev. E 65, 037402,
+ * 2002), sampled by inverting its distribution function:
+ *   mu = (1 + xi - 2 u_cos) / (1 + xi - 2 xi u_cos),
+ * and the azimuth 2 pi u_phi turns about the incident direction d in the
+ * orthonormal frame (e1, e2, d) of Duff et al., "Building an orthonormal
+ * basis, revisited", JCGT 6(1), 2017.  A resting electron has d = +z.
+ * Returns mu (cos chi; for xi = 0 the lab cos theta). */
+static double scatter(double xi, const double v[3], double u_cos, double u_phi, double n[3])
+{
+    if (xi == 0.0) {
+        isotropic(u_cos, u_phi, n);
+        double sp = sqrt(dot3(v, v));
+        return sp > 0.0 ? dot3(v, n) / sp : n[2];
+    }
+    double den = 1.0 + xi - 2.0 * xi * u_cos;
+    double mu = (1.0 + xi - 2.0 * u_cos) / den;
+    double one_minus = 2.0 * u_cos * (1.0 - xi) / den; /* 1 - mu without cancellation */
+    double s2 = one_minus * (2.0 - one_minus);
+    double sc = s2 > 0.0 ? sqrt(s2) : 0.0;               /* sin chi */
+    double sp = sqrt(dot3(v, v));
+    double d[3] = {0.0, 0.0, 1.0};
+    if (sp > 0.0) {
+        d[0] = v[0] / sp; d[1] = v[1] / sp; d[2] = v[2] / sp;
+    }
+    double sg = d[2] >= 0.0 ? 1.0 : -1.0;
+    double a = -1.0 / (sg + d[2]);
+    double b = d[0] * d[1] * a;
+    double e1[3] = {1.0 + sg * d[0] * d[0] * a, sg * b, -sg * d[0]};
+    double e2[3] = {b, sg + d[1] * d[1] * a, -d[1]};
+    double phi = 2.0 * OR_PI * u_phi;
+    double c = cos(phi), s = sin(phi);
+    for (int k = 0; k < 3; ++k) n[k] = mu * d[k] + sc * (c * e1[k] + s * e2[k]);
+    return mu;
+}
+
+/* Test hook: scatter() above. */
+double or_scatter(double xi, const double v[3], double u_cos, double u_phi, double n[3])
+{
+    return scatter(xi, v, u_cos, u_phi, n);
+}
+
+/* Elastic collision on a heavy target at rest: new direction n from
+ * scatter(); the energy is scaled by 1 - recoil*(1 - cos chi), chi the lab
+ * deflection angle and recoil = 2m/M (first order in m/M of the two-body
+ * kinematics).  Writes the new velocity. */
+void or_elastic(double recoil, double xi, const double v[3], double u_cos, double u_phi,
+                double v_out[3])
 {
     double n[3];
-    isotropic(u_cos, u_phi, n);
     double eps = kinetic_energy(v);
     double sp = sqrt(dot3(v, v));
+    scatter(xi, v, u_cos, u_phi, n);
     double cchi = sp > 0.0 ? dot3(v, n) / sp : 0.0;
     double s = speed_of(eps * (1.0 - recoil * (1.0 - cchi)));
     v_out[0] = s * n[0]; v_out[1] = s * n[1]; v_out[2] = s * n[2];
 }
+
+/* Energy of the new electron of an ionisation from the remainder
+ * rest = eps - I: uniform on [0, rest] (w = 0), or with density
+ * proportional to 1 / (1 + (x / w)^2) on [0, rest / 2] (the form of Opal,
+ * Peterson and Beaty, J. Chem. Phys. 55, 4100, 1971), by inversion
+ * x = w tan(u atan(rest / (2 w))). */
+static double ionisation_share(double w, double rest, double u)
+{
+    if (w <= 0.0) return u * rest;
+    return w * tan(u * atan(rest / (2.0 * w)));
+}
+
+/* Test hook: ionisation_share() above. */
+double or_ionisation_share(double w, double rest, double u) { return ionisation_share(w, rest, u); }
 
 /* Transport one electron until its status is non-zero (Fig. 2, dashed box). */
 static void transport_electron(const or_table *tb, const or_field *f, const or_run_args *a,
@@ -644,20 +726,26 @@ static void transport_electron(const or_table *tb, const or_field *f, const or_r
             continue;
         }
         o->tally[lvl] += 1;
+        if (tb->type[lvl] == OR_ATTACHMENT) { /* captured: the electron ends here */
+            status = OR_ATTACHED;
+            break;
+        }
+        const double xi = level_xi(tb, lvl, eps);
         if (tb->type[lvl] == OR_ELASTIC) {
-            or_elastic(tb->recoil, v, u[2], u[3], v);
+            or_elastic(tb->recoil, xi, v, u[2], u[3], v);
             recoil += eps - kinetic_energy(v);
         } else {
             double n[3];
-            isotropic(u[2], u[3], n);
+            scatter(xi, v, u[2], u[3], n);
             double eps_new = eps - tb->thr[lvl];
             inel += tb->thr[lvl];
             if (tb->type[lvl] == OR_IONISATION) {
-                /* the remainder is split uniformly; the new electron starts
-                 * here, now, in an independent isotropic direction */
+                /* the remainder is shared (ionisation_share); the new
+                 * electron starts here, now, in an independent isotropic
+                 * direction */
                 double u2[4];
                 draw4(a->seed, aval, start->uid, flight, 1u, u2);
-                double eps_sec = u2[0] * eps_new;
+                double eps_sec = ionisation_share(tb->split_w, eps_new, u2[0]);
                 eps_new = eps_new - eps_sec;
                 share += eps_sec;
                 double ns[3];

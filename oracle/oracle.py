@@ -24,7 +24,8 @@ _lock = threading.Lock()
 _lib = None
 
 __all__ = ["build", "philox4x32_10", "splitmix64_mix", "child_uid", "flight", "elastic", "field_eval",
-           "boundary", "select", "majorant", "run", "default_threads"]
+           "boundary", "select", "majorant", "scatter", "ionisation_share", "run",
+           "default_threads"]
 
 
 def build(force: bool = False) -> str:
@@ -42,7 +43,8 @@ def build(force: bool = False) -> str:
 class _Gas(C.Structure):
     _fields_ = [("n_levels", C.c_int32), ("n_nodes", C.c_int32), ("d_eps", C.c_double),
                 ("level_type", C.c_void_p), ("threshold", C.c_void_p), ("rate", C.c_void_p),
-                ("recoil", C.c_double), ("nu_max", C.c_double)]
+                ("recoil", C.c_double), ("nu_max", C.c_double), ("xi0", C.c_void_p),
+                ("screen", C.c_void_p), ("split_w", C.c_double)]
 
 
 class _Field(C.Structure):
@@ -75,9 +77,14 @@ def _load():
             lib.or_child_uid.restype = C.c_uint64
             lib.or_flight.argtypes = [C.c_void_p] * 4 + [C.c_double]
             lib.or_flight.restype = None
-            lib.or_elastic.argtypes = [C.c_double, C.c_void_p, C.c_double, C.c_double,
-                                       C.c_void_p]
+            lib.or_elastic.argtypes = [C.c_double, C.c_double, C.c_void_p, C.c_double,
+                                       C.c_double, C.c_void_p]
             lib.or_elastic.restype = None
+            lib.or_scatter.argtypes = [C.c_double, C.c_void_p, C.c_double, C.c_double,
+                                       C.c_void_p]
+            lib.or_scatter.restype = C.c_double
+            lib.or_ionisation_share.argtypes = [C.c_double, C.c_double, C.c_double]
+            lib.or_ionisation_share.restype = C.c_double
             lib.or_field_eval.argtypes = [C.POINTER(_Field), C.c_double, C.c_void_p, C.c_void_p]
             lib.or_field_eval.restype = None
             lib.or_boundary.argtypes = [C.POINTER(_Field), C.c_void_p]
@@ -111,8 +118,16 @@ def _gas_struct(gas, keep):
     th = np.ascontiguousarray(gas.threshold, np.float64)
     rt = np.ascontiguousarray(gas.rate, np.float64)
     keep += [lt, th, rt]
+    xi = sc = None
+    if getattr(gas, "xi0", None) is not None:
+        xi = np.ascontiguousarray(gas.xi0, np.float64)
+        keep.append(xi)
+    if getattr(gas, "screen", None) is not None:
+        sc = np.ascontiguousarray(gas.screen, np.float64)
+        keep.append(sc)
     return _Gas(rt.shape[1], rt.shape[0], gas.d_eps, _ptr(lt).value, _ptr(th).value,
-                _ptr(rt).value, gas.recoil, gas.nu_max)
+                _ptr(rt).value, gas.recoil, gas.nu_max, _ptr(xi).value if xi is not None else None,
+                _ptr(sc).value if sc is not None else None, float(getattr(gas, "split_w", 0.0)))
 
 
 def _field_struct(field, keep):
@@ -168,13 +183,27 @@ def flight(r, v, a, w, dt):
     return r, v
 
 
-def elastic(recoil: float, v, u_cos: float, u_phi: float):
-    """Velocity after an elastic collision (isotropic direction from the two
-    uniforms, recoil loss with recoil = 2m/M)."""
+def elastic(recoil: float, v, u_cos: float, u_phi: float, xi: float = 0.0):
+    """Velocity after an elastic collision (direction from the two uniforms,
+    isotropic for xi = 0 else screened-Coulomb about v; recoil loss with
+    recoil = 2m/M)."""
     v = np.ascontiguousarray(v, np.float64)
     out = np.zeros(3)
-    _load().or_elastic(float(recoil), _ptr(v), float(u_cos), float(u_phi), _ptr(out))
+    _load().or_elastic(float(recoil), float(xi), _ptr(v), float(u_cos), float(u_phi), _ptr(out))
     return out
+
+
+def scatter(xi: float, v, u_cos: float, u_phi: float):
+    """(new unit direction, cos chi) after a collision with anisotropy xi."""
+    v = np.ascontiguousarray(v, np.float64)
+    out = np.zeros(3)
+    mu = _load().or_scatter(float(xi), _ptr(v), float(u_cos), float(u_phi), _ptr(out))
+    return out, mu
+
+
+def ionisation_share(w: float, rest: float, u: float) -> float:
+    """Energy of the new electron of an ionisation from the remainder `rest`."""
+    return float(_load().or_ionisation_share(float(w), float(rest), float(u)))
 
 
 def field_eval(field, r, plate_e=0.0):

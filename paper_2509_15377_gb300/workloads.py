@@ -22,7 +22,7 @@ from typing import Optional
 import numpy as np
 
 # Level kinds of a gas table (interface values of the C ABI).
-ELASTIC, EXCITATION, IONISATION = 0, 1, 2
+ELASTIC, EXCITATION, IONISATION, ATTACHMENT = 0, 1, 2, 3
 # Field kinds (interface values of the C ABI).
 UNIFORM, PLATE, COAX, GRID = 0, 1, 2, 3
 # Electron status codes written to the endpoints (non-zero = finished).
@@ -31,6 +31,7 @@ STATUS_NAMES = {
     5: "out_of_map", 6: "time", 7: "coll_limit", 8: "flight_limit",
 }
 ANODE, CATHODE, WIRE, TUBE, OUT_OF_MAP, TIME, COLL_LIMIT = 1, 2, 3, 4, 5, 6, 7
+FLIGHT_LIMIT, ATTACHED = 8, 9
 
 # Electron mass in unified atomic mass units (CODATA 2018).
 ELECTRON_MASS_U = 5.48579909065e-4
@@ -52,6 +53,11 @@ class Gas:
     recoil: float = 0.0      # 2m/M (elastic recoil loss), 0 = no loss
     nu_max: float = 0.0      # 1/ns, 0 = derived by the consumer
     band_width: float = 1.0  # eV per energy band of the banded majorant
+    # angular model per level: anisotropy xi0 (constant) where screen == 0,
+    # else xi = eps / (eps + screen); None = all isotropic
+    xi0: Optional[np.ndarray] = None      # float64 [L] in (-1, 1)
+    screen: Optional[np.ndarray] = None   # float64 [L] eV, >= 0
+    split_w: float = 0.0     # ionisation sharing width (eV); 0 = uniform split
 
     @property
     def n_levels(self) -> int:
@@ -126,9 +132,10 @@ class Workload:
 # ------------------------------------------------------------------ gases
 def model_gas(nu_elastic: float = 1000.0, nu_ion: float = 0.0, ion_threshold: float = 0.0,
               recoil: float = 0.0, n_nodes: int = 2, d_eps: float = 1000.0,
-              exact_nu_max: bool = True) -> Gas:
-    """Energy-independent rates: elastic (isotropic) and optionally an
-    ionisation level with a fixed rate."""
+              exact_nu_max: bool = True, nu_att: float = 0.0, xi_elastic: float = 0.0) -> Gas:
+    """Energy-independent rates: elastic (isotropic, or with the constant
+    anisotropy xi_elastic) and optionally an ionisation level and an
+    attachment level (threshold 0) with fixed rates."""
     types = [ELASTIC]
     thr = [0.0]
     cols = [np.full(n_nodes, nu_elastic)]
@@ -136,9 +143,17 @@ def model_gas(nu_elastic: float = 1000.0, nu_ion: float = 0.0, ion_threshold: fl
         types.append(IONISATION)
         thr.append(ion_threshold)
         cols.append(np.full(n_nodes, nu_ion))
+    if nu_att > 0.0:
+        types.append(ATTACHMENT)
+        thr.append(0.0)
+        cols.append(np.full(n_nodes, nu_att))
     rate = np.stack(cols, axis=1).astype(np.float64)
+    xi0 = None
+    if xi_elastic != 0.0:
+        xi0 = np.zeros(len(types))
+        xi0[0] = xi_elastic
     return Gas(np.array(types, np.int32), np.array(thr, np.float64), rate, float(d_eps),
-               float(recoil), float(nu_elastic + nu_ion) if exact_nu_max else 0.0)
+               float(recoil), float(rate[0].sum()) if exact_nu_max else 0.0, xi0=xi0)
 
 
 def argon_like_gas(k_exc: float = ARGON_LIKE_K_EXC) -> Gas:
@@ -158,6 +173,22 @@ def argon_like_gas(k_exc: float = ARGON_LIKE_K_EXC) -> Gas:
     thr = np.concatenate([[0.0], thr_exc, [15.7]]).astype(np.float64)
     recoil = 2.0 * ELECTRON_MASS_U / ARGON_MASS_U
     return Gas(types, thr, rate, d_eps, recoil, 0.0)
+
+
+def argon_like_physical_gas(k_exc: float = ARGON_LIKE_K_EXC, screen: float = 6.8,
+                            split_w: float = 10.0, nu_att: float = 2.0) -> Gas:
+    """The argon-like gas with the physics of the next level of detail:
+    every level scatters with the screened-Coulomb anisotropy
+    xi = eps / (eps + screen); the ionisation remainder is shared with the
+    Opal-Peterson-Beaty form of width split_w; and an attachment level with
+    the constant rate nu_att (1/ns, threshold 0) stands in for an
+    electronegative admixture.  All three are synthetic choices."""
+    g = argon_like_gas(k_exc)
+    rate = np.concatenate([g.rate, np.full((g.n_nodes, 1), nu_att)], axis=1)
+    types = np.concatenate([g.level_type, [ATTACHMENT]]).astype(np.int32)
+    thr = np.concatenate([g.threshold, [0.0]])
+    return Gas(types, thr, rate, g.d_eps, g.recoil, 0.0,
+               screen=np.full(len(types), float(screen)), split_w=float(split_w))
 
 
 # -------------------------------------------------------------- primaries

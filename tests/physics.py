@@ -78,3 +78,30 @@ def ramp_first_collision_survival(t, eps0, cos_a, e_vcm, c):
     t = np.asarray(t, float)
     integral = v0 * v0 * t + v0 * a * np.asarray(cos_a, float) * t * t + a * a * t ** 3 / 3.0
     return np.exp(-c * integral / (2.0 * a1))
+
+
+def screened_coulomb_cdf(mu, xi):
+    """P(cos chi <= mu) for the density (1 - xi^2) / (2 (1 - xi mu)^2) on
+    [-1, 1] (xi != 0)."""
+    mu = np.asarray(mu, float)
+    return (1.0 - xi * xi) / (2.0 * xi) * (1.0 / (1.0 - xi * mu) - 1.0 / (1.0 + xi))
+
+
+def screened_coulomb_mean_cos(xi):
+    """<cos chi> of that density, by quadrature."""
+    from scipy import integrate
+    val, _ = integrate.quad(lambda m: m * (1.0 - xi * xi) / (2.0 * (1.0 - xi * m) ** 2), -1.0, 1.0)
+    return val
+
+
+def birth_death(lam, mu, t):
+    """Linear birth-death process started from one individual (Kendall 1948):
+    mean population at t and the probability of extinction by t."""
+    g = math.exp((lam - mu) * t)
+    return g, mu * (g - 1.0) / (lam * g - mu)
+
+
+def opb_cdf(x, w, rest):
+    """P(share <= x) for the density proportional to 1 / (1 + (x/w)^2) on
+    [0, rest / 2]."""
+    return np.arctan(np.asarray(x, float) / w) / math.atan(rest / (2.0 * w))

@@ -558,3 +558,149 @@ def test_ramp_first_collision_closed_form(majorant, band_width, window):
     assert np.all(o["status"] == W.COLL_LIMIT)
     u = ramp_pit(o, w, c)
     assert stats.kstest(u, "uniform").pvalue > 0.01
+
+
+# ------------------------------------------ attachment, anisotropy, sharing
+@pytest.mark.parametrize("xi", [0.3, 0.8, 0.97, -0.5])
+def test_screened_coulomb_deflection(xi):
+    """Deflection cosines follow the screened-Coulomb law (KS against its
+    distribution function), measured from the geometry of the returned
+    direction; the azimuth about the incident direction is uniform; the
+    direction is a unit vector."""
+    from scipy import stats
+    rng = np.random.default_rng(51)
+    v = rng.normal(size=3) * 0.1
+    d = v / np.linalg.norm(v)
+    # a frame of the test's own: e1 from Gram-Schmidt on the x axis
+    e1 = np.array([1.0, 0.0, 0.0]) - d[0] * d
+    e1 /= np.linalg.norm(e1)
+    e2 = np.cross(d, e1)
+    mus, phis = [], []
+    for u, w in rng.uniform(size=(6000, 2)):
+        n, mu = oracle.scatter(xi, v, u, w)
+        assert abs(np.linalg.norm(n) - 1.0) < 1e-12
+        assert abs(mu - float(np.dot(n, d))) < 1e-12
+        mus.append(float(np.dot(n, d)))
+        phis.append(math.atan2(float(np.dot(n, e2)), float(np.dot(n, e1))))
+    assert stats.kstest(mus, lambda m: P.screened_coulomb_cdf(m, xi)).pvalue > 0.01
+    assert stats.kstest(np.mod(phis, 2 * math.pi) / (2 * math.pi), "uniform").pvalue > 0.01
+
+
+def test_screened_coulomb_from_rest_and_isotropic_limit():
+    n, mu = oracle.scatter(0.6, np.zeros(3), 0.3, 0.7)  # a resting electron: d = +z
+    assert abs(n[2] - mu) < 1e-15 and abs(np.linalg.norm(n) - 1.0) < 1e-12
+    n0, _ = oracle.scatter(0.0, np.array([0.1, 0.0, 0.0]), 0.3, 0.7)
+    assert np.allclose(n0[2], 1.0 - 2.0 * 0.3)  # lab-frame isotropic sampling
+
+
+def test_anisotropic_drift_closed_form():
+    """Constant rate nu, energy-independent anisotropy: each collision keeps
+    the mean velocity fraction g = <cos chi>, so the drift velocity is
+    eE / (m nu (1 - g)) exactly (momentum-transfer rate)."""
+    xi = 0.6
+    w = W.drift_model(n_electrons=20000, n_coll=3000, seed=53)
+    w.gas = W.model_gas(1000.0, xi_elastic=xi)
+    o = oracle.run(w.gas, w.field, w.primaries, seed=53, coll_limit=3000)
+    g = P.screened_coulomb_mean_cos(xi)
+    dz, dt = o["z1"] - o["z0"], o["t1"] - o["t0"]
+    vd = P.drift_velocity(1000.0, 1000.0 * (1.0 - g))
+    se = np.std(dz - vd * dt) / math.sqrt(len(dz)) / dt.mean()
+    assert P.within_sigma(dz.mean() / dt.mean(), vd, se)
+    assert np.allclose(o["e1"], o["e0"] + 1000.0 * dz, rtol=1e-9, atol=1e-9)
+
+
+def test_elastic_recoil_uses_the_deflection_with_anisotropy():
+    rng = np.random.default_rng(55)
+    r = 0.02
+    for _ in range(200):
+        v = rng.normal(size=3) * 0.1
+        u, ph, xi = rng.uniform(), rng.uniform(), rng.uniform(-0.9, 0.99)
+        v1 = oracle.elastic(r, v, u, ph, xi)
+        n, mu = oracle.scatter(xi, v, u, ph)
+        assert np.allclose(v1 / np.linalg.norm(v1), n, atol=1e-12)
+        assert np.dot(v1, v1) == pytest.approx(np.dot(v, v) * (1.0 - r * (1.0 - mu)), rel=1e-12)
+
+
+def test_attachment_time_is_exponential():
+    """Constant attachment rate nu_a: the capture time is Exp(nu_a); the
+    electron ends where it was captured with its energy unchanged (the
+    energy ledger still closes)."""
+    from scipy import stats
+    nu_a = 5.0
+    w = W.drift_model(n_electrons=5000, n_coll=0, seed=57)
+    w.gas = W.model_gas(1000.0, nu_att=nu_a)
+    # ~200 collisions before capture; the limit only bounds a broken capture
+    o = oracle.run(w.gas, w.field, w.primaries, seed=57, coll_limit=200_000)
+    assert np.all(o["status"] == W.ATTACHED)
+    assert stats.kstest((o["t1"] - o["t0"]) * nu_a, "expon").pvalue > 0.01
+    led = o["ledger"]
+    assert np.allclose(o["e1"], o["e0"] + led[:, 0] - led[:, 1] - led[:, 2] - led[:, 3],
+                       rtol=1e-10, atol=1e-9)
+    assert np.all(o["tallies"][:, 1] == 1)  # one attachment per avalanche
+
+
+def test_birth_death_process():
+    """Constant ionisation (lam) and attachment (mu) rates: the number of
+    electrons alive at T has mean exp((lam - mu) T) and the avalanche is
+    extinct by T with Kendall's probability."""
+    lam, mu, T, n = 10.0, 4.0, 0.4, 3000
+    w = W.drift_model(n_electrons=n, n_coll=0, e_field=100.0, seed=59)
+    w.gas = W.model_gas(1000.0, nu_ion=lam, ion_threshold=0.0, nu_att=mu)
+    o = oracle.run(w.gas, w.field, w.primaries, seed=59, t_max=T)
+    alive = np.bincount(o["aval"][o["status"] == W.TIME], minlength=n).astype(float)
+    mean, p0 = P.birth_death(lam, mu, T)
+    assert P.within_sigma(alive.mean(), mean, alive.std() / math.sqrt(n))
+    ext = float((alive == 0).mean())
+    assert P.within_sigma(ext, p0, math.sqrt(p0 * (1 - p0) / n))
+    # every electron ends either alive at T or attached
+    assert set(np.unique(o["status"])) <= {W.TIME, W.ATTACHED}
+
+
+@pytest.mark.parametrize("w_opb,rest", [(10.0, 30.0), (2.0, 80.0), (50.0, 5.0)])
+def test_ionisation_sharing_opb(w_opb, rest):
+    from scipy import stats
+    rng = np.random.default_rng(61)
+    x = np.array([oracle.ionisation_share(w_opb, rest, u) for u in rng.uniform(size=8000)])
+    assert np.all((x >= 0.0) & (x <= rest / 2 * (1 + 1e-12)))
+    assert stats.kstest(x, lambda q: P.opb_cdf(q, w_opb, rest)).pvalue > 0.01
+    assert oracle.ionisation_share(0.0, rest, 0.25) == 0.25 * rest  # uniform split
+
+
+def test_physical_gas_ledger_and_charge():
+    """The argon-like gas with anisotropy, OPB sharing and attachment: the
+    energy ledger closes per electron, charge is conserved per avalanche,
+    attached electrons end with status ATTACHED, and new electrons never
+    take more than half the remainder (shares <= (eps - I) / 2)."""
+    w = W.plate(n_avalanches=40, e_field=45_000.0, seed=63)
+    w.gas = W.argon_like_physical_gas()
+    o = oracle.run(w.gas, w.field, w.primaries, seed=63, t_max=w.t_max)
+    led = o["ledger"]
+    assert np.allclose(o["e1"], o["e0"] + led[:, 0] - led[:, 1] - led[:, 2] - led[:, 3],
+                       rtol=1e-9, atol=1e-8)
+    L = w.gas.n_levels
+    ion = o["tallies"][:, L - 2]  # ionisation is the level before attachment
+    assert np.array_equal(o["electrons"], 1 + ion)
+    att = o["tallies"][:, L - 1]
+    assert np.array_equal(np.bincount(o["aval"][o["status"] == W.ATTACHED], minlength=40), att)
+    assert att.sum() > 0 and ion.sum() > 0
+    child = o["uid"] >= 40
+    assert np.all(o["e0"][child] <= (100.0 - 15.7) / 2)
+
+
+def test_screened_anisotropy_diffusion_closed_form():
+    """No field, constant rate nu and fixed energy eps0 (nothing changes the
+    speed): with the energy-dependent anisotropy xi = eps0 / (eps0 + screen)
+    successive directions have <n_i . n_j> = g^|i-j| (g = <cos chi>), so after
+    N flights <|r|^2> = (v/nu)^2 (2N + 2 sum_k (N - k) g^k)."""
+    eps0, screen, N, n = 10.0, 5.0, 40, 20000
+    w = W.drift_model(n_electrons=n, n_coll=N, e_field=0.0, seed=65)
+    w.gas = W.model_gas(1000.0)
+    w.gas.screen = np.array([screen])
+    w.primaries.e[:] = eps0
+    o = oracle.run(w.gas, w.field, w.primaries, seed=65, coll_limit=N)
+    r2 = (o["x1"] - o["x0"]) ** 2 + (o["y1"] - o["y0"]) ** 2 + (o["z1"] - o["z0"]) ** 2
+    g = P.screened_coulomb_mean_cos(eps0 / (eps0 + screen))
+    k = np.arange(1, N)
+    expect = P.speed_sq(eps0) / 1000.0 ** 2 * (2 * N + 2 * np.sum((N - k) * g ** k))
+    assert P.within_sigma(r2.mean(), expect, r2.std() / math.sqrt(n))
+    assert np.allclose(o["e1"], eps0, rtol=1e-12)
