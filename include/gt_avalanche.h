@@ -42,7 +42,7 @@
 extern "C" {
 #endif
 
-#define GT_ABI_VERSION 1
+#define GT_ABI_VERSION 2
 #define GT_MAX_LEVELS 32 /* collision levels per gas table */
 
 /* ---- return codes ---------------------------------------------------- */
@@ -68,12 +68,16 @@ extern "C" {
 #define GT_ST_TIME 6          /* reached t_max */
 #define GT_ST_COLL_LIMIT 7    /* reached coll_limit real collisions */
 #define GT_ST_FLIGHT_LIMIT 8  /* 2^32 - 1 flights */
+#define GT_ST_ATTACHED 9      /* captured by an attachment collision (Fig. 2
+                                 "ionisation or attachment?") */
 
 /* ---- enumerations ---------------------------------------------------- */
-#define GT_LEVEL_ELASTIC 0    /* isotropic, energy x (1 - recoil (1 - cos chi)) */
-#define GT_LEVEL_EXCITATION 1 /* isotropic, energy - threshold */
-#define GT_LEVEL_IONISATION 2 /* isotropic, energy - threshold split uniformly
-                                 with a new isotropic electron */
+#define GT_LEVEL_ELASTIC 0    /* energy x (1 - recoil (1 - cos chi)) */
+#define GT_LEVEL_EXCITATION 1 /* energy - threshold */
+#define GT_LEVEL_IONISATION 2 /* energy - threshold shared with a new electron
+                                 in an isotropic direction (see split_w) */
+#define GT_LEVEL_ATTACHMENT 3 /* the electron is captured: it ends at the
+                                 collision with status GT_ST_ATTACHED */
 
 #define GT_FIELD_UNIFORM 0 /* E = (0, 0, -e0) everywhere, no boundary */
 #define GT_FIELD_PLATE 1   /* E = (0, 0, -E_k) between z = 0 and z = gap */
@@ -111,6 +115,18 @@ typedef struct {
     double nu_max;             /* 1/ns */
     double band_width;         /* eV per energy band of the banded majorant,
                                   rounded to whole nodes; 0 = 1 eV */
+    /* Angular model per level (NULL = isotropic for all levels): the
+     * anisotropy is xi = xi0[j] where screen[j] == 0, else
+     * xi = eps / (eps + screen[j]); xi = 0 scatters isotropically in the lab
+     * frame, otherwise the deflection chi from the incident direction has
+     * the screened-Coulomb density (1 - xi^2) / (2 (1 - xi cos chi)^2) in
+     * cos chi and a uniform azimuth. */
+    const double *xi0;         /* host [n_levels] in (-1, 1), or NULL */
+    const double *screen;      /* host [n_levels] eV >= 0, or NULL */
+    double split_w;            /* ionisation sharing: 0 = the new electron takes a
+                                  uniform share of eps - I; > 0 = a share on
+                                  [0, (eps - I)/2] with density proportional to
+                                  1 / (1 + (x / split_w)^2) (eV) */
 } gt_gas;
 
 /* ---- field and geometry (Fig. 2 "Find E field"; Sec. 3.1 field maps) -- */

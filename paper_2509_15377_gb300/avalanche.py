@@ -30,6 +30,7 @@ GT_BATCHED, GT_PLAIN = 0, 1
 GT_DEBUG_UNFILLED_SLOT = 1
 GT_MAJORANT_GLOBAL, GT_MAJORANT_BANDED = 0, 1
 GT_OBS_COUNT = 8
+GT_ABI_VERSION = 2
 PARTIAL_OK = (GT_OK, GT_ERR_QUEUE_OVERFLOW, GT_ERR_TIMEOUT)
 
 
@@ -43,7 +44,8 @@ class GtError(RuntimeError):
 class gt_gas(C.Structure):
     _fields_ = [("n_levels", C.c_int32), ("n_nodes", C.c_int32), ("d_eps", C.c_double),
                 ("level_type", C.c_void_p), ("threshold", C.c_void_p), ("rate", C.c_void_p),
-                ("recoil", C.c_double), ("nu_max", C.c_double), ("band_width", C.c_double)]
+                ("recoil", C.c_double), ("nu_max", C.c_double), ("band_width", C.c_double),
+                ("xi0", C.c_void_p), ("screen", C.c_void_p), ("split_w", C.c_double)]
 
 
 class gt_field(C.Structure):
@@ -140,6 +142,8 @@ def load(path: str = LIB_PATH):
         f = getattr(lib, name)
         f.argtypes = args
         f.restype = res
+    if lib.gt_abi_version() != GT_ABI_VERSION:
+        raise RuntimeError(f"library ABI {lib.gt_abi_version()}, binding {GT_ABI_VERSION}")
     sizes = (sz * 5)()
     if lib.gt_abi_sizes(sizes, 5) != GT_OK:
         raise RuntimeError("gt_abi_sizes failed")
@@ -176,8 +180,15 @@ def gas_table_upload(ctx, gas: W.Gas) -> None:
     lt = np.ascontiguousarray(gas.level_type, np.int32)
     th = np.ascontiguousarray(gas.threshold, np.float64)
     rt = np.ascontiguousarray(gas.rate, np.float64)
+    xi = None if gas.xi0 is None else np.ascontiguousarray(gas.xi0, np.float64)
+    sc = None if gas.screen is None else np.ascontiguousarray(gas.screen, np.float64)
+    for a in (xi, sc):
+        if a is not None and a.shape != (rt.shape[1],):
+            raise ValueError("xi0 / screen need one value per level")
     g = gt_gas(rt.shape[1], rt.shape[0], gas.d_eps, lt.ctypes.data, th.ctypes.data,
-               rt.ctypes.data, gas.recoil, gas.nu_max, getattr(gas, "band_width", 0.0))
+               rt.ctypes.data, gas.recoil, gas.nu_max, gas.band_width,
+               xi.ctypes.data if xi is not None else None,
+               sc.ctypes.data if sc is not None else None, gas.split_w)
     _check(load().gas_table_upload(ctx, C.byref(g)), "gas_table_upload", ctx)
 
 

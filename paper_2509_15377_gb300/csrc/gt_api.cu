@@ -236,10 +236,15 @@ int gas_table_upload(gt_ctx *ctx, const gt_gas *g)
         return GT_ERR_ARG;
     for (int j = 0; j < L; ++j) {
         const int t = g->level_type[j];
-        if (t != GT_LEVEL_ELASTIC && t != GT_LEVEL_EXCITATION && t != GT_LEVEL_IONISATION)
+        if (t != GT_LEVEL_ELASTIC && t != GT_LEVEL_EXCITATION && t != GT_LEVEL_IONISATION &&
+            t != GT_LEVEL_ATTACHMENT)
             return GT_ERR_ARG;
         if (!(g->threshold[j] >= 0.0) || !std::isfinite(g->threshold[j])) return GT_ERR_ARG;
+        if (g->xi0 && !(g->xi0[j] > -1.0 && g->xi0[j] < 1.0)) return GT_ERR_ARG;
+        if (g->screen && (!(g->screen[j] >= 0.0) || !std::isfinite(g->screen[j])))
+            return GT_ERR_ARG;
     }
+    if (!(g->split_w >= 0.0) || !std::isfinite(g->split_w)) return GT_ERR_ARG;
     // cumulative rates over levels at every node, FP64, and their maximum
     std::vector<double> cum((size_t)N * L);
     double top = 0.0;
@@ -333,10 +338,16 @@ int gas_table_upload(gt_ctx *ctx, const gt_gas *g)
     d.last_band_f = (float)(B - 1);
     d.band64 = ctx->d_band64;
     d.band32 = ctx->d_band32;
+    d.any_aniso = 0;
     for (int j = 0; j < L; ++j) {
         d.type[j] = g->level_type[j];
         d.thr[j] = g->threshold[j];
+        d.xi0[j] = g->xi0 ? g->xi0[j] : 0.0;
+        d.screen[j] = g->screen ? g->screen[j] : 0.0;
+        if (d.xi0[j] != 0.0 || d.screen[j] > 0.0) d.any_aniso = 1;
     }
+    d.split_w = g->split_w;
+    d.split_w_f = (float)g->split_w;
     ctx->has_gas = true;
     return GT_OK;
 }

@@ -50,6 +50,12 @@ struct DevGas {
     const float *band32;
     int32_t type[GT_MAX_LEVELS];
     double thr[GT_MAX_LEVELS];
+    // angular model per level (xi0 where screen == 0, else eps/(eps+screen))
+    // and the ionisation sharing width; any_aniso = 0 when all isotropic
+    double xi0[GT_MAX_LEVELS], screen[GT_MAX_LEVELS];
+    double split_w;
+    float split_w_f;
+    int any_aniso;
 };
 
 struct DevField {
@@ -217,6 +223,8 @@ struct Tables {
     const int *type;        // shared [L]
     const double *thr;      // shared [L]
     const float *thr_f;     // shared [L]
+    const float *xi0_f;     // shared [L]
+    const float *screen_f;  // shared [L]
     uint32_t *tally;        // shared [L][blockDim]: real collisions per level
     double *base;           // shared [4][blockDim]: FP64 position/time bases (mixed)
     int stride32;           // odd in shared memory: rows start on every bank
@@ -543,6 +551,89 @@ __device__ __forceinline__ void isotropic32(float u, float v, float &nx, float &
     nx = sr * c; ny = sr * s; nz = ct;
 }
 
+// Anisotropy of level j at energy eps: xi0 where the screening energy is 0,
+// else eps / (eps + screen) (screened-Coulomb form).
+__device__ __forceinline__ double level_xi64(const DevGas &g, int j, double eps)
+{
+    return g.screen[j] > 0.0 ? eps / (eps + g.screen[j]) : g.xi0[j];
+}
+
+// New unit direction after a collision with anisotropy xi != 0: deflection
+// chi from the incident velocity v with the screened-Coulomb density
+// (1 - xi^2) / (2 (1 - xi mu)^2) in mu = cos chi, sampled by inversion,
+// mu = (1 + xi - 2u) / (1 + xi - 2 xi u) (1 - mu = 2u (1 - xi) / (same),
+// without cancellation); azimuth 2 pi w about the incident direction d in
+// the orthonormal frame (e1, e2, d) of Duff et al., JCGT 6(1), 2017; a
+// resting electron takes d = +z.  Returns mu.
+__device__ __forceinline__ double scatter64(double xi, double vx, double vy, double vz, double u,
+                                            double w, double &nx, double &ny, double &nz)
+{
+    const double den = 1.0 + xi - 2.0 * xi * u;
+    const double mu = (1.0 + xi - 2.0 * u) / den;
+    const double om = 2.0 * u * (1.0 - xi) / den;
+    const double s2 = om * (2.0 - om);
+    const double sc = s2 > 0.0 ? sqrt(s2) : 0.0;
+    const double sp = sqrt(vx * vx + vy * vy + vz * vz);
+    double d0 = 0.0, d1 = 0.0, d2 = 1.0;
+    if (sp > 0.0) {
+        d0 = vx / sp; d1 = vy / sp; d2 = vz / sp;
+    }
+    const double sg = d2 >= 0.0 ? 1.0 : -1.0;
+    const double a = -1.0 / (sg + d2);
+    const double b = d0 * d1 * a;
+    double sn, cs;
+    sincos(kTwoPi * w, &sn, &cs);
+    nx = mu * d0 + sc * (cs * (1.0 + sg * d0 * d0 * a) + sn * b);
+    ny = mu * d1 + sc * (cs * (sg * b) + sn * (sg + d1 * d1 * a));
+    nz = mu * d2 + sc * (cs * (-sg * d0) + sn * (-d1));
+    return mu;
+}
+
+// FP32 version; the direction is rescaled to unit length with a
+// Newton-refined rsqrt so that the speed set from it carries no systematic
+// error from collision to collision.
+__device__ __forceinline__ float scatter32(float xi, float vx, float vy, float vz, float u, float w,
+                                           float &nx, float &ny, float &nz)
+{
+    const float den = fmaf(-2.0f * xi, u, 1.0f + xi);
+    const float mu = __fdividef(fmaf(-2.0f, u, 1.0f + xi), den);
+    const float om = __fdividef(2.0f * u * (1.0f - xi), den);
+    const float sc = sqrtf(fmaxf(om * (2.0f - om), 0.0f));
+    const float v2 = fmaf(vx, vx, fmaf(vy, vy, vz * vz));
+    float d0 = 0.0f, d1 = 0.0f, d2 = 1.0f;
+    if (v2 > 0.0f) {
+        const float r = rsqrtf(v2);
+        d0 = vx * r; d1 = vy * r; d2 = vz * r;
+    }
+    const float sg = d2 >= 0.0f ? 1.0f : -1.0f;
+    const float a = -1.0f / (sg + d2);
+    const float b = d0 * d1 * a;
+    float sn, cs;
+    __sincosf(kTwoPiF * w, &sn, &cs);
+    float x = fmaf(mu, d0, sc * fmaf(cs, fmaf(sg * d0 * d0, a, 1.0f), sn * b));
+    float y = fmaf(mu, d1, sc * fmaf(cs, sg * b, sn * fmaf(d1 * d1, a, sg)));
+    float z = fmaf(mu, d2, sc * fmaf(cs, -sg * d0, -sn * d1));
+    const float g = fmaf(x, x, fmaf(y, y, z * z));
+    float r = rsqrtf(g);
+    r = r * fmaf(-0.5f * g, r * r, 1.5f);
+    nx = x * r; ny = y * r; nz = z * r;
+    return mu;
+}
+
+// Energy of the new electron of an ionisation from the remainder
+// rest = eps - I: uniform share u * rest (w = 0), or the inverse of the
+// distribution with density proportional to 1 / (1 + (x/w)^2) on
+// [0, rest/2] (Opal, Peterson and Beaty, J. Chem. Phys. 55, 4100, 1971).
+__device__ __forceinline__ double ionisation_share64(double w, double rest, double u)
+{
+    return w <= 0.0 ? u * rest : w * tan(u * atan(rest / (2.0 * w)));
+}
+
+__device__ __forceinline__ float ionisation_share32(float w, float rest, float u)
+{
+    return w <= 0.0f ? u * rest : w * tanf(u * atanf(rest / (2.0f * w)));
+}
+
 // Store the birth record of a new electron in queue slot s: position and
 // time are the parent's at the ionising collision (read from the parent),
 // energy, velocity and id from the child record.
@@ -723,11 +814,19 @@ struct Fp64Electron {
             return EV_NONE;
         }
         tb.tally[lvl * blockDim.x + threadIdx.x] += 1u;
+        const int type = tb.type[lvl];
+        if (type == GT_LEVEL_ATTACHMENT) {  // captured: the electron ends here
+            status = GT_ST_ATTACHED;
+            return EV_RETIRE;
+        }
         double nx, ny, nz;
-        isotropic64(u01d(w.z), u01d(w.w), nx, ny, nz);
+        const double xi = p.gas.any_aniso ? level_xi64(p.gas, lvl, eps) : 0.0;
+        if (xi == 0.0)
+            isotropic64(u01d(w.z), u01d(w.w), nx, ny, nz);
+        else
+            scatter64(xi, vx, vy, vz, u01d(w.z), u01d(w.w), nx, ny, nz);
         double eps_new;
         int ev = EV_NONE;
-        const int type = tb.type[lvl];
         if (type == GT_LEVEL_ELASTIC) {
             const double sp = sqrt(vx * vx + vy * vy + vz * vz);
             const double cchi = sp > 0.0 ? (vx * nx + vy * ny + vz * nz) / sp : 0.0;
@@ -736,7 +835,7 @@ struct Fp64Electron {
             eps_new = eps - tb.thr[lvl];
             if (type == GT_LEVEL_IONISATION) {
                 const uint4 w2 = draw(p.seed, aval, uid, flight, 1u);
-                const double es = u01d(w2.x) * eps_new;
+                const double es = ionisation_share64(p.gas.split_w, eps_new, u01d(w2.x));
                 eps_new = eps_new - es;
                 double sx, sy, sz;
                 isotropic64(u01d(w2.y), u01d(w2.z), sx, sy, sz);
@@ -1029,10 +1128,22 @@ struct MixedElectron {
             }
         }
         tb.tally[lvl * blockDim.x + threadIdx.x] += 1u;
+        if (type == GT_LEVEL_ATTACHMENT) {  // captured: the electron ends here
+            status = GT_ST_ATTACHED;
+            return EV_RETIRE;
+        }
         float nx, ny, nz;
-        isotropic32(u01f(pd.w2), u01f(pd.w3), nx, ny, nz);
         float sp;
         int ev = EV_NONE;
+        float xi = 0.0f, mu = 0.0f;
+        if (p.gas.any_aniso) {
+            const float sc = tb.screen_f[lvl];
+            xi = sc > 0.0f ? __fdividef(eps, eps + sc) : tb.xi0_f[lvl];
+        }
+        if (xi != 0.0f)
+            mu = scatter32(xi, vx, vy, vz, u01f(pd.w2), u01f(pd.w3), nx, ny, nz);
+        else
+            isotropic32(u01f(pd.w2), u01f(pd.w3), nx, ny, nz);
         if (type == GT_LEVEL_ELASTIC) {
             // scale the speed itself: |v'| = |v| sqrt(1 - recoil (1 - cos chi));
             // a round trip through the energy would multiply by
@@ -1040,14 +1151,15 @@ struct MixedElectron {
             // (cos chi only enters multiplied by recoil ~ 1e-5, so the
             // hardware rsqrt is accurate enough there)
             const float v2 = vx * vx + vy * vy + vz * vz;
-            const float cchi = v2 > 0.f ? (vx * nx + vy * ny + vz * nz) * rsqrtf(v2) : 0.f;
+            const float cchi = xi != 0.0f ? mu
+                               : (v2 > 0.f ? (vx * nx + vy * ny + vz * nz) * rsqrtf(v2) : 0.f);
             sp = sqrtf(v2 * (1.0f - p.gas.recoil_f * (1.0f - cchi)));
         } else {
             float eps_new = fmaxf(eps - tb.thr_f[lvl], 0.0f);
             if (type == GT_LEVEL_IONISATION) {
                 const uint32_t flight = nf - 1u;
                 const uint4 w2 = draw(p.seed, aval, uid, flight, 1u);
-                const float es = u01f(w2.x) * eps_new;
+                const float es = ionisation_share32(p.gas.split_w_f, eps_new, u01f(w2.x));
                 eps_new = eps_new - es;
                 float sx, sy, sz;
                 isotropic32(u01f(w2.y), u01f(w2.z), sx, sy, sz);

@@ -54,6 +54,8 @@ __device__ __forceinline__ Tables stage_tables(const RunParams &p, unsigned char
 {
     __shared__ double s_thr[GT_MAX_LEVELS];
     __shared__ float s_thr_f[GT_MAX_LEVELS];
+    __shared__ float s_xi0_f[GT_MAX_LEVELS];
+    __shared__ float s_screen_f[GT_MAX_LEVELS];
     __shared__ int s_type[GT_MAX_LEVELS];
     const int L = p.gas.n_levels;
     double *s_base = reinterpret_cast<double *>(smem);
@@ -67,6 +69,8 @@ __device__ __forceinline__ Tables stage_tables(const RunParams &p, unsigned char
     for (int i = threadIdx.x; i < L; i += blockDim.x) {
         s_thr[i] = p.gas.thr[i];
         s_thr_f[i] = (float)p.gas.thr[i];
+        s_xi0_f[i] = (float)p.gas.xi0[i];
+        s_screen_f[i] = (float)p.gas.screen[i];
         s_type[i] = p.gas.type[i];
     }
     for (int i = threadIdx.x; i < L * (int)blockDim.x; i += blockDim.x) s_tally[i] = 0u;
@@ -94,6 +98,8 @@ __device__ __forceinline__ Tables stage_tables(const RunParams &p, unsigned char
     tb.type = s_type;
     tb.thr = s_thr;
     tb.thr_f = s_thr_f;
+    tb.xi0_f = s_xi0_f;
+    tb.screen_f = s_screen_f;
     tb.tally = s_tally;
     tb.base = s_base;
     return tb;
