@@ -56,6 +56,7 @@ struct DevGas {
     double split_w;
     float split_w_f;
     int any_aniso;
+    int any_special;  // anisotropy, attachment or a sharing law (general step)
 };
 
 struct DevField {
@@ -747,8 +748,9 @@ struct Fp64Electron {
     }
 
     // One flight and its collision (Fig. 2: "Find E field and add random
-    // time step", "Collision?", "ionisation or attachment?").
-    template <int FK>
+    // time step", "Collision?", "ionisation or attachment?").  (PHYS is
+    // ignored: the FP64 step always handles every gas.)
+    template <int FK, bool PHYS = true>
     __device__ __forceinline__ int fly(const RunParams &p, const Tables &tb, ChildT &ch)
     {
         if (nf == 0xFFFFFFFFu) {
@@ -1109,7 +1111,10 @@ struct MixedElectron {
 
     // The pending real collision (Fig. 2 "Collision is ionisation or
     // attachment?"): level selection, threshold guard, isotropic scattering.
-    template <int FK>
+    // PHYS = false builds the collision of a gas with isotropic levels, no
+    // attachment and a uniform ionisation split (the basic gas) without the
+    // code of the general case; PHYS = true handles every gas.
+    template <int FK, bool PHYS>
     __device__ __forceinline__ int collide(const RunParams &p, const Tables &tb, Pending &pd,
                                            ChildT &ch)
     {
@@ -1128,7 +1133,7 @@ struct MixedElectron {
             }
         }
         tb.tally[lvl * blockDim.x + threadIdx.x] += 1u;
-        if (type == GT_LEVEL_ATTACHMENT) {  // captured: the electron ends here
+        if (PHYS && type == GT_LEVEL_ATTACHMENT) {  // captured: the electron ends here
             status = GT_ST_ATTACHED;
             return EV_RETIRE;
         }
@@ -1136,7 +1141,7 @@ struct MixedElectron {
         float sp;
         int ev = EV_NONE;
         float xi = 0.0f, mu = 0.0f;
-        if (p.gas.any_aniso) {
+        if (PHYS && p.gas.any_aniso) {
             const float sc = tb.screen_f[lvl];
             xi = sc > 0.0f ? __fdividef(eps, eps + sc) : tb.xi0_f[lvl];
         }
@@ -1159,7 +1164,8 @@ struct MixedElectron {
             if (type == GT_LEVEL_IONISATION) {
                 const uint32_t flight = nf - 1u;
                 const uint4 w2 = draw(p.seed, aval, uid, flight, 1u);
-                const float es = ionisation_share32(p.gas.split_w_f, eps_new, u01f(w2.x));
+                const float es = PHYS ? ionisation_share32(p.gas.split_w_f, eps_new, u01f(w2.x))
+                                      : u01f(w2.x) * eps_new;
                 eps_new = eps_new - es;
                 float sx, sy, sz;
                 isotropic32(u01f(w2.y), u01f(w2.z), sx, sy, sz);
@@ -1181,13 +1187,13 @@ struct MixedElectron {
     }
 
     // Flight and collision in one call (plain mode).
-    template <int FK>
+    template <int FK, bool PHYS = true>
     __device__ __forceinline__ int fly(const RunParams &p, const Tables &tb, ChildT &ch)
     {
         Pending pd;
         const int ev = advance<FK>(p, tb, pd);
         if (ev || !pd.real) return ev;
-        return collide<FK>(p, tb, pd, ch);
+        return collide<FK, PHYS>(p, tb, pd, ch);
     }
 
     template <int FK>

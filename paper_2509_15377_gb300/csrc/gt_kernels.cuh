@@ -183,7 +183,7 @@ __device__ __forceinline__ int push_children(const RunParams &p, bool want, cons
     return 0;
 }
 
-template <class E, int FK, bool SMEM_TABLE, int MAXT, int MP = 0>
+template <class E, int FK, bool SMEM_TABLE, int MAXT, int MP = 0, bool PHYS = true>
 __global__ void __launch_bounds__(MAXT) k_batched(const RunParams p)
 {
     extern __shared__ __align__(16) unsigned char smem[];
@@ -281,7 +281,7 @@ __global__ void __launch_bounds__(MAXT) k_batched(const RunParams p)
                 }
                 typename E::ChildT ch;
                 int ev = EV_NONE;
-                if (pd.real) ev = e.template collide<FK>(p, tb, pd, ch);
+                if (pd.real) ev = e.template collide<FK, PHYS>(p, tb, pd, ch);
                 if (__any_sync(FULL, ev & EV_CHILD))
                     retired += push_children(p, (ev & EV_CHILD) != 0, e, ch, lane);
                 if (ev & EV_RETIRE) {
@@ -322,7 +322,7 @@ __global__ void __launch_bounds__(MAXT) k_batched(const RunParams p)
 // One generation of one avalanche (plain mode): every electron of `cur`
 // flies until it ionises (it stays alive and its new electron goes to
 // `fresh`) or finishes (alive = 0).
-template <class E, int FK, bool SMEM_TABLE, int MAXT>
+template <class E, int FK, bool SMEM_TABLE, int MAXT, bool PHYS = true>
 __global__ void __launch_bounds__(MAXT)
     k_plain_transport(const RunParams p, const Stack cur, long long n_active, const Stack fresh,
                       int parity, int aval)
@@ -344,7 +344,7 @@ __global__ void __launch_bounds__(MAXT)
     if (e.nf == 0u) ev = e.template check_start<FK>(p);
     unsigned long long k = 0;
     while (ev == EV_NONE) {
-        ev = e.template fly<FK>(p, tb, ch);
+        ev = e.template fly<FK, PHYS>(p, tb, ch);
         if ((++k & 4095ull) == 0ull) {
             if ((long long)(globaltimer() - t_start) > p.time_limit_ns) {
                 atomicOr(&p.hdr->error, ERR_TIMEOUT);

@@ -1,156 +1,51 @@
-// gt_kernels_mixed.cu -- mixed-precision instantiations of the transport
-// kernels, with the FP32 cumulative table staged in shared memory when it
-// fits next to the per-thread tallies (else read through the read-only path).
-#include "gt_kernels.cuh"
-#include "gt_launch.h"
+// gt_kernels_mixed.cu -- mixed-precision transport kernels for the basic
+// gas (isotropic levels, no attachment, uniform ionisation split), and the
+// mixed-precision launch entry points, which pick the basic or the general
+// instantiation (gt_kernels_mixed_phys.cu) from the uploaded gas.
+#include "gt_kernels_mixed.inl"
 
 namespace gt {
 
-// The batched kernel is built for three launch bounds: more resident warps
-// per SM against fewer registers per thread (the FP32 table in shared
-// memory limits an SM to one CTA).
-constexpr int kMaxThreadsMixed = 1024;
-constexpr int kPlainThreadsMixed = 512;
+// the general instantiation lives in gt_kernels_mixed_phys.cu
+extern template cudaError_t launch_batched_mixed_t<true>(const RunParams &, bool, int, int,
+                                                         size_t, cudaStream_t);
+extern template cudaError_t launch_plain_mixed_t<true>(const RunParams &, const PlainArgs &, bool,
+                                                       int, size_t, cudaStream_t);
+extern template cudaError_t configure_mixed_t<true>(size_t);
 
-template <int FK, bool TAB, int MAXT>
-static cudaError_t batched_t(const RunParams &p, int grid, int block, size_t smem, cudaStream_t s)
-{
-    if (p.flights_per_phase == 1)
-        k_batched<MixedElectron, FK, TAB, MAXT, 1><<<grid, block, smem, s>>>(p);
-    else
-        k_batched<MixedElectron, FK, TAB, MAXT, 0><<<grid, block, smem, s>>>(p);
-    return cudaGetLastError();
-}
-
-template <int FK, bool TAB>
-static cudaError_t batched(const RunParams &p, int grid, int block, size_t smem, cudaStream_t s)
-{
-    if (block <= 512) return batched_t<FK, TAB, 512>(p, grid, block, smem, s);
-    if (block <= 768) return batched_t<FK, TAB, 768>(p, grid, block, smem, s);
-    return batched_t<FK, TAB, 1024>(p, grid, block, smem, s);
-}
-
-template <int FK, bool TAB>
-static cudaError_t plain(const RunParams &p, const PlainArgs &a, int block, size_t smem,
-                         cudaStream_t s)
-{
-    const long long n = a.n_active;
-    if (n <= 0) return cudaSuccess;
-    k_plain_transport<MixedElectron, FK, TAB, kPlainThreadsMixed>
-        <<<(unsigned)((n + block - 1) / block), block, smem, s>>>(p, a.cur, n, a.fresh, a.parity,
-                                                                  a.aval);
-    return cudaGetLastError();
-}
-
-template <bool TAB>
-static cudaError_t batched_fk(const RunParams &p, int grid, int block, size_t smem, cudaStream_t s)
-{
-    switch (p.field.kind) {
-    case GT_FIELD_UNIFORM: return batched<GT_FIELD_UNIFORM, TAB>(p, grid, block, smem, s);
-    case GT_FIELD_PLATE: return batched<GT_FIELD_PLATE, TAB>(p, grid, block, smem, s);
-    case GT_FIELD_COAX: return batched<GT_FIELD_COAX, TAB>(p, grid, block, smem, s);
-    default: return batched<GT_FIELD_GRID, TAB>(p, grid, block, smem, s);
-    }
-}
-
-template <bool TAB>
-static cudaError_t plain_fk(const RunParams &p, const PlainArgs &a, int block, size_t smem,
-                            cudaStream_t s)
-{
-    switch (p.field.kind) {
-    case GT_FIELD_UNIFORM: return plain<GT_FIELD_UNIFORM, TAB>(p, a, block, smem, s);
-    case GT_FIELD_PLATE: return plain<GT_FIELD_PLATE, TAB>(p, a, block, smem, s);
-    case GT_FIELD_COAX: return plain<GT_FIELD_COAX, TAB>(p, a, block, smem, s);
-    default: return plain<GT_FIELD_GRID, TAB>(p, a, block, smem, s);
-    }
-}
+template cudaError_t launch_batched_mixed_t<false>(const RunParams &, bool, int, int, size_t,
+                                                   cudaStream_t);
+template cudaError_t launch_plain_mixed_t<false>(const RunParams &, const PlainArgs &, bool, int,
+                                                 size_t, cudaStream_t);
+template cudaError_t configure_mixed_t<false>(size_t);
+template int occupancy_batched_mixed_t<false>(int, bool, int, size_t);
 
 cudaError_t launch_batched_mixed(const RunParams &p, bool smem_table, int grid, int block,
                                  size_t smem, cudaStream_t s)
 {
-    return smem_table ? batched_fk<true>(p, grid, block, smem, s)
-                      : batched_fk<false>(p, grid, block, smem, s);
+    return p.gas.any_special ? launch_batched_mixed_t<true>(p, smem_table, grid, block, smem, s)
+                             : launch_batched_mixed_t<false>(p, smem_table, grid, block, smem, s);
 }
 
 cudaError_t launch_plain_mixed(const RunParams &p, const PlainArgs &a, bool smem_table, int block,
                                size_t smem, cudaStream_t s)
 {
-    return smem_table ? plain_fk<true>(p, a, block, smem, s) : plain_fk<false>(p, a, block, smem, s);
-}
-
-template <int FK, bool TAB, int MP>
-static cudaError_t configure_mp(size_t max_smem)
-{
-    cudaError_t e;
-    if ((e = allow_dynamic_smem(k_batched<MixedElectron, FK, TAB, 512, MP>, max_smem)) !=
-        cudaSuccess)
-        return e;
-    if ((e = allow_dynamic_smem(k_batched<MixedElectron, FK, TAB, 768, MP>, max_smem)) !=
-        cudaSuccess)
-        return e;
-    return allow_dynamic_smem(k_batched<MixedElectron, FK, TAB, 1024, MP>, max_smem);
-}
-
-template <int FK, bool TAB>
-static cudaError_t configure_one(size_t max_smem)
-{
-    cudaError_t e;
-    if ((e = configure_mp<FK, TAB, 0>(max_smem)) != cudaSuccess) return e;
-    if ((e = configure_mp<FK, TAB, 1>(max_smem)) != cudaSuccess) return e;
-    return allow_dynamic_smem(k_plain_transport<MixedElectron, FK, TAB, kPlainThreadsMixed>,
-                              max_smem);
-}
-
-template <bool TAB>
-static cudaError_t configure_tab(size_t max_smem)
-{
-    cudaError_t e;
-    if ((e = configure_one<GT_FIELD_UNIFORM, TAB>(max_smem)) != cudaSuccess) return e;
-    if ((e = configure_one<GT_FIELD_PLATE, TAB>(max_smem)) != cudaSuccess) return e;
-    if ((e = configure_one<GT_FIELD_COAX, TAB>(max_smem)) != cudaSuccess) return e;
-    return configure_one<GT_FIELD_GRID, TAB>(max_smem);
+    return p.gas.any_special ? launch_plain_mixed_t<true>(p, a, smem_table, block, smem, s)
+                             : launch_plain_mixed_t<false>(p, a, smem_table, block, smem, s);
 }
 
 cudaError_t configure_mixed(size_t max_smem)
 {
-    cudaError_t e = configure_tab<true>(max_smem);
+    cudaError_t e = configure_mixed_t<false>(max_smem);
     if (e != cudaSuccess) return e;
-    return configure_tab<false>(max_smem);
+    return configure_mixed_t<true>(max_smem);
 }
 
 int max_block_mixed() { return kMaxThreadsMixed; }
 
-template <int FK, bool TAB>
-static int occ(int block, size_t smem)
-{
-    int n = 0;
-    cudaError_t e;
-    if (block <= 512)
-        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_batched<MixedElectron, FK, TAB, 512>,
-                                                          block, smem);
-    else if (block <= 768)
-        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_batched<MixedElectron, FK, TAB, 768>,
-                                                          block, smem);
-    else
-        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_batched<MixedElectron, FK, TAB, 1024>,
-                                                          block, smem);
-    return e == cudaSuccess ? n : 0;
-}
-
-template <bool TAB>
-static int occ_fk(int field_kind, int block, size_t smem)
-{
-    switch (field_kind) {
-    case GT_FIELD_UNIFORM: return occ<GT_FIELD_UNIFORM, TAB>(block, smem);
-    case GT_FIELD_PLATE: return occ<GT_FIELD_PLATE, TAB>(block, smem);
-    case GT_FIELD_COAX: return occ<GT_FIELD_COAX, TAB>(block, smem);
-    default: return occ<GT_FIELD_GRID, TAB>(block, smem);
-    }
-}
-
 int occupancy_batched_mixed(int field_kind, bool smem_table, int block, size_t smem)
 {
-    return smem_table ? occ_fk<true>(field_kind, block, smem) : occ_fk<false>(field_kind, block, smem);
+    return occupancy_batched_mixed_t<false>(field_kind, smem_table, block, smem);
 }
 
 }  // namespace gt

@@ -54,6 +54,18 @@ cudaError_t launch_plain_fp64(const RunParams &p, const PlainArgs &a, int block,
                               cudaStream_t s);
 cudaError_t launch_plain_mixed(const RunParams &p, const PlainArgs &a, bool smem_table, int block,
                                size_t smem, cudaStream_t s);
+// The mixed launchers above dispatch on the gas: the general collision
+// (PHYS = true) or the basic gas's (gt_kernels_mixed.inl).
+template <bool PHYS>
+cudaError_t launch_batched_mixed_t(const RunParams &p, bool smem_table, int grid, int block,
+                                   size_t smem, cudaStream_t s);
+template <bool PHYS>
+cudaError_t launch_plain_mixed_t(const RunParams &p, const PlainArgs &a, bool smem_table,
+                                 int block, size_t smem, cudaStream_t s);
+template <bool PHYS>
+cudaError_t configure_mixed_t(size_t max_smem);
+template <bool PHYS>
+int occupancy_batched_mixed_t(int field_kind, bool smem_table, int block, size_t smem);
 // Raise the dynamic shared-memory limit of every transport instantiation.
 cudaError_t configure_fp64(size_t max_smem);
 cudaError_t configure_mixed(size_t max_smem);
