@@ -131,6 +131,9 @@ typedef struct {
     int32_t majorant;                /* 0: one global nu_max; 1: banded (below) */
     double window;                   /* banded: flight window = window / band rate */
     double band_width;               /* banded: eV per energy band (whole nodes) */
+    int32_t substeps;                /* field evaluations per flight (<= 1: one, held) */
+    int32_t crossing;                /* 1: an electron leaving the volume ends at the
+                                        first crossing of the boundary */
 } or_run_args;
 
 /* ------------------------------------------------ Philox4x32-10
@@ -305,6 +308,64 @@ void or_flight(double r[3], double v[3], const double a[3], const double w[3], d
     }
 }
 
+/* ------------------------------------------------ boundary crossings
+ * The first time in (0, hi] at which the flight from (r0, v0) under the
+ * held acceleration acc (and rotation w) is outside the volume, given that
+ * it is outside at hi: bisection to within hi * 2^-60; the state at the
+ * returned time is outside. */
+static double first_exit(const or_field *f, const double r0[3], const double v0[3],
+                         const double acc[3], const double w[3], double hi)
+{
+    double lo = 0.0;
+    for (int it = 0; it < 60; ++it) {
+        double mid = 0.5 * (lo + hi);
+        double r[3] = {r0[0], r0[1], r0[2]}, v[3] = {v0[0], v0[1], v0[2]};
+        or_flight(r, v, acc, w, mid);
+        if (or_boundary(f, r))
+            hi = mid;
+        else
+            lo = mid;
+    }
+    return hi;
+}
+
+/* Plate without B: z(t) = z0 + vz t + az t^2 / 2 is a parabola, so a step
+ * that starts and ends inside may still have left the gap at its vertex.
+ * Returns the status at the vertex if the vertex lies inside (0, h) and
+ * outside the gap, with *t_out the vertex time; else 0. */
+static int plate_vertex_exit(const or_field *f, const double r0[3], const double v0[3],
+                             const double acc[3], double h, double *t_out)
+{
+    if (acc[2] == 0.0) return 0;
+    double tv = -v0[2] / acc[2];
+    if (!(tv > 0.0 && tv < h)) return 0;
+    double r[3] = {r0[0] + v0[0] * tv + 0.5 * acc[0] * tv * tv,
+                   r0[1] + v0[1] * tv + 0.5 * acc[1] * tv * tv,
+                   r0[2] + v0[2] * tv + 0.5 * acc[2] * tv * tv};
+    int st = or_boundary(f, r);
+    if (st) *t_out = tv;
+    return st;
+}
+
+/* Largest field magnitude of the volume (V/cm): the bound of the banded
+ * majorant when the field is re-evaluated along a flight.  0 for fields
+ * that are the same everywhere (the held-field bound stays exact). */
+static double field_emax(const or_field *f)
+{
+    if (f->kind == OR_COAX) return fabs(f->voltage) / (log(f->tube_r / f->wire_r) * f->wire_r);
+    if (f->kind == OR_GRID) {
+        double m = 0.0;
+        int64_t n = (int64_t)f->nx * f->ny * f->nz;
+        for (int64_t i = 0; i < n; ++i) {
+            const float *p = f->grid + 4 * i;
+            double e = sqrt((double)p[0] * p[0] + (double)p[1] * p[1] + (double)p[2] * p[2]);
+            if (e > m) m = e;
+        }
+        return m;
+    }
+    return 0.0;
+}
+
 /* ------------------------------------------------ rate table */
 typedef struct {
     int L, N;
@@ -317,6 +378,8 @@ typedef struct {
     double top;  /* largest total rate over the nodes */
     int band_nodes, B; /* banded majorant: nodes per band, number of bands */
     double *bmax;      /* [B]: largest total rate over the band's nodes */
+    double field_emax; /* > 0: bound |E| by this in the banded majorant (a field
+                          re-evaluated along the flight), 0: the held field */
 } or_table;
 
 static int table_build(const or_gas *g, or_table *t)
@@ -419,7 +482,14 @@ static double banded_majorant(const or_table *tb, const double v[3], const doubl
     double eps0 = kinetic_energy(v);
     double w = window / tb->bmax[band_of(tb, eps0)];
     double lo, hi;
-    if (!has_b) {
+    if (tb->field_emax > 0.0) {
+        /* the field changes along the flight: the reach of the largest
+         * field magnitude (|dv/dt| <= a1 E_max) bounds the energy change */
+        double Em = tb->field_emax;
+        double D = Em * (sqrt(dot3(v, v)) * w + 0.5 * (OR_ACCEL_PER_VCM * Em) * w * w);
+        lo = eps0 - D;
+        hi = eps0 + D;
+    } else if (!has_b) {
         double vE = dot3(v, E), E2 = dot3(E, E);
         double gw = -vE * w + 0.5 * OR_ACCEL_PER_VCM * E2 * w * w;
         hi = eps0 + (gw > 0.0 ? gw : 0.0);
@@ -455,6 +525,7 @@ double or_majorant(const or_gas *g, double band_width, const double v[3], const 
         return -1.0;
     }
     double tau = 0.0;
+    t.field_emax = 0.0;
     double nu = banded_majorant(&t, v, E, has_b, window, &tau);
     if (tau_out) *tau_out = tau;
     free(t.cum);
@@ -705,14 +776,44 @@ static void transport_electron(const or_table *tb, const or_field *f, const or_r
             dt = a->t_max - t;
             timed = 1;
         }
-        double r_before[3] = {r[0], r[1], r[2]};
-        or_flight(r, v, acc, w, dt);
-        t = timed ? a->t_max : t + dt;
+        /* The flight, in `ns` equal sub-steps with the field evaluated at
+         * the start of each (ns = 1: the field of the flight's start is
+         * held).  With `crossing`, a sub-step that leaves the volume ends at
+         * its first boundary crossing. */
+        const int ns = a->substeps > 1 ? a->substeps : 1;
+        const double h = ns > 1 ? dt / ns : dt;
+        double t_end = timed ? a->t_max : t + dt;
+        for (int sub = 0; sub < ns; ++sub) {
+            if (sub > 0) {
+                or_field_eval(f, plate_e, r, E);
+                for (int d = 0; d < 3; ++d) acc[d] = -OR_ACCEL_PER_VCM * E[d];
+            }
+            double r0[3] = {r[0], r[1], r[2]}, v0[3] = {v[0], v[1], v[2]};
+            or_flight(r, v, acc, w, h);
+            status = or_boundary(f, r);
+            double tc = h;
+            if (a->crossing && f->kind == OR_PLATE && !has_b) {
+                /* the vertex comes before the end: if it is outside, the
+                 * first crossing lies before it */
+                int sv = plate_vertex_exit(f, r0, v0, acc, h, &tc);
+                if (sv) status = sv;
+            }
+            if (a->crossing && status) {
+                double hs = first_exit(f, r0, v0, acc, w, tc);
+                r[0] = r0[0]; r[1] = r0[1]; r[2] = r0[2];
+                v[0] = v0[0]; v[1] = v0[1]; v[2] = v0[2];
+                or_flight(r, v, acc, w, hs);
+                status = or_boundary(f, r);
+                t_end = t + sub * h + hs;
+            } else if (status && sub < ns - 1) {
+                t_end = t + (sub + 1) * h;
+            }
+            /* work done by the field on the electron (eV): -E . dr */
+            work += -(E[0] * (r[0] - r0[0]) + E[1] * (r[1] - r0[1]) + E[2] * (r[2] - r0[2]));
+            if (status) break;
+        }
+        t = t_end;
         n_flight = flight + 1u;
-        /* work done by the held field on the electron (eV): -E . dr */
-        work += -(E[0] * (r[0] - r_before[0]) + E[1] * (r[1] - r_before[1]) +
-                  E[2] * (r[2] - r_before[2]));
-        status = or_boundary(f, r);
         if (status) break;
         if (timed) {
             status = OR_TIME;
@@ -858,8 +959,10 @@ int or_run(const or_gas *g, const or_field *f, const or_run_args *a, or_result *
     if (f->kind == OR_GRID && (f->nx < 2 || f->ny < 2 || f->nz < 2 || !f->grid)) return -3;
     for (int64_t p = 0; p < a->n_primaries; ++p)
         if (a->aval[p] < 0 || a->aval[p] >= a->n_avalanches) return -3;
+    if (a->substeps < 0 || a->crossing < 0 || a->crossing > 1) return -3;
     or_table tb;
     if (table_build(g, &tb)) return -2;
+    tb.field_emax = a->substeps > 1 ? field_emax(f) : 0.0;
     if (a->majorant == 1) {
         if (!(a->window > 0.0) || !(a->band_width > 0.0) || bands_build(&tb, a->band_width)) {
             free(tb.cum);

@@ -61,7 +61,7 @@ class _Run(C.Structure):
                 ("aval", C.c_void_p), ("uid", C.c_void_p), ("aval_field", C.c_void_p),
                 ("seed", C.c_uint64), ("t_max", C.c_double), ("coll_limit", C.c_uint32),
                 ("n_threads", C.c_int32), ("majorant", C.c_int32), ("window", C.c_double),
-                ("band_width", C.c_double)]
+                ("band_width", C.c_double), ("substeps", C.c_int32), ("crossing", C.c_int32)]
 
 
 def _load():
@@ -252,10 +252,12 @@ def majorant(gas, band_width: float, v, e_field, has_b: bool, window: float):
 # -------------------------------------------------------------------- run
 def run(gas, field, prim, seed: int = 0, t_max: float = 0.0, coll_limit: int = 0,
         n_threads: int | None = None, majorant: int = 0, window: float = 2.0,
-        band_width: float = 1.0) -> dict:
+        band_width: float = 1.0, substeps: int = 1, crossing: bool = False) -> dict:
     """Transport every avalanche of `prim` and return a dict of arrays
     (majorant 0: one global nu_max; 1: the banded majorant with flight
-    window `window` / band rate and bands of `band_width` eV):
+    window `window` / band rate and bands of `band_width` eV; `substeps`
+    field evaluations per flight; `crossing`: an electron that leaves ends
+    at its first boundary crossing):
     x0..e0 (start), x1..e1 (end), status, aval, uid, n_flight, ledger [n, 4]
     (field work, inelastic loss, recoil loss, secondary share; eV),
     electrons [n_avalanches], tallies [n_avalanches, L+1] (real collisions
@@ -288,6 +290,8 @@ def run(gas, field, prim, seed: int = 0, t_max: float = 0.0, coll_limit: int = 0
     ra.majorant = majorant
     ra.window = window
     ra.band_width = band_width
+    ra.substeps = int(substeps)
+    ra.crossing = int(bool(crossing))
     handle = C.c_void_p()
     rc = lib.or_run(C.byref(g), C.byref(f), C.byref(ra), C.byref(handle))
     if rc != 0:

@@ -704,3 +704,113 @@ def test_screened_anisotropy_diffusion_closed_form():
     expect = P.speed_sq(eps0) / 1000.0 ** 2 * (2 * N + 2 * np.sum((N - k) * g ** k))
     assert P.within_sigma(r2.mean(), expect, r2.std() / math.sqrt(n))
     assert np.allclose(o["e1"], eps0, rtol=1e-12)
+
+
+# --------------------------------------- boundary crossings and sub-steps
+def by_uid(o):
+    """Per-electron arrays of a run ordered by electron id (primaries: input order)."""
+    idx = np.argsort(o["uid"], kind="stable")
+    n = len(o["uid"])
+    return {k: (v[idx] if hasattr(v, "__len__") and len(v) == n and k not in
+                ("electrons", "tallies") else v) for k, v in o.items()}
+
+
+def _collisionless(n, e_field, seed):
+    """Plate electrons in a gas with a negligible rate: each flight runs to
+    the 100 ns time limit unless the electron leaves first."""
+    w = W.plate(n_avalanches=n, e_field=e_field, seed=seed)
+    w.gas = W.model_gas(1e-9)
+    return w
+
+
+def test_crossing_at_the_anode_closed_form():
+    """Uniform acceleration a from z = 0: the anode (z = d) is reached at
+    t* = (sqrt(vz^2 + 2 a d) - vz) / a; with exact crossings the endpoint is
+    the crossing point at t*, without them the post-flight point."""
+    w = _collisionless(200, 30_000.0, 67)
+    a = P.ACCEL_PER_VCM * 30_000.0
+    vz = w.primaries.dz * np.sqrt(P.speed_sq(w.primaries.e))
+    ts = (np.sqrt(vz * vz + 2 * a * w.field.gap) - vz) / a
+    o = by_uid(oracle.run(w.gas, w.field, w.primaries, seed=67, t_max=100.0, crossing=True))
+    assert np.all(o["status"] == W.ANODE)
+    # (1e-10: e/m is quoted to 12 digits; the test derives it from e and m_e)
+    assert np.allclose(o["t1"] - o["t0"], ts, rtol=1e-10, atol=0)
+    assert np.all((o["z1"] >= w.field.gap) & (o["z1"] - w.field.gap < 1e-12))
+    led = o["ledger"]
+    assert np.allclose(o["e1"], o["e0"] + led[:, 0], rtol=1e-12, atol=1e-12)
+    p = oracle.run(w.gas, w.field, w.primaries, seed=67, t_max=100.0)
+    assert np.all(p["z1"] > 1.0)  # the post-flight point is far beyond the anode
+
+
+def test_crossing_catches_an_exit_and_return():
+    """An electron started 1 um from the cathode towards it, in a field
+    that turns it back: it touches the cathode iff vz^2 > 2 a z0, at the
+    smaller root of z0 + vz t + a t^2 / 2 = 0.  A post-flight test misses it
+    (the flight ends at the anode)."""
+    n = 400
+    w = _collisionless(n, 30_000.0, 69)
+    a = P.ACCEL_PER_VCM * 30_000.0
+    z0 = 1e-4
+    w.primaries.z[:] = z0
+    w.primaries.dz[:] = -np.abs(w.primaries.dz)
+    w.primaries.e[:] = np.random.default_rng(5).uniform(1.0, 20.0, n)
+    vz = w.primaries.dz * np.sqrt(P.speed_sq(w.primaries.e))
+    hits = vz * vz > 2 * a * z0
+    assert 0.2 < hits.mean() < 0.8
+    o = by_uid(oracle.run(w.gas, w.field, w.primaries, seed=69, t_max=100.0, crossing=True))
+    assert np.array_equal(o["status"] == W.CATHODE, hits)
+    ts = (-vz[hits] - np.sqrt(vz[hits] ** 2 - 2 * a * z0)) / a
+    assert np.allclose(o["t1"][hits] - o["t0"][hits], ts, rtol=1e-9, atol=0)
+    assert np.all((o["z1"][hits] < 0.0) & (o["z1"][hits] > -1e-12))
+    p = oracle.run(w.gas, w.field, w.primaries, seed=69, t_max=100.0)
+    assert np.all(p["status"] == W.ANODE)
+
+
+def _coax_potential(field, r):
+    """Potential of the coax (V): V at the wire, 0 at the tube."""
+    return field.voltage * np.log(r / field.tube_r) / math.log(field.wire_r / field.tube_r)
+
+
+def test_substeps_converge_to_energy_conservation():
+    """Collisionless electrons in the coax field drift to the wire: the
+    energy gained must equal e (V(r1) - V(r0)).  With the field held over a
+    flight it does not; re-evaluating it over n sub-steps the error falls
+    like 1/n.  With exact crossings the electrons end on the wire."""
+    w = W.coax(n_avalanches=100, r_lo=0.004, r_hi=0.02, b_axial=0.0, seed=71)
+    w.gas = W.model_gas(1e-9)
+    errs, times = [], []
+    for n in (32, 128, 512):  # one flight of 0.05 ns (the fall takes ~0.02 ns)
+        o = oracle.run(w.gas, w.field, w.primaries, seed=71, t_max=0.05, substeps=n,
+                       crossing=True)
+        assert np.all(o["status"] == W.WIRE)
+        r0 = np.hypot(o["x0"], o["y0"])
+        r1 = np.hypot(o["x1"], o["y1"])
+        assert np.all(r1 <= w.field.wire_r) and np.all(r1 > w.field.wire_r * (1 - 1e-9))
+        gain = _coax_potential(w.field, r1) - _coax_potential(w.field, r0)
+        errs.append(np.abs((o["e1"] - o["e0"]) - gain).max() / gain.max())
+        times.append(by_uid(o)["t1"] - by_uid(o)["t0"])
+        led = o["ledger"]
+        assert np.allclose(o["e1"], o["e0"] + led[:, 0], rtol=1e-12, atol=1e-9)
+    assert errs[1] < errs[0] / 3 and errs[2] < errs[1] / 3, errs
+    assert errs[2] < 2e-2
+    # the fall times converge too
+    assert np.allclose(times[2], times[1], rtol=0.05) and times[2].min() > 1e-3
+
+
+def test_crossing_keeps_the_physics_of_the_plate():
+    """With collisions, exact crossings change only where electrons end:
+    the gain distribution is the same (KS), every anode endpoint lies on
+    the anode, and the ledger closes."""
+    from scipy import stats
+    n = 200
+    w = W.plate(n_avalanches=n, e_field=40_000.0, seed=73)
+    a = oracle.run(w.gas, w.field, w.primaries, seed=73, t_max=w.t_max)
+    b = oracle.run(w.gas, w.field, w.primaries, seed=73, t_max=w.t_max, crossing=True)
+    ga = np.bincount(a["aval"][a["status"] == W.ANODE], minlength=n)
+    gb = np.bincount(b["aval"][b["status"] == W.ANODE], minlength=n)
+    assert stats.ks_2samp(np.log1p(ga), np.log1p(gb)).pvalue > 0.01
+    an = b["status"] == W.ANODE
+    assert np.all((b["z1"][an] >= w.field.gap) & (b["z1"][an] - w.field.gap < 1e-12))
+    led = b["ledger"]
+    assert np.allclose(b["e1"], b["e0"] + led[:, 0] - led[:, 1] - led[:, 2] - led[:, 3],
+                       rtol=1e-9, atol=1e-9)
