@@ -310,6 +310,16 @@ def run_ours(args) -> None:
                     "value_kernel_time": p_real / (p_ms / 1e3), "unit": UNIT,
                     "flights_per_real": p_fl / max(p_real, 1), "gain": p_obs[0]}
         av.set_gas(w.gas)
+        # the basic gas with exact boundary crossings (the general kernel)
+        c_opt = dataclasses.replace(opt, crossing=1)
+        c_real, c_ms = 0, 0.0
+        for _ in range(2):
+            flush.fill_(1)
+            c_st = av.run(prim_dev, c_opt, cap, stream=stream, allow=(A.GT_OK,))
+            c_real += c_st["real_collisions"]
+            c_ms += c_st["transport_ms"]
+        physical["crossing"] = {"value_kernel_time": c_real / (c_ms / 1e3), "unit": UNIT,
+                                "note": "basic gas, endpoints at the first boundary crossing"}
 
     # plain FP64 GPU path (the paper's structure: one avalanche at a time, one
     # launch per generation) on a sample, with both majorants

@@ -183,6 +183,18 @@ typedef struct {
     int32_t majorant;                 /* GT_MAJORANT_GLOBAL / GT_MAJORANT_BANDED */
     int32_t pad;
     double majorant_window;           /* banded: window factor c, 0 = 2 */
+    int32_t substeps;                 /* field evaluations per flight: <= 1 holds
+                                         the field of the flight's start (Sec. 2
+                                         reading); n > 1 splits every flight into
+                                         n equal sub-steps, each in the field at
+                                         its own start (at most 4096) */
+    int32_t crossing;                 /* 0: an electron that leaves the volume ends
+                                         at the point after its (sub-)step; 1: at
+                                         its first boundary crossing, found by
+                                         bisection on the exact motion of the
+                                         (sub-)step (to 2^-60 of it); for the plate
+                                         without B a step that leaves and returns
+                                         is caught at the vertex of z(t) */
 } gt_run;
 
 /* Majorant of the null-collision flights.

@@ -67,7 +67,8 @@ class gt_run(C.Structure):
                 ("size_limit", C.c_uint64), ("spin_limit_ms", C.c_double),
                 ("time_limit_ms", C.c_double), ("debug_flags", C.c_int32),
                 ("flights_per_phase", C.c_int32), ("majorant", C.c_int32), ("pad", C.c_int32),
-                ("majorant_window", C.c_double)]
+                ("majorant_window", C.c_double), ("substeps", C.c_int32),
+                ("crossing", C.c_int32)]
 
 
 _EP_ARRAYS = ("x0", "y0", "z0", "t0", "e0", "x1", "y1", "z1", "t1", "e1", "status", "aval",
@@ -282,6 +283,8 @@ class RunOptions:
     spin_limit_ms: float = 0.0
     time_limit_ms: float = 0.0
     debug_flags: int = 0
+    substeps: int = 0          # field evaluations per flight (<= 1: held field)
+    crossing: int = 0          # 1: leaving electrons end at the first crossing
 
 
 class Avalanche:
@@ -416,6 +419,8 @@ class Avalanche:
         r.spin_limit_ms = opt.spin_limit_ms
         r.time_limit_ms = opt.time_limit_ms
         r.debug_flags = opt.debug_flags
+        r.substeps = opt.substeps
+        r.crossing = opt.crossing
         return r
 
     def run(self, prim: dict, opt: RunOptions, capacity: int, stream=None,

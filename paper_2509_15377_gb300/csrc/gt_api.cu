@@ -389,6 +389,7 @@ int field_setup(gt_ctx *ctx, const gt_field *f)
         d.wire_r2 = f->wire_r * f->wire_r;
         d.tube_r2 = f->tube_r * f->tube_r;
         d.coax_k = f->voltage / std::log(f->tube_r / f->wire_r);
+        d.emax = std::fabs(d.coax_k) / f->wire_r;
         break;
     case GT_FIELD_GRID:
         if (f->nx < 2 || f->ny < 2 || f->nz < 2 || f->nx > (1 << 22) || f->ny > (1 << 22) ||
@@ -406,6 +407,11 @@ int field_setup(gt_ctx *ctx, const gt_field *f)
         d.hi[2] = f->origin[2] + (f->nz - 1) * f->spacing[2];
         d.wire_r2 = f->wire_r * f->wire_r;
         d.grid = reinterpret_cast<const float4 *>(f->grid);
+        {
+            DeviceGuard dg(ctx->device);
+            if (!dg.ok) return GT_ERR_CUDA;
+            GT_CUDA(ctx, grid_emax(d.grid, (long long)f->nx * f->ny * f->nz, ctx->sms, &d.emax));
+        }
         break;
     default:
         return GT_ERR_ARG;
@@ -454,7 +460,8 @@ static int validate_run(gt_ctx *ctx, const gt_run *r, const gt_endpoints *o, voi
     if (r->block < 0 || r->refill_period < 0 || r->grid < 0 || r->flights_per_phase < 0)
         return GT_ERR_ARG;
     if ((r->majorant != GT_MAJORANT_GLOBAL && r->majorant != GT_MAJORANT_BANDED) ||
-        !(r->majorant_window >= 0.0) || !std::isfinite(r->majorant_window))
+        !(r->majorant_window >= 0.0) || !std::isfinite(r->majorant_window) ||
+        r->substeps < 0 || r->substeps > 4096 || (r->crossing != 0 && r->crossing != 1))
         return GT_ERR_ARG;
     if (r->block && (r->block % 32 != 0 ||
                      r->block > (r->precision == GT_FP64 ? max_block_fp64() : max_block_mixed())))
@@ -538,6 +545,12 @@ int avalanche_run(gt_ctx *ctx, const gt_run *r, const gt_endpoints *o, void *ws,
     p.majorant = r->majorant;
     p.window = r->majorant_window > 0.0 ? r->majorant_window : 2.0;
     p.window_f = (float)p.window;
+    p.substeps = r->substeps > 1 ? r->substeps : 1;
+    p.crossing = r->crossing;
+    // a field re-evaluated along the flight: bound its reach by the largest
+    // field of the volume (uniform and plate fields do not change)
+    p.field_emax = p.substeps > 1 ? ctx->field.emax : 0.0;
+    p.field_emax_f = (float)(p.field_emax * (1.0 + 1e-6));
     p.size_limit = r->size_limit;
     p.spin_limit_ns = (long long)((r->spin_limit_ms > 0 ? r->spin_limit_ms : 60000.0) * 1e6);
     p.time_limit_ns = (long long)((r->time_limit_ms > 0 ? r->time_limit_ms : 600000.0) * 1e6);

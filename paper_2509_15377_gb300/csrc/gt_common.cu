@@ -4,6 +4,8 @@
 #include "gt_kernels.cuh"
 #include "gt_launch.h"
 
+#include <cstring>
+
 namespace gt {
 
 // Primary injection: primary i goes to queue / endpoint slot i with its
@@ -143,6 +145,39 @@ cudaError_t launch_count_electrons(const RunParams &p, int sms, cudaStream_t s)
 {
     k_count_electrons<<<sms * 4, 256, 0, s>>>(p);
     return cudaGetLastError();
+}
+
+// Largest |E| over the nodes of a grid map (bits of non-negative floats
+// order like the floats, so an integer atomicMax finds the largest).
+__global__ void k_grid_emax(const float4 *grid, long long n, unsigned *out)
+{
+    float m = 0.0f;
+    const long long stride = (long long)gridDim.x * blockDim.x;
+    for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += stride) {
+        const float4 e = __ldg(grid + i);
+        m = fmaxf(m, sqrtf(e.x * e.x + e.y * e.y + e.z * e.z));
+    }
+    for (int o = 16; o > 0; o >>= 1) m = fmaxf(m, __shfl_xor_sync(FULL, m, o));
+    if ((threadIdx.x & 31) == 0) atomicMax(out, __float_as_uint(m));
+}
+
+cudaError_t grid_emax(const float4 *grid, long long n, int sms, double *emax)
+{
+    unsigned *d = nullptr, h = 0;
+    cudaError_t e = cudaMalloc((void **)&d, sizeof(unsigned));
+    if (e != cudaSuccess) return e;
+    e = cudaMemset(d, 0, sizeof(unsigned));
+    if (e == cudaSuccess) {
+        k_grid_emax<<<sms * 4, 256>>>(grid, n, d);
+        e = cudaGetLastError();
+    }
+    if (e == cudaSuccess) e = cudaMemcpy(&h, d, sizeof(unsigned), cudaMemcpyDeviceToHost);
+    cudaFree(d);
+    float f;
+    memcpy(&f, &h, sizeof(f));
+    // one ulp up: the FP32 norm above may round below the exact one
+    *emax = (double)f * (1.0 + 1e-6);
+    return e;
 }
 
 // ---------------------------------------------------------- observables

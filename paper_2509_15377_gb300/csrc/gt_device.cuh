@@ -74,6 +74,7 @@ struct DevField {
     float wire_r2_hi_f, tube_r2_lo_f;    // radial pre-test limits (1e-5 margins)
     float box_lo_f[3], box_hi_f[3];      // map-box pre-test limits (inside by 1e-5)
     float cell_hi_f[3], node_hi_f[3];    // n - 2 and n - 1 per axis
+    double emax;                         // largest |E| of the volume (COAX, GRID; else 0)
 };
 
 struct Header {  // at the start of the work space, 256 bytes
@@ -128,6 +129,10 @@ struct RunParams {
     int majorant;           // GT_MAJORANT_GLOBAL / GT_MAJORANT_BANDED
     double window;          // banded: window factor c
     float window_f;
+    int substeps;           // field evaluations per flight (1: held field)
+    int crossing;           // 1: leaving electrons end at the first crossing
+    double field_emax;      // > 0: bound |E| by this in the banded majorant
+    float field_emax_f;
     uint64_t size_limit;
     long long spin_limit_ns, time_limit_ns;
     int n_avalanches;
@@ -471,11 +476,17 @@ __device__ __forceinline__ T band_range_max(const T *bt, int n_bands, int lo, in
 // end, lo its vertex (t* = v.E / (a1 |E|^2) when inside the window) or its
 // smaller end.  With B, |dv/dt| <= a1 |E| bounds the displacement, and the
 // range is eps0 -+ |E| (|v| tau + a1 |E| tau^2 / 2).
-__device__ __forceinline__ void reach64(int has_b, double eps0, double vx, double vy, double vz,
-                                        double ex, double ey, double ez, double tau, double &lo,
-                                        double &hi)
+__device__ __forceinline__ void reach64(int has_b, double emax, double eps0, double vx, double vy,
+                                        double vz, double ex, double ey, double ez, double tau,
+                                        double &lo, double &hi)
 {
-    if (!has_b) {
+    if (emax > 0.0) {
+        // a field re-evaluated along the flight: |dv/dt| <= a1 emax
+        const double D = emax * (sqrt(vx * vx + vy * vy + vz * vz) * tau +
+                                 0.5 * (kAccel * emax) * tau * tau);
+        lo = eps0 - D;
+        hi = eps0 + D;
+    } else if (!has_b) {
         const double vE = vx * ex + vy * ey + vz * ez, E2 = ex * ex + ey * ey + ez * ez;
         const double gw = -vE * tau + 0.5 * kAccel * E2 * tau * tau;
         hi = eps0 + (gw > 0.0 ? gw : 0.0);
@@ -496,11 +507,16 @@ __device__ __forceinline__ void reach64(int has_b, double eps0, double vx, doubl
 
 // FP32 version, widened by 1e-5 of the energies involved against rounding.
 template <int FK>
-__device__ __forceinline__ void reach32(int has_b, float eps0, float vx, float vy, float vz,
-                                        float ex, float ey, float ez, float plate_e, float tau,
-                                        float &lo, float &hi)
+__device__ __forceinline__ void reach32(int has_b, float emax, float eps0, float vx, float vy,
+                                        float vz, float ex, float ey, float ez, float plate_e,
+                                        float tau, float &lo, float &hi)
 {
-    if (!has_b) {
+    if (emax > 0.0f) {
+        const float D = emax * fmaf(0.5f * kAccelF * emax * tau, tau,
+                                    sqrtf(vx * vx + vy * vy + vz * vz) * tau) * 1.00001f;
+        lo = eps0 - D;
+        hi = eps0 + D;
+    } else if (!has_b) {
         const float vE = FK == GT_FIELD_PLATE ? -vz * plate_e : fmaf(vx, ex, fmaf(vy, ey, vz * ez));
         const float E2 = FK == GT_FIELD_PLATE ? plate_e * plate_e
                                               : fmaf(ex, ex, fmaf(ey, ey, ez * ez));
@@ -701,6 +717,30 @@ static __device__ __noinline__ int boundary_confirm64(const double *xb, const do
     return 0;
 }
 
+// FP32 boundary status of a mixed-precision position (the crossing search):
+// plate limits zg (anode) and zc (cathode) as offsets from the FP64 base,
+// other kinds from the FP32 position (px + ox, ...).
+template <int FK>
+__device__ __forceinline__ int outside32(const DevField &f, float zg, float zc, float x, float y,
+                                         float z)
+{
+    if (FK == GT_FIELD_PLATE) {
+        if (z >= zg) return GT_ST_ANODE;
+        if (z < zc) return GT_ST_CATHODE;
+    } else if (FK == GT_FIELD_COAX) {
+        const float r2 = x * x + y * y;
+        if (r2 <= (float)f.wire_r2) return GT_ST_WIRE;
+        if (r2 >= (float)f.tube_r2) return GT_ST_TUBE;
+    } else if (FK == GT_FIELD_GRID) {
+        const float r2 = x * x + y * y;
+        if (f.wire_r2 > 0.0 && r2 <= (float)f.wire_r2) return GT_ST_WIRE;
+        if (x < (float)f.origin[0] || x > (float)f.hi[0] || y < (float)f.origin[1] ||
+            y > (float)f.hi[1] || z < (float)f.origin[2] || z > (float)f.hi[2])
+            return GT_ST_OUT_OF_MAP;
+    }
+    return 0;
+}
+
 // ============================================================ FP64 electron
 struct Fp64Electron {
     static constexpr bool kTwoPhase = false;
@@ -747,10 +787,82 @@ struct Fp64Electron {
         return status ? EV_RETIRE : EV_NONE;
     }
 
+    // Exact motion over dt with the acceleration a (and the field's B).
+    __device__ __forceinline__ void move(const RunParams &p, double ax, double ay, double az,
+                                         double dt)
+    {
+        if (!p.field.has_b) {
+            x = x + vx * dt + 0.5 * ax * dt * dt;
+            y = y + vy * dt + 0.5 * ay * dt * dt;
+            z = z + vz * dt + 0.5 * az * dt * dt;
+            vx += ax * dt; vy += ay * dt; vz += az * dt;
+        } else {
+            double dx, dy, dz;
+            lorentz_step<double>(p.field.w, ax, ay, az, dt, vx, vy, vz, dx, dy, dz);
+            x += dx; y += dy; z += dz;
+        }
+    }
+
+    // A flight of length dt in p.substeps equal sub-steps, the field
+    // evaluated at the start of each; with p.crossing a sub-step that leaves
+    // the volume ends at its first boundary crossing (bisection on the exact
+    // motion to 2^-60 of the sub-step; for the plate without B the vertex of
+    // z(t) catches a sub-step that leaves and returns).  Moves the electron,
+    // returns its boundary status (0 inside) and updates t_end when the
+    // electron leaves before the flight's end.
+    template <int FK>
+    __device__ int fly_steps(const RunParams &p, double dt, double ex, double ey, double ez,
+                             double &t_end)
+    {
+        const int ns = p.substeps > 1 ? p.substeps : 1;
+        const double h = ns > 1 ? dt / ns : dt;
+        for (int sub = 0; sub < ns; ++sub) {
+            if (sub > 0) field64<FK>(p.field, plate_e, x, y, z, ex, ey, ez);
+            const double ax = -kAccel * ex, ay = -kAccel * ey, az = -kAccel * ez;
+            const double x0 = x, y0 = y, z0 = z, vx0 = vx, vy0 = vy, vz0 = vz;
+            move(p, ax, ay, az, h);
+            int st = boundary64<FK>(p.field, x, y, z);
+            double tc = h;
+            if (FK == GT_FIELD_PLATE && p.crossing && !p.field.has_b && az != 0.0) {
+                const double tv = -vz0 / az;
+                if (tv > 0.0 && tv < h) {
+                    const int sv = boundary64<FK>(p.field, x0 + vx0 * tv + 0.5 * ax * tv * tv,
+                                                  y0 + vy0 * tv + 0.5 * ay * tv * tv,
+                                                  z0 + vz0 * tv + 0.5 * az * tv * tv);
+                    if (sv) {
+                        st = sv;
+                        tc = tv;
+                    }
+                }
+            }
+            if (p.crossing && st) {
+                double lo = 0.0, hi = tc;
+                for (int it = 0; it < 60; ++it) {
+                    const double mid = 0.5 * (lo + hi);
+                    x = x0; y = y0; z = z0; vx = vx0; vy = vy0; vz = vz0;
+                    move(p, ax, ay, az, mid);
+                    if (boundary64<FK>(p.field, x, y, z))
+                        hi = mid;
+                    else
+                        lo = mid;
+                }
+                x = x0; y = y0; z = z0; vx = vx0; vy = vy0; vz = vz0;
+                move(p, ax, ay, az, hi);
+                t_end = t + sub * h + hi;
+                return boundary64<FK>(p.field, x, y, z);
+            }
+            if (st) {
+                if (sub < ns - 1) t_end = t + (sub + 1) * h;
+                return st;
+            }
+        }
+        return 0;
+    }
+
     // One flight and its collision (Fig. 2: "Find E field and add random
     // time step", "Collision?", "ionisation or attachment?").  (PHYS is
     // ignored: the FP64 step always handles every gas.)
-    template <int FK, bool PHYS = true>
+    template <int FK, bool PHYS = true, bool GEO = true>
     __device__ __forceinline__ int fly(const RunParams &p, const Tables &tb, ChildT &ch)
     {
         if (nf == 0xFFFFFFFFu) {
@@ -769,7 +881,7 @@ struct Fp64Electron {
             const double eps0 = (vx * vx + vy * vy + vz * vz) * kInvTwoAccel;
             const double tau = p.window / __ldg(p.gas.band64 + band_index64(p.gas, eps0));
             double lo, hi;
-            reach64(p.field.has_b, eps0, vx, vy, vz, ex, ey, ez, tau, lo, hi);
+            reach64(p.field.has_b, p.field_emax, eps0, vx, vy, vz, ex, ey, ez, tau, lo, hi);
             nu = band_range_max(p.gas.band64, p.gas.n_bands, band_index64(p.gas, lo),
                                 band_index64(p.gas, hi));
             dt = -log(u01d(w.x)) / nu;
@@ -785,19 +897,16 @@ struct Fp64Electron {
             dt = p.t_max - t;
             timed = true;
         }
-        if (!p.field.has_b) {
-            x = x + vx * dt + 0.5 * ax * dt * dt;
-            y = y + vy * dt + 0.5 * ay * dt * dt;
-            z = z + vz * dt + 0.5 * az * dt * dt;
-            vx += ax * dt; vy += ay * dt; vz += az * dt;
+        double t_end = timed ? p.t_max : t + dt;
+        int st;
+        if (p.substeps > 1 || p.crossing) {
+            st = fly_steps<FK>(p, dt, ex, ey, ez, t_end);
         } else {
-            double dx, dy, dz;
-            lorentz_step<double>(p.field.w, ax, ay, az, dt, vx, vy, vz, dx, dy, dz);
-            x += dx; y += dy; z += dz;
+            move(p, ax, ay, az, dt);
+            st = boundary64<FK>(p.field, x, y, z);
         }
-        t = timed ? p.t_max : t + dt;
+        t = t_end;
         nf = flight + 1u;
-        const int st = boundary64<FK>(p.field, x, y, z);
         if (st) {
             status = st;
             return EV_RETIRE;
@@ -1025,10 +1134,91 @@ struct MixedElectron {
                                       f.hi[1], f.hi[2]);
     }
 
+    // Exact motion of the FP32 offsets over dt with the acceleration a.
+    __device__ __forceinline__ void move(const RunParams &p, float ax, float ay, float az, float dt)
+    {
+        float dx, dy, dz;
+        if (!p.field.has_b) {
+            const float h = 0.5f * dt;
+            dx = dt * fmaf(h, ax, vx);
+            dy = dt * fmaf(h, ay, vy);
+            dz = dt * fmaf(h, az, vz);
+            vx = fmaf(ax, dt, vx); vy = fmaf(ay, dt, vy); vz = fmaf(az, dt, vz);
+        } else {
+            lorentz_step<float>(p.field.w_f, ax, ay, az, dt, vx, vy, vz, dx, dy, dz);
+        }
+        ox += dx; oy += dy; oz += dz;
+    }
+
+    // A flight of length dt in p.substeps equal sub-steps (the field at the
+    // start of each), with the first boundary crossing located in FP64
+    // (crossing64) when p.crossing is set.  Returns the boundary status; on
+    // a crossing the FP64 base moves to the crossing point and time.
+    template <int FK>
+    __device__ int fly_steps(const RunParams &p, float dt, float ex, float ey, float ez)
+    {
+        const int ns = p.substeps > 1 ? p.substeps : 1;
+        const float h = ns > 1 ? dt / (float)ns : dt;
+        const unsigned S = blockDim.x;
+        for (int sub = 0; sub < ns; ++sub) {
+            if (sub > 0) field32<FK>(p.field, plate_e, px + ox, py + oy, pz + oz, ex, ey, ez);
+            const float ax = -kAccelF * ex, ay = -kAccelF * ey, az = -kAccelF * ez;
+            const float sox = ox, soy = oy, soz = oz, sot = ot, svx = vx, svy = vy, svz = vz;
+            move(p, ax, ay, az, h);
+            ot += h;
+            int st = boundary<FK>(p);
+            float tc = h;
+            if (FK == GT_FIELD_PLATE && p.crossing && !p.field.has_b && az != 0.0f) {
+                // a sub-step that leaves the gap and returns: the vertex of z(t)
+                const float tv = -svz / az;
+                if (tv > 0.0f && tv < h) {
+                    const float zv = soz + tv * fmaf(0.5f * tv, az, svz);
+                    if (zv >= zhi || zv < zlo) {
+                        const int sv = boundary_confirm64<FK>(b, b + S, b + 2 * S, sox, soy, zv,
+                                                              p.field.gap, 0.0, 0.0, 0.0, 0.0,
+                                                              0.0, 0.0, 0.0, 0.0);
+                        if (sv) {
+                            st = sv;
+                            tc = tv;
+                        }
+                    }
+                }
+            }
+            if (p.crossing && st) {
+                // first crossing within (0, tc], by bisection on the FP32
+                // motion of the offsets (2^-32 of tc: below FP32 resolution);
+                // the point found is on the surface to FP32 rounding
+                const float zg = FK == GT_FIELD_PLATE ? (float)(p.field.gap - b[2 * S]) : 0.0f;
+                const float zc = FK == GT_FIELD_PLATE ? (float)(-b[2 * S]) : 0.0f;
+                float lo = 0.0f, hi = tc;
+                for (int it = 0; it < 32; ++it) {
+                    const float mid = 0.5f * (lo + hi);
+                    ox = sox; oy = soy; oz = soz; vx = svx; vy = svy; vz = svz;
+                    move(p, ax, ay, az, mid);
+                    if (outside32<FK>(p.field, zg, zc, px + ox, py + oy,
+                                      FK == GT_FIELD_PLATE ? oz : pz + oz))
+                        hi = mid;
+                    else
+                        lo = mid;
+                }
+                ox = sox; oy = soy; oz = soz; vx = svx; vy = svy; vz = svz;
+                move(p, ax, ay, az, hi);
+                ot = sot + hi;
+                timed = false;  // the electron left before the time limit
+                const int sc = outside32<FK>(p.field, zg, zc, px + ox, py + oy,
+                                             FK == GT_FIELD_PLATE ? oz : pz + oz);
+                return sc ? sc : st;
+            }
+            if (st) return st;
+        }
+        return 0;
+    }
+
     // One free flight and the real/null decision (Fig. 2 "Find E field and
     // add random time step", "Collision?").  Returns EV_RETIRE or EV_NONE;
-    // fills `pd` (pd.real) for a real collision.
-    template <int FK>
+    // fills `pd` (pd.real) for a real collision.  GEO = true also builds
+    // the sub-steps and exact crossings of fly_steps().
+    template <int FK, bool GEO>
     __device__ __forceinline__ int advance(const RunParams &p, const Tables &tb, Pending &pd)
     {
         pd.real = false;
@@ -1047,7 +1237,8 @@ struct MixedElectron {
             const float eps0 = (vx * vx + vy * vy + vz * vz) * kInvTwoAccelF;
             const float tau = __fdividef(p.window_f, tb.band32[band_index32(p.gas, eps0)]);
             float lo, hi;
-            reach32<FK>(p.field.has_b, eps0, vx, vy, vz, ex, ey, ez, plate_e, tau, lo, hi);
+            reach32<FK>(p.field.has_b, p.field_emax_f, eps0, vx, vy, vz, ex, ey, ez, plate_e, tau,
+                        lo, hi);
             nu = band_range_max(tb.band32, p.gas.n_bands, band_index32(p.gas, lo),
                                 band_index32(p.gas, hi));
             dt = -__fdividef(__logf(u01f(w.x)), nu);
@@ -1063,19 +1254,15 @@ struct MixedElectron {
             dt = c.x;
             timed = c.y != 0.0f;
         }
-        float dx, dy, dz;
-        if (!p.field.has_b) {
-            const float h = 0.5f * dt;
-            dx = dt * fmaf(h, ax, vx);
-            dy = dt * fmaf(h, ay, vy);
-            dz = dt * fmaf(h, az, vz);
-            vx = fmaf(ax, dt, vx); vy = fmaf(ay, dt, vy); vz = fmaf(az, dt, vz);
+        int st;
+        if (GEO && (p.substeps > 1 || p.crossing)) {
+            st = fly_steps<FK>(p, dt, ex, ey, ez);
         } else {
-            lorentz_step<float>(p.field.w_f, ax, ay, az, dt, vx, vy, vz, dx, dy, dz);
+            move(p, ax, ay, az, dt);
+            ot += dt;
+            st = boundary<FK>(p);
         }
-        ox += dx; oy += dy; oz += dz; ot += dt;
         ++nf;
-        const int st = boundary<FK>(p);
         if (st) {
             status = st;
             return EV_RETIRE;
@@ -1187,11 +1374,11 @@ struct MixedElectron {
     }
 
     // Flight and collision in one call (plain mode).
-    template <int FK, bool PHYS = true>
+    template <int FK, bool PHYS = true, bool GEO = true>
     __device__ __forceinline__ int fly(const RunParams &p, const Tables &tb, ChildT &ch)
     {
         Pending pd;
-        const int ev = advance<FK>(p, tb, pd);
+        const int ev = advance<FK, GEO>(p, tb, pd);
         if (ev || !pd.real) return ev;
         return collide<FK, PHYS>(p, tb, pd, ch);
     }

@@ -183,7 +183,8 @@ __device__ __forceinline__ int push_children(const RunParams &p, bool want, cons
     return 0;
 }
 
-template <class E, int FK, bool SMEM_TABLE, int MAXT, int MP = 0, bool PHYS = true>
+template <class E, int FK, bool SMEM_TABLE, int MAXT, int MP = 0, bool PHYS = true,
+          bool GEO = true>
 __global__ void __launch_bounds__(MAXT) k_batched(const RunParams p)
 {
     extern __shared__ __align__(16) unsigned char smem[];
@@ -273,7 +274,7 @@ __global__ void __launch_bounds__(MAXT) k_batched(const RunParams p)
                 for (int mm = 0; mm < M; ++mm) {
                     const bool go = has && !pd.real;
                     if (MP != 1 && !__any_sync(FULL, go)) break;
-                    if (go && (e.template advance<FK>(p, tb, pd) & EV_RETIRE)) {
+                    if (go && (e.template advance<FK, GEO>(p, tb, pd) & EV_RETIRE)) {
                         finish(p, tb, e, bs);
                         has = false;
                         ++retired;
@@ -322,7 +323,7 @@ __global__ void __launch_bounds__(MAXT) k_batched(const RunParams p)
 // One generation of one avalanche (plain mode): every electron of `cur`
 // flies until it ionises (it stays alive and its new electron goes to
 // `fresh`) or finishes (alive = 0).
-template <class E, int FK, bool SMEM_TABLE, int MAXT, bool PHYS = true>
+template <class E, int FK, bool SMEM_TABLE, int MAXT, bool PHYS = true, bool GEO = true>
 __global__ void __launch_bounds__(MAXT)
     k_plain_transport(const RunParams p, const Stack cur, long long n_active, const Stack fresh,
                       int parity, int aval)
@@ -344,7 +345,7 @@ __global__ void __launch_bounds__(MAXT)
     if (e.nf == 0u) ev = e.template check_start<FK>(p);
     unsigned long long k = 0;
     while (ev == EV_NONE) {
-        ev = e.template fly<FK, PHYS>(p, tb, ch);
+        ev = e.template fly<FK, PHYS, GEO>(p, tb, ch);
         if ((++k & 4095ull) == 0ull) {
             if ((long long)(globaltimer() - t_start) > p.time_limit_ns) {
                 atomicOr(&p.hdr->error, ERR_TIMEOUT);

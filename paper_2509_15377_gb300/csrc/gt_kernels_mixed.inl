@@ -1,9 +1,10 @@
 // gt_kernels_mixed.inl -- mixed-precision instantiations of the transport
 // kernels, as templates on PHYS (the general collision with anisotropy,
-// attachment and a sharing law, or the basic gas's collision without
-// their code).  Included by gt_kernels_mixed.cu (PHYS = false) and
-// gt_kernels_mixed_phys.cu (PHYS = true), which instantiate one value each
-// so the two compile in parallel.  The FP32 cumulative table is staged in
+// attachment and a sharing law, or the basic gas's collision without their
+// code) and GEO (flights in sub-steps and exact boundary crossings, or not).
+// Included by gt_kernels_mixed.cu (basic), gt_kernels_mixed_phys.cu (PHYS)
+// and gt_kernels_mixed_geo.cu (PHYS and GEO), which instantiate one variant
+// each so that they compile in parallel.  The FP32 cumulative table is staged in
 // shared memory when it fits next to the per-thread tallies (else read
 // through the read-only path).
 #pragma once
@@ -19,149 +20,149 @@ namespace gt {
 constexpr int kMaxThreadsMixed = 1024;
 constexpr int kPlainThreadsMixed = 512;
 
-template <int FK, bool TAB, int MAXT, bool PHYS>
+template <int FK, bool TAB, int MAXT, bool PHYS, bool GEO>
 static cudaError_t batched_t(const RunParams &p, int grid, int block, size_t smem, cudaStream_t s)
 {
     if (p.flights_per_phase == 1)
-        k_batched<MixedElectron, FK, TAB, MAXT, 1, PHYS><<<grid, block, smem, s>>>(p);
+        k_batched<MixedElectron, FK, TAB, MAXT, 1, PHYS, GEO><<<grid, block, smem, s>>>(p);
     else
-        k_batched<MixedElectron, FK, TAB, MAXT, 0, PHYS><<<grid, block, smem, s>>>(p);
+        k_batched<MixedElectron, FK, TAB, MAXT, 0, PHYS, GEO><<<grid, block, smem, s>>>(p);
     return cudaGetLastError();
 }
 
-template <int FK, bool TAB, bool PHYS>
+template <int FK, bool TAB, bool PHYS, bool GEO>
 static cudaError_t batched(const RunParams &p, int grid, int block, size_t smem, cudaStream_t s)
 {
-    if (block <= 512) return batched_t<FK, TAB, 512, PHYS>(p, grid, block, smem, s);
-    if (block <= 768) return batched_t<FK, TAB, 768, PHYS>(p, grid, block, smem, s);
-    return batched_t<FK, TAB, 1024, PHYS>(p, grid, block, smem, s);
+    if (block <= 512) return batched_t<FK, TAB, 512, PHYS, GEO>(p, grid, block, smem, s);
+    if (block <= 768) return batched_t<FK, TAB, 768, PHYS, GEO>(p, grid, block, smem, s);
+    return batched_t<FK, TAB, 1024, PHYS, GEO>(p, grid, block, smem, s);
 }
 
-template <int FK, bool TAB, bool PHYS>
+template <int FK, bool TAB, bool PHYS, bool GEO>
 static cudaError_t plain(const RunParams &p, const PlainArgs &a, int block, size_t smem,
                          cudaStream_t s)
 {
     const long long n = a.n_active;
     if (n <= 0) return cudaSuccess;
-    k_plain_transport<MixedElectron, FK, TAB, kPlainThreadsMixed, PHYS>
+    k_plain_transport<MixedElectron, FK, TAB, kPlainThreadsMixed, PHYS, GEO>
         <<<(unsigned)((n + block - 1) / block), block, smem, s>>>(p, a.cur, n, a.fresh, a.parity,
                                                                   a.aval);
     return cudaGetLastError();
 }
 
-template <bool TAB, bool PHYS>
+template <bool TAB, bool PHYS, bool GEO>
 static cudaError_t batched_fk(const RunParams &p, int grid, int block, size_t smem, cudaStream_t s)
 {
     switch (p.field.kind) {
-    case GT_FIELD_UNIFORM: return batched<GT_FIELD_UNIFORM, TAB, PHYS>(p, grid, block, smem, s);
-    case GT_FIELD_PLATE: return batched<GT_FIELD_PLATE, TAB, PHYS>(p, grid, block, smem, s);
-    case GT_FIELD_COAX: return batched<GT_FIELD_COAX, TAB, PHYS>(p, grid, block, smem, s);
-    default: return batched<GT_FIELD_GRID, TAB, PHYS>(p, grid, block, smem, s);
+    case GT_FIELD_UNIFORM: return batched<GT_FIELD_UNIFORM, TAB, PHYS, GEO>(p, grid, block, smem, s);
+    case GT_FIELD_PLATE: return batched<GT_FIELD_PLATE, TAB, PHYS, GEO>(p, grid, block, smem, s);
+    case GT_FIELD_COAX: return batched<GT_FIELD_COAX, TAB, PHYS, GEO>(p, grid, block, smem, s);
+    default: return batched<GT_FIELD_GRID, TAB, PHYS, GEO>(p, grid, block, smem, s);
     }
 }
 
-template <bool TAB, bool PHYS>
+template <bool TAB, bool PHYS, bool GEO>
 static cudaError_t plain_fk(const RunParams &p, const PlainArgs &a, int block, size_t smem,
                             cudaStream_t s)
 {
     switch (p.field.kind) {
-    case GT_FIELD_UNIFORM: return plain<GT_FIELD_UNIFORM, TAB, PHYS>(p, a, block, smem, s);
-    case GT_FIELD_PLATE: return plain<GT_FIELD_PLATE, TAB, PHYS>(p, a, block, smem, s);
-    case GT_FIELD_COAX: return plain<GT_FIELD_COAX, TAB, PHYS>(p, a, block, smem, s);
-    default: return plain<GT_FIELD_GRID, TAB, PHYS>(p, a, block, smem, s);
+    case GT_FIELD_UNIFORM: return plain<GT_FIELD_UNIFORM, TAB, PHYS, GEO>(p, a, block, smem, s);
+    case GT_FIELD_PLATE: return plain<GT_FIELD_PLATE, TAB, PHYS, GEO>(p, a, block, smem, s);
+    case GT_FIELD_COAX: return plain<GT_FIELD_COAX, TAB, PHYS, GEO>(p, a, block, smem, s);
+    default: return plain<GT_FIELD_GRID, TAB, PHYS, GEO>(p, a, block, smem, s);
     }
 }
 
-template <bool PHYS>
+template <bool PHYS, bool GEO>
 cudaError_t launch_batched_mixed_t(const RunParams &p, bool smem_table, int grid, int block,
                                    size_t smem, cudaStream_t s)
 {
-    return smem_table ? batched_fk<true, PHYS>(p, grid, block, smem, s)
-                      : batched_fk<false, PHYS>(p, grid, block, smem, s);
+    return smem_table ? batched_fk<true, PHYS, GEO>(p, grid, block, smem, s)
+                      : batched_fk<false, PHYS, GEO>(p, grid, block, smem, s);
 }
 
-template <bool PHYS>
+template <bool PHYS, bool GEO>
 cudaError_t launch_plain_mixed_t(const RunParams &p, const PlainArgs &a, bool smem_table,
                                  int block, size_t smem, cudaStream_t s)
 {
-    return smem_table ? plain_fk<true, PHYS>(p, a, block, smem, s)
-                      : plain_fk<false, PHYS>(p, a, block, smem, s);
+    return smem_table ? plain_fk<true, PHYS, GEO>(p, a, block, smem, s)
+                      : plain_fk<false, PHYS, GEO>(p, a, block, smem, s);
 }
 
-template <int FK, bool TAB, int MP, bool PHYS>
+template <int FK, bool TAB, int MP, bool PHYS, bool GEO>
 static cudaError_t configure_mp(size_t max_smem)
 {
     cudaError_t e;
-    if ((e = allow_dynamic_smem(k_batched<MixedElectron, FK, TAB, 512, MP, PHYS>, max_smem)) !=
+    if ((e = allow_dynamic_smem(k_batched<MixedElectron, FK, TAB, 512, MP, PHYS, GEO>, max_smem)) !=
         cudaSuccess)
         return e;
-    if ((e = allow_dynamic_smem(k_batched<MixedElectron, FK, TAB, 768, MP, PHYS>, max_smem)) !=
+    if ((e = allow_dynamic_smem(k_batched<MixedElectron, FK, TAB, 768, MP, PHYS, GEO>, max_smem)) !=
         cudaSuccess)
         return e;
-    return allow_dynamic_smem(k_batched<MixedElectron, FK, TAB, 1024, MP, PHYS>, max_smem);
+    return allow_dynamic_smem(k_batched<MixedElectron, FK, TAB, 1024, MP, PHYS, GEO>, max_smem);
 }
 
-template <int FK, bool TAB, bool PHYS>
+template <int FK, bool TAB, bool PHYS, bool GEO>
 static cudaError_t configure_one(size_t max_smem)
 {
     cudaError_t e;
-    if ((e = configure_mp<FK, TAB, 0, PHYS>(max_smem)) != cudaSuccess) return e;
-    if ((e = configure_mp<FK, TAB, 1, PHYS>(max_smem)) != cudaSuccess) return e;
-    return allow_dynamic_smem(k_plain_transport<MixedElectron, FK, TAB, kPlainThreadsMixed, PHYS>,
+    if ((e = configure_mp<FK, TAB, 0, PHYS, GEO>(max_smem)) != cudaSuccess) return e;
+    if ((e = configure_mp<FK, TAB, 1, PHYS, GEO>(max_smem)) != cudaSuccess) return e;
+    return allow_dynamic_smem(k_plain_transport<MixedElectron, FK, TAB, kPlainThreadsMixed, PHYS, GEO>,
                               max_smem);
 }
 
-template <bool TAB, bool PHYS>
+template <bool TAB, bool PHYS, bool GEO>
 static cudaError_t configure_tab(size_t max_smem)
 {
     cudaError_t e;
-    if ((e = configure_one<GT_FIELD_UNIFORM, TAB, PHYS>(max_smem)) != cudaSuccess) return e;
-    if ((e = configure_one<GT_FIELD_PLATE, TAB, PHYS>(max_smem)) != cudaSuccess) return e;
-    if ((e = configure_one<GT_FIELD_COAX, TAB, PHYS>(max_smem)) != cudaSuccess) return e;
-    return configure_one<GT_FIELD_GRID, TAB, PHYS>(max_smem);
+    if ((e = configure_one<GT_FIELD_UNIFORM, TAB, PHYS, GEO>(max_smem)) != cudaSuccess) return e;
+    if ((e = configure_one<GT_FIELD_PLATE, TAB, PHYS, GEO>(max_smem)) != cudaSuccess) return e;
+    if ((e = configure_one<GT_FIELD_COAX, TAB, PHYS, GEO>(max_smem)) != cudaSuccess) return e;
+    return configure_one<GT_FIELD_GRID, TAB, PHYS, GEO>(max_smem);
 }
 
-template <bool PHYS>
+template <bool PHYS, bool GEO>
 cudaError_t configure_mixed_t(size_t max_smem)
 {
-    cudaError_t e = configure_tab<true, PHYS>(max_smem);
+    cudaError_t e = configure_tab<true, PHYS, GEO>(max_smem);
     if (e != cudaSuccess) return e;
-    return configure_tab<false, PHYS>(max_smem);
+    return configure_tab<false, PHYS, GEO>(max_smem);
 }
 
-template <int FK, bool TAB, bool PHYS>
+template <int FK, bool TAB, bool PHYS, bool GEO>
 static int occ(int block, size_t smem)
 {
     int n = 0;
     cudaError_t e;
     if (block <= 512)
         e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(
-            &n, k_batched<MixedElectron, FK, TAB, 512, 0, PHYS>, block, smem);
+            &n, k_batched<MixedElectron, FK, TAB, 512, 0, PHYS, GEO>, block, smem);
     else if (block <= 768)
         e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(
-            &n, k_batched<MixedElectron, FK, TAB, 768, 0, PHYS>, block, smem);
+            &n, k_batched<MixedElectron, FK, TAB, 768, 0, PHYS, GEO>, block, smem);
     else
         e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(
-            &n, k_batched<MixedElectron, FK, TAB, 1024, 0, PHYS>, block, smem);
+            &n, k_batched<MixedElectron, FK, TAB, 1024, 0, PHYS, GEO>, block, smem);
     return e == cudaSuccess ? n : 0;
 }
 
-template <bool TAB, bool PHYS>
+template <bool TAB, bool PHYS, bool GEO>
 static int occ_fk(int field_kind, int block, size_t smem)
 {
     switch (field_kind) {
-    case GT_FIELD_UNIFORM: return occ<GT_FIELD_UNIFORM, TAB, PHYS>(block, smem);
-    case GT_FIELD_PLATE: return occ<GT_FIELD_PLATE, TAB, PHYS>(block, smem);
-    case GT_FIELD_COAX: return occ<GT_FIELD_COAX, TAB, PHYS>(block, smem);
-    default: return occ<GT_FIELD_GRID, TAB, PHYS>(block, smem);
+    case GT_FIELD_UNIFORM: return occ<GT_FIELD_UNIFORM, TAB, PHYS, GEO>(block, smem);
+    case GT_FIELD_PLATE: return occ<GT_FIELD_PLATE, TAB, PHYS, GEO>(block, smem);
+    case GT_FIELD_COAX: return occ<GT_FIELD_COAX, TAB, PHYS, GEO>(block, smem);
+    default: return occ<GT_FIELD_GRID, TAB, PHYS, GEO>(block, smem);
     }
 }
 
-template <bool PHYS>
+template <bool PHYS, bool GEO>
 int occupancy_batched_mixed_t(int field_kind, bool smem_table, int block, size_t smem)
 {
-    return smem_table ? occ_fk<true, PHYS>(field_kind, block, smem)
-                      : occ_fk<false, PHYS>(field_kind, block, smem);
+    return smem_table ? occ_fk<true, PHYS, GEO>(field_kind, block, smem)
+                      : occ_fk<false, PHYS, GEO>(field_kind, block, smem);
 }
 
 }  // namespace gt

@@ -54,17 +54,18 @@ cudaError_t launch_plain_fp64(const RunParams &p, const PlainArgs &a, int block,
                               cudaStream_t s);
 cudaError_t launch_plain_mixed(const RunParams &p, const PlainArgs &a, bool smem_table, int block,
                                size_t smem, cudaStream_t s);
-// The mixed launchers above dispatch on the gas: the general collision
-// (PHYS = true) or the basic gas's (gt_kernels_mixed.inl).
-template <bool PHYS>
+// The mixed launchers above dispatch on the gas and the run: the general
+// collision (PHYS) and the sub-steps / crossings (GEO) are separate builds
+// of the kernels (gt_kernels_mixed.inl).
+template <bool PHYS, bool GEO>
 cudaError_t launch_batched_mixed_t(const RunParams &p, bool smem_table, int grid, int block,
                                    size_t smem, cudaStream_t s);
-template <bool PHYS>
+template <bool PHYS, bool GEO>
 cudaError_t launch_plain_mixed_t(const RunParams &p, const PlainArgs &a, bool smem_table,
                                  int block, size_t smem, cudaStream_t s);
-template <bool PHYS>
+template <bool PHYS, bool GEO>
 cudaError_t configure_mixed_t(size_t max_smem);
-template <bool PHYS>
+template <bool PHYS, bool GEO>
 int occupancy_batched_mixed_t(int field_kind, bool smem_table, int block, size_t smem);
 // Raise the dynamic shared-memory limit of every transport instantiation.
 cudaError_t configure_fp64(size_t max_smem);
@@ -81,6 +82,8 @@ cudaError_t launch_plain_init(const RunParams &p, const Stack &st, const long lo
                               long long first, long long count, cudaStream_t s);
 cudaError_t launch_plain_compact(const RunParams &p, const PlainArgs &a, cudaStream_t s);
 cudaError_t launch_count_electrons(const RunParams &p, int sms, cudaStream_t s);
+// Largest |E| over the nodes of a device grid map (synchronous; setup only).
+cudaError_t grid_emax(const float4 *grid, long long n, int sms, double *emax);
 cudaError_t launch_observables(const RunParams &p, long long n_endpoints, int n_avalanches,
                                const int32_t *n_prim, int collect_status, int drift_status,
                                double gap, unsigned long long *scratch_counts,
