@@ -134,6 +134,9 @@ typedef struct {
     int32_t substeps;                /* field evaluations per flight (<= 1: one, held) */
     int32_t crossing;                /* 1: an electron leaving the volume ends at the
                                         first crossing of the boundary */
+    int32_t signal_kind;             /* readout electrode (OR_W_*), 0: no signal */
+    int32_t signal_bins;             /* time bins of the induced signal */
+    double signal_t0, signal_dt;     /* bin j covers [t0 + j dt, t0 + (j+1) dt) */
 } or_run_args;
 
 /* ------------------------------------------------ Philox4x32-10
@@ -364,6 +367,95 @@ static double field_emax(const or_field *f)
         return m;
     }
     return 0.0;
+}
+
+/* ------------------------------------------------ induced signal
+ * Shockley-Ramo: a charge q at r induces -q phi_w(r) on the readout
+ * electrode, phi_w the electrode's weighting potential (1 on the electrode,
+ * 0 on the others).  An electron (q = -e) moving from r_a to r_b therefore
+ * induces phi_w(r_b) - phi_w(r_a) in units of e, whatever its path; the
+ * signal in a time bin is that difference between the electron's positions
+ * at the bin's edges (or its birth and end inside the bin). */
+enum { OR_W_NONE = 0, OR_W_PLATE = 1, OR_W_COAX = 2, OR_W_MAP = 3 };
+
+static double weighting_potential(const or_field *f, int kind, const double r[3])
+{
+    if (kind == OR_W_PLATE) return r[2] / f->gap; /* anode at z = gap */
+    if (kind == OR_W_COAX) {                        /* wire at r = a, tube at r = b */
+        double rr = sqrt(r[0] * r[0] + r[1] * r[1]);
+        return log(rr / f->tube_r) / log(f->wire_r / f->tube_r);
+    }
+    if (kind == OR_W_MAP) { /* trilinear interpolation of the nodes' 4th component */
+        int n[3] = {f->nx, f->ny, f->nz};
+        int idx[3];
+        double w[3];
+        for (int d = 0; d < 3; ++d) {
+            double g = (r[d] - f->origin[d]) / f->spacing[d];
+            int i = (int)floor(g);
+            if (i < 0) i = 0;
+            if (i > n[d] - 2) i = n[d] - 2;
+            idx[d] = i;
+            w[d] = g - i;
+        }
+        double phi = 0.0;
+        for (int c = 0; c < 8; ++c) {
+            int di = c & 1, dj = (c >> 1) & 1, dk = (c >> 2) & 1;
+            double wt = (di ? w[0] : 1.0 - w[0]) * (dj ? w[1] : 1.0 - w[1]) *
+                        (dk ? w[2] : 1.0 - w[2]);
+            const float *p = f->grid + 4 * (((int64_t)(idx[2] + dk) * f->ny + (idx[1] + dj)) *
+                                                f->nx + (idx[0] + di));
+            phi += wt * p[3];
+        }
+        return phi;
+    }
+    return 0.0;
+}
+
+/* Test hook: the weighting potential above. */
+double or_weighting_potential(const or_field *f, int kind, const double r[3])
+{
+    return weighting_potential(f, kind, r);
+}
+
+/* Per-electron signal state: the next bin edge and the potential at the
+ * last edge (or birth). */
+typedef struct {
+    int64_t next;     /* index of the next bin edge t0 + next dt after the current time */
+    double phi_last;
+} or_signal;
+
+static void signal_start(const or_run_args *a, const or_field *f, or_signal *sg, double t,
+                         const double r[3])
+{
+    double x = (t - a->signal_t0) / a->signal_dt;
+    sg->next = x < 0.0 ? 0 : (int64_t)floor(x) + 1;
+    sg->phi_last = sg->next >= 1 ? weighting_potential(f, a->signal_kind, r) : 0.0;
+}
+
+/* A step from (r0, v0) at time ts to te under acc (and rotation w): every
+ * bin edge it passes closes a bin. */
+static void signal_step(const or_run_args *a, const or_field *f, or_signal *sg, double *sig,
+                        const double r0[3], const double v0[3], const double acc[3],
+                        const double w[3], double ts, double te)
+{
+    for (;;) {
+        if (sg->next > a->signal_bins) return;
+        double tb = a->signal_t0 + (double)sg->next * a->signal_dt;
+        if (tb > te) return;
+        double r[3] = {r0[0], r0[1], r0[2]}, v[3] = {v0[0], v0[1], v0[2]};
+        or_flight(r, v, acc, w, tb - ts);
+        double ph = weighting_potential(f, a->signal_kind, r);
+        if (sg->next >= 1) sig[sg->next - 1] += ph - sg->phi_last;
+        sg->phi_last = ph;
+        sg->next += 1;
+    }
+}
+
+static void signal_end(const or_run_args *a, const or_field *f, const or_signal *sg, double *sig,
+                       const double r[3])
+{
+    if (sg->next >= 1 && sg->next <= a->signal_bins)
+        sig[sg->next - 1] += weighting_potential(f, a->signal_kind, r) - sg->phi_last;
 }
 
 /* ------------------------------------------------ rate table */
@@ -599,6 +691,7 @@ typedef struct {
     or_pending *stack;
     int64_t n_st, cap_st;
     uint64_t *tally; /* [L+1] */
+    double *signal;  /* [signal_bins] induced charge per time bin (units of e) */
     int err;
 } or_aval_out;
 
@@ -740,6 +833,9 @@ static void transport_electron(const or_table *tb, const or_field *f, const or_r
     double w[3] = {-OR_OMEGA_PER_T * f->b[0], -OR_OMEGA_PER_T * f->b[1],
                    -OR_OMEGA_PER_T * f->b[2]}; /* electron: q = -e */
     const int has_b = f->b[0] != 0.0 || f->b[1] != 0.0 || f->b[2] != 0.0;
+    const int signal = a->signal_kind != OR_W_NONE && a->signal_bins > 0;
+    or_signal sg;
+    if (signal) signal_start(a, f, &sg, t, r);
     int status = or_boundary(f, r);
     while (status == 0) {
         if (n_flight == 0xFFFFFFFFu) {
@@ -798,16 +894,18 @@ static void transport_electron(const or_table *tb, const or_field *f, const or_r
                 int sv = plate_vertex_exit(f, r0, v0, acc, h, &tc);
                 if (sv) status = sv;
             }
+            double te = sub == ns - 1 ? t_end : t + (sub + 1) * h; /* this step's end */
             if (a->crossing && status) {
                 double hs = first_exit(f, r0, v0, acc, w, tc);
                 r[0] = r0[0]; r[1] = r0[1]; r[2] = r0[2];
                 v[0] = v0[0]; v[1] = v0[1]; v[2] = v0[2];
                 or_flight(r, v, acc, w, hs);
                 status = or_boundary(f, r);
-                t_end = t + sub * h + hs;
+                t_end = te = t + sub * h + hs;
             } else if (status && sub < ns - 1) {
-                t_end = t + (sub + 1) * h;
+                t_end = te;
             }
+            if (signal) signal_step(a, f, &sg, o->signal, r0, v0, acc, w, t + sub * h, te);
             /* work done by the field on the electron (eV): -E . dr */
             work += -(E[0] * (r[0] - r0[0]) + E[1] * (r[1] - r0[1]) + E[2] * (r[2] - r0[2]));
             if (status) break;
@@ -872,6 +970,7 @@ static void transport_electron(const or_table *tb, const or_field *f, const or_r
             break;
         }
     }
+    if (signal) signal_end(a, f, &sg, o->signal, r);
     or_endpoint *e = new_endpoint(o);
     if (!e) {
         o->err = -1;
@@ -905,7 +1004,8 @@ static void run_avalanche(or_job *J, int32_t av)
     const or_run_args *a = J->a;
     double plate_e = a->aval_field ? a->aval_field[av] : J->f->e0;
     o->tally = (uint64_t *)calloc((size_t)J->tb->L + 1, sizeof(uint64_t));
-    if (!o->tally) {
+    o->signal = (double *)calloc((size_t)(a->signal_bins > 0 ? a->signal_bins : 1), sizeof(double));
+    if (!o->tally || !o->signal) {
         o->err = -1;
         return;
     }
@@ -960,6 +1060,13 @@ int or_run(const or_gas *g, const or_field *f, const or_run_args *a, or_result *
     for (int64_t p = 0; p < a->n_primaries; ++p)
         if (a->aval[p] < 0 || a->aval[p] >= a->n_avalanches) return -3;
     if (a->substeps < 0 || a->crossing < 0 || a->crossing > 1) return -3;
+    if (a->signal_kind < OR_W_NONE || a->signal_kind > OR_W_MAP) return -3;
+    if (a->signal_kind != OR_W_NONE &&
+        (a->signal_bins < 0 || !(a->signal_dt > 0.0) || !isfinite(a->signal_t0) ||
+         (a->signal_kind == OR_W_PLATE && f->kind != OR_PLATE) ||
+         (a->signal_kind == OR_W_COAX && f->kind != OR_COAX && f->kind != OR_GRID) ||
+         (a->signal_kind == OR_W_MAP && f->kind != OR_GRID)))
+        return -3;
     or_table tb;
     if (table_build(g, &tb)) return -2;
     tb.field_emax = a->substeps > 1 ? field_emax(f) : 0.0;
@@ -1062,12 +1169,22 @@ int or_result_fetch(const or_result *R, double *x0, double *y0, double *z0, doub
     return 0;
 }
 
+/* Per-avalanche signals, [n_aval][bins]. */
+int or_result_signal(const or_result *R, int32_t bins, double *out)
+{
+    if (!R || bins < 0) return -3;
+    for (int32_t k = 0; k < R->n_aval; ++k)
+        for (int32_t j = 0; j < bins; ++j) out[(int64_t)k * bins + j] = R->out[k].signal[j];
+    return 0;
+}
+
 void or_result_free(or_result *R)
 {
     if (!R) return;
     for (int32_t k = 0; k < R->n_aval; ++k) {
         free(R->out[k].ep);
         free(R->out[k].tally);
+        free(R->out[k].signal);
     }
     free(R->out);
     free(R);

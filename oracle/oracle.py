@@ -24,7 +24,8 @@ _lock = threading.Lock()
 _lib = None
 
 __all__ = ["build", "philox4x32_10", "splitmix64_mix", "child_uid", "flight", "elastic", "field_eval",
-           "boundary", "select", "majorant", "scatter", "ionisation_share", "run",
+           "boundary", "select", "majorant", "scatter", "ionisation_share",
+           "weighting_potential", "run",
            "default_threads"]
 
 
@@ -61,7 +62,9 @@ class _Run(C.Structure):
                 ("aval", C.c_void_p), ("uid", C.c_void_p), ("aval_field", C.c_void_p),
                 ("seed", C.c_uint64), ("t_max", C.c_double), ("coll_limit", C.c_uint32),
                 ("n_threads", C.c_int32), ("majorant", C.c_int32), ("window", C.c_double),
-                ("band_width", C.c_double), ("substeps", C.c_int32), ("crossing", C.c_int32)]
+                ("band_width", C.c_double), ("substeps", C.c_int32), ("crossing", C.c_int32),
+                ("signal_kind", C.c_int32), ("signal_bins", C.c_int32),
+                ("signal_t0", C.c_double), ("signal_dt", C.c_double)]
 
 
 def _load():
@@ -103,6 +106,10 @@ def _load():
             lib.or_result_count.restype = C.c_int64
             lib.or_result_fetch.argtypes = [C.c_void_p] + [C.c_void_p] * 17
             lib.or_result_fetch.restype = C.c_int
+            lib.or_result_signal.argtypes = [C.c_void_p, C.c_int32, C.c_void_p]
+            lib.or_result_signal.restype = C.c_int
+            lib.or_weighting_potential.argtypes = [C.POINTER(_Field), C.c_int, C.c_void_p]
+            lib.or_weighting_potential.restype = C.c_double
             lib.or_result_free.argtypes = [C.c_void_p]
             lib.or_result_free.restype = None
             _lib = lib
@@ -233,6 +240,15 @@ def select(gas, eps: float, u1: float):
     return j, nm.value
 
 
+def weighting_potential(field, kind: int, r) -> float:
+    """Weighting potential of the readout electrode (kind 1 plate anode,
+    2 coax wire, 3 the grid map's 4th component) at r."""
+    keep = []
+    f = _field_struct(field, keep)
+    r = np.ascontiguousarray(r, np.float64)
+    return float(_load().or_weighting_potential(C.byref(f), int(kind), _ptr(r)))
+
+
 def majorant(gas, band_width: float, v, e_field, has_b: bool, window: float):
     """Banded majorant (1/ns) and window tau (ns) of a flight with velocity
     v (cm/ns) in the held field e_field (V/cm); has_b selects the bound for
@@ -252,12 +268,15 @@ def majorant(gas, band_width: float, v, e_field, has_b: bool, window: float):
 # -------------------------------------------------------------------- run
 def run(gas, field, prim, seed: int = 0, t_max: float = 0.0, coll_limit: int = 0,
         n_threads: int | None = None, majorant: int = 0, window: float = 2.0,
-        band_width: float = 1.0, substeps: int = 1, crossing: bool = False) -> dict:
+        band_width: float = 1.0, substeps: int = 1, crossing: bool = False,
+        signal: tuple | None = None) -> dict:
     """Transport every avalanche of `prim` and return a dict of arrays
     (majorant 0: one global nu_max; 1: the banded majorant with flight
     window `window` / band rate and bands of `band_width` eV; `substeps`
     field evaluations per flight; `crossing`: an electron that leaves ends
-    at its first boundary crossing):
+    at its first boundary crossing; `signal` = (electrode kind, bins, t0, dt)
+    for the induced signal per avalanche, out["signal"] [n_avalanches, bins]
+    in units of e):
     x0..e0 (start), x1..e1 (end), status, aval, uid, n_flight, ledger [n, 4]
     (field work, inelastic loss, recoil loss, secondary share; eV),
     electrons [n_avalanches], tallies [n_avalanches, L+1] (real collisions
@@ -292,6 +311,9 @@ def run(gas, field, prim, seed: int = 0, t_max: float = 0.0, coll_limit: int = 0
     ra.band_width = band_width
     ra.substeps = int(substeps)
     ra.crossing = int(bool(crossing))
+    if signal is not None:
+        ra.signal_kind, ra.signal_bins = int(signal[0]), int(signal[1])
+        ra.signal_t0, ra.signal_dt = float(signal[2]), float(signal[3])
     handle = C.c_void_p()
     rc = lib.or_run(C.byref(g), C.byref(f), C.byref(ra), C.byref(handle))
     if rc != 0:
@@ -311,6 +333,9 @@ def run(gas, field, prim, seed: int = 0, t_max: float = 0.0, coll_limit: int = 0
         order = ("x0", "y0", "z0", "t0", "e0", "x1", "y1", "z1", "t1", "e1", "status", "aval",
                  "uid", "n_flight", "ledger", "electrons", "tallies")
         lib.or_result_fetch(handle, *[_ptr(out[k]) for k in order])
+        if signal is not None:
+            out["signal"] = np.zeros((A, int(signal[1])), np.float64)
+            lib.or_result_signal(handle, int(signal[1]), _ptr(out["signal"]))
     finally:
         lib.or_result_free(handle)
     return out

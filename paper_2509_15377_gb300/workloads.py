@@ -31,6 +31,7 @@ STATUS_NAMES = {
     5: "out_of_map", 6: "time", 7: "coll_limit", 8: "flight_limit",
 }
 ANODE, CATHODE, WIRE, TUBE, OUT_OF_MAP, TIME, COLL_LIMIT = 1, 2, 3, 4, 5, 6, 7
+W_NONE, W_PLATE, W_COAX, W_MAP = 0, 1, 2, 3   # readout electrode of induced signals
 FLIGHT_LIMIT, ATTACHED = 8, 9
 
 # Electron mass in unified atomic mass units (CODATA 2018).
@@ -266,7 +267,9 @@ def coax(n_avalanches: int = 2048, wire_r: float = 25e-4, tube_r: float = 0.5,
 def coax_grid_map(n: int = 256, half_width: float = 0.15, length: float = 1.0,
                   wire_r: float = 25e-4, tube_r: float = 0.5, voltage: float = 1500.0) -> Field:
     """A regular n^3 float32 map of the coaxial field on
-    [-w, w]^2 x [0, length]; nodes inside the wire take the field at r = a."""
+    [-w, w]^2 x [0, length]; nodes inside the wire take the field at r = a.
+    The 4th component holds the wire's weighting potential
+    ln(r/b) / ln(a/b) (1 on the wire, 0 on the tube) for induced signals."""
     xs = np.linspace(-half_width, half_width, n)
     zs = np.linspace(0.0, length, n)
     X, Y = np.meshgrid(xs, xs, indexing="xy")          # [ny, nx]
@@ -275,6 +278,7 @@ def coax_grid_map(n: int = 256, half_width: float = 0.15, length: float = 1.0,
     plane = np.zeros((n, n, 4), np.float32)
     plane[..., 0] = s * X
     plane[..., 1] = s * Y
+    plane[..., 3] = np.log(np.sqrt(r2) / tube_r) / math.log(wire_r / tube_r)
     grid = np.broadcast_to(plane, (len(zs), n, n, 4)).astype(np.float32)
     sp = 2.0 * half_width / (n - 1)
     return Field(GRID, wire_r=wire_r, tube_r=tube_r, voltage=voltage, grid=np.ascontiguousarray(grid),

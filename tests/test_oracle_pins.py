@@ -814,3 +814,81 @@ def test_crossing_keeps_the_physics_of_the_plate():
     led = b["ledger"]
     assert np.allclose(b["e1"], b["e0"] + led[:, 0] - led[:, 1] - led[:, 2] - led[:, 3],
                        rtol=1e-9, atol=1e-9)
+
+
+# --------------------------------------------------------- induced signals
+def test_signal_telescopes_to_the_weighting_potential():
+    """Shockley-Ramo: summed over a window that covers every electron's life,
+    an avalanche's signal equals the sum over its electrons of
+    phi_w(end) - phi_w(start) (phi_w = z / d for the plate anode): no piece
+    of any path is lost or counted twice, with or without crossings and
+    sub-steps."""
+    n = 40
+    w = W.plate(n_avalanches=n, e_field=40_000.0, seed=91)
+    for kw in (dict(), dict(crossing=True, substeps=3)):
+        o = oracle.run(w.gas, w.field, w.primaries, seed=91, t_max=w.t_max,
+                       signal=(W.W_PLATE, 400, 0.0, 0.005), **kw)
+        per_e = (o["z1"] - o["z0"]) / w.field.gap
+        expect = np.bincount(o["aval"], weights=per_e, minlength=n)
+        assert np.allclose(o["signal"].sum(axis=1), expect, rtol=1e-12, atol=1e-12)
+
+
+def test_signal_bins_of_a_uniform_acceleration():
+    """Collisionless plate electrons released at t_r inside a bin: in bin
+    [b_k, b_k+1) the signal is (z(b_k+1) - z(b_k)) / d with
+    z(t) = vz (t - t_r) + a (t - t_r)^2 / 2, counted from the release in its
+    own bin and up to the arrival at the anode (crossing mode), where it is
+    (d - z(b_k)) / d; the bin before the release holds nothing."""
+    w = _collisionless(50, 30_000.0, 93)
+    a = P.ACCEL_PER_VCM * 30_000.0
+    vz = w.primaries.dz * np.sqrt(P.speed_sq(w.primaries.e))
+    tr = 0.0052  # released inside the first bin [0.004, 0.007)
+    w.primaries.t[:] = tr
+    ts = tr + (np.sqrt(vz * vz + 2 * a * w.field.gap) - vz) / a
+    t0, dt, nb = 0.001, 0.003, 9
+    o = oracle.run(w.gas, w.field, w.primaries, seed=93, t_max=100.0, crossing=True,
+                   signal=(W.W_PLATE, nb, t0, dt))
+    edges = t0 + dt * np.arange(nb + 1)
+    for i in range(50):
+        te = np.clip(edges, tr, ts[i]) - tr
+        z = np.where(edges < ts[i], vz[i] * te + 0.5 * a * te * te, w.field.gap)
+        expect = np.diff(z) / w.field.gap
+        # (atol: e/m is quoted to 12 digits, the test derives it from e and m_e)
+        assert np.allclose(o["signal"][i], expect, rtol=1e-9, atol=1e-10), i
+
+
+def test_signal_drift_current_closed_form():
+    """Constant rate nu in a uniform field, far from the electrodes: each
+    electron carries the mean current e v_d / d, so after the first
+    collisions a bin of width dt holds v_d dt / d per electron (3 sigma)."""
+    n, nu, e_field, gap = 20000, 1000.0, 1000.0, 100.0
+    w = W.drift_model(n_electrons=n, n_coll=0, e_field=e_field, seed=95)
+    w.field = W.Field(W.PLATE, e0=e_field, gap=gap)
+    w.primaries.z[:] = 1.0
+    dt, nb = 0.5, 10
+    o = oracle.run(w.gas, w.field, w.primaries, seed=95, t_max=nb * dt,
+                   signal=(W.W_PLATE, nb, 0.0, dt))
+    s = o["signal"][:, 1:]  # per electron (one per avalanche), bins after the transient
+    vd = P.drift_velocity(e_field, nu)
+    assert np.all(o["status"] == W.TIME)
+    for k in range(s.shape[1]):
+        assert P.within_sigma(s[:, k].mean(), vd * dt / gap, s[:, k].std() / math.sqrt(n))
+
+
+def test_signal_of_a_fall_onto_the_wire():
+    """Collisionless fall onto the coax wire (crossing mode): every
+    electron induces 1 - phi_w(r0) on the wire, phi_w = ln(r/b) / ln(a/b);
+    the grid map's 4th component gives the same within its interpolation."""
+    w = W.coax(n_avalanches=60, r_lo=0.004, r_hi=0.02, b_axial=0.0, seed=97)
+    w.gas = W.model_gas(1e-9)
+    o = oracle.run(w.gas, w.field, w.primaries, seed=97, t_max=0.05, substeps=256,
+                   crossing=True, signal=(W.W_COAX, 5, 0.0, 0.01))
+    r0 = np.hypot(o["x0"], o["y0"])
+    phi0 = np.log(r0 / w.field.tube_r) / math.log(w.field.wire_r / w.field.tube_r)
+    assert np.all(o["status"] == W.WIRE)
+    assert np.allclose(o["signal"].sum(axis=1), 1.0 - phi0, rtol=1e-9)
+    f = W.coax_grid_map(n=64, half_width=0.03, length=0.05)
+    for r in ([0.004, 0.0, 0.02], [0.01, 0.013, 0.03], [-0.02, 0.005, 0.001]):
+        rr = math.hypot(r[0], r[1])
+        exact = math.log(rr / f.tube_r) / math.log(f.wire_r / f.tube_r)
+        assert abs(oracle.weighting_potential(f, W.W_MAP, r) - exact) < 2e-3
