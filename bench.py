@@ -320,6 +320,18 @@ def run_ours(args) -> None:
             c_ms += c_st["transport_ms"]
         physical["crossing"] = {"value_kernel_time": c_real / (c_ms / 1e3), "unit": UNIT,
                                 "note": "basic gas, endpoints at the first boundary crossing"}
+        # the basic gas with the anode's induced signal, 2000 bins of 50 ps
+        s_opt = dataclasses.replace(opt, signal_kind=W.W_PLATE, signal_bins=2000,
+                                    signal_t0=0.0, signal_dt=0.05)
+        s_real, s_ms = 0, 0.0
+        for _ in range(2):
+            flush.fill_(1)
+            s_st = av.run(prim_dev, s_opt, cap, stream=stream, allow=(A.GT_OK,))
+            s_real += s_st["real_collisions"]
+            s_ms += s_st["transport_ms"]
+        physical["signal"] = {"value_kernel_time": s_real / (s_ms / 1e3), "unit": UNIT,
+                              "note": "basic gas, Shockley-Ramo anode signal per avalanche, "
+                                      "2000 bins x 0.05 ns"}
 
     # plain FP64 GPU path (the paper's structure: one avalanche at a time, one
     # launch per generation) on a sample, with both majorants

@@ -195,7 +195,24 @@ typedef struct {
                                          (sub-)step (to 2^-60 of it); for the plate
                                          without B a step that leaves and returns
                                          is caught at the vertex of z(t) */
+    /* Induced signal (Shockley-Ramo theorem): with signal_kind != GT_W_NONE
+     * and signal_bins > 0, out->signal[a][j] receives the charge (in units
+     * of e) that the electrons of avalanche a induce on the readout electrode
+     * during [signal_t0 + j signal_dt, signal_t0 + (j+1) signal_dt): for each
+     * electron the change of the electrode's weighting potential phi_w
+     * between its positions at the bin's edges (or its birth and end inside
+     * the bin).  Positive when electrons move towards the electrode. */
+    int32_t signal_kind;              /* GT_W_* */
+    int32_t signal_bins;
+    double signal_t0;                 /* ns */
+    double signal_dt;                 /* ns, > 0 */
 } gt_run;
+
+/* Readout electrodes for induced signals (their weighting potentials). */
+#define GT_W_NONE 0
+#define GT_W_PLATE 1 /* PLATE anode: phi_w = z / gap */
+#define GT_W_COAX 2  /* COAX (or GRID) wire: phi_w = ln(r / tube_r) / ln(wire_r / tube_r) */
+#define GT_W_MAP 3   /* GRID: trilinear interpolation of the map's 4th component */
 
 /* Majorant of the null-collision flights.
  * GLOBAL: dt = -ln(u)/nu_max with one nu_max for all energies (Skullerud).
@@ -234,6 +251,9 @@ typedef struct {
     uint64_t *electrons;              /* [n_avalanches] electrons stored */
     uint64_t *tallies;                /* [n_avalanches][n_levels + 1] real
                                          collisions per level, then null ones */
+    double *signal;                   /* [n_avalanches][signal_bins] induced charge
+                                         (set to 0 by the run), or NULL without
+                                         a signal */
 } gt_endpoints;
 
 /* ---- run summary (host, filled by avalanche_run) ---------------------- */

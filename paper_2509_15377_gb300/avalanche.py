@@ -68,7 +68,8 @@ class gt_run(C.Structure):
                 ("time_limit_ms", C.c_double), ("debug_flags", C.c_int32),
                 ("flights_per_phase", C.c_int32), ("majorant", C.c_int32), ("pad", C.c_int32),
                 ("majorant_window", C.c_double), ("substeps", C.c_int32),
-                ("crossing", C.c_int32)]
+                ("crossing", C.c_int32), ("signal_kind", C.c_int32), ("signal_bins", C.c_int32),
+                ("signal_t0", C.c_double), ("signal_dt", C.c_double)]
 
 
 _EP_ARRAYS = ("x0", "y0", "z0", "t0", "e0", "x1", "y1", "z1", "t1", "e1", "status", "aval",
@@ -77,7 +78,7 @@ _EP_ARRAYS = ("x0", "y0", "z0", "t0", "e0", "x1", "y1", "z1", "t1", "e1", "statu
 
 class gt_endpoints(C.Structure):
     _fields_ = [("capacity", C.c_int64)] + [(k, C.c_void_p) for k in _EP_ARRAYS] + \
-               [("electrons", C.c_void_p), ("tallies", C.c_void_p)]
+               [("electrons", C.c_void_p), ("tallies", C.c_void_p), ("signal", C.c_void_p)]
 
 
 class gt_stats(C.Structure):
@@ -285,6 +286,10 @@ class RunOptions:
     debug_flags: int = 0
     substeps: int = 0          # field evaluations per flight (<= 1: held field)
     crossing: int = 0          # 1: leaving electrons end at the first crossing
+    signal_kind: int = 0       # readout electrode for induced signals (workloads.W_*)
+    signal_bins: int = 0
+    signal_t0: float = 0.0
+    signal_dt: float = 0.0
 
 
 class Avalanche:
@@ -341,7 +346,8 @@ class Avalanche:
         dev = f"cuda:{self.device}"
         L = self.gas.n_levels
         f64, i32 = torch.float64, torch.int32
-        need = dict(capacity=capacity, n_avalanches=n_avalanches, L=L)
+        bins = run.signal_bins if run.signal_kind else 0
+        need = dict(capacity=capacity, n_avalanches=n_avalanches, L=L, bins=bins)
         if self.ep is None or self.ep["_need"] != need:
             ep = {k: torch.empty(capacity, dtype=f64, device=dev)
                   for k in ("x0", "y0", "z0", "t0", "e0", "x1", "y1", "z1", "t1", "e1")}
@@ -351,6 +357,8 @@ class Avalanche:
             ep["n_flight"] = torch.empty(capacity, dtype=i32, device=dev)
             ep["electrons"] = torch.empty(max(n_avalanches, 1), dtype=torch.int64, device=dev)
             ep["tallies"] = torch.empty((max(n_avalanches, 1), L + 1), dtype=torch.int64, device=dev)
+            ep["signal"] = (torch.empty((max(n_avalanches, 1), bins), dtype=f64, device=dev)
+                            if bins else None)
             ep["_need"] = need
             self.ep = ep
         nbytes = workspace_bytes(self.ctx, run, capacity)
@@ -365,6 +373,7 @@ class Avalanche:
             setattr(o, k, self.ep[k].data_ptr())
         o.electrons = self.ep["electrons"].data_ptr()
         o.tallies = self.ep["tallies"].data_ptr()
+        o.signal = self.ep["signal"].data_ptr() if self.ep.get("signal") is not None else None
         return o
 
     def primaries_device(self, prim: W.Primaries) -> dict:
@@ -421,6 +430,10 @@ class Avalanche:
         r.debug_flags = opt.debug_flags
         r.substeps = opt.substeps
         r.crossing = opt.crossing
+        r.signal_kind = opt.signal_kind
+        r.signal_bins = opt.signal_bins
+        r.signal_t0 = opt.signal_t0
+        r.signal_dt = opt.signal_dt
         return r
 
     def run(self, prim: dict, opt: RunOptions, capacity: int, stream=None,
@@ -456,6 +469,8 @@ class Avalanche:
             out[k] = a
         out["electrons"] = self.ep["electrons"].cpu().numpy().view(np.uint64)
         out["tallies"] = self.ep["tallies"].cpu().numpy().view(np.uint64)
+        if self.ep.get("signal") is not None:
+            out["signal"] = self.ep["signal"].cpu().numpy()
         return out
 
     def observables(self, n_endpoints: int, prim: W.Primaries, collect_status: int,

@@ -381,6 +381,7 @@ int field_setup(gt_ctx *ctx, const gt_field *f)
     case GT_FIELD_PLATE:
         if (!std::isfinite(f->e0) || !finite_pos(f->gap)) return GT_ERR_ARG;
         d.gap = f->gap;
+        d.inv_gap = 1.0 / f->gap;
         break;
     case GT_FIELD_COAX:
         if (!finite_pos(f->wire_r) || !finite_pos(f->tube_r) || f->tube_r <= f->wire_r ||
@@ -390,6 +391,8 @@ int field_setup(gt_ctx *ctx, const gt_field *f)
         d.tube_r2 = f->tube_r * f->tube_r;
         d.coax_k = f->voltage / std::log(f->tube_r / f->wire_r);
         d.emax = std::fabs(d.coax_k) / f->wire_r;
+        d.ln_tube = std::log(f->tube_r);
+        d.inv_ln_ab = 1.0 / std::log(f->wire_r / f->tube_r);
         break;
     case GT_FIELD_GRID:
         if (f->nx < 2 || f->ny < 2 || f->nz < 2 || f->nx > (1 << 22) || f->ny > (1 << 22) ||
@@ -407,6 +410,10 @@ int field_setup(gt_ctx *ctx, const gt_field *f)
         d.hi[2] = f->origin[2] + (f->nz - 1) * f->spacing[2];
         d.wire_r2 = f->wire_r * f->wire_r;
         d.grid = reinterpret_cast<const float4 *>(f->grid);
+        if (f->wire_r > 0.0 && f->tube_r > f->wire_r) {
+            d.ln_tube = std::log(f->tube_r);
+            d.inv_ln_ab = 1.0 / std::log(f->wire_r / f->tube_r);
+        }
         {
             DeviceGuard dg(ctx->device);
             if (!dg.ok) return GT_ERR_CUDA;
@@ -463,6 +470,18 @@ static int validate_run(gt_ctx *ctx, const gt_run *r, const gt_endpoints *o, voi
         !(r->majorant_window >= 0.0) || !std::isfinite(r->majorant_window) ||
         r->substeps < 0 || r->substeps > 4096 || (r->crossing != 0 && r->crossing != 1))
         return GT_ERR_ARG;
+    if (r->signal_kind < GT_W_NONE || r->signal_kind > GT_W_MAP) return GT_ERR_ARG;
+    if (r->signal_kind != GT_W_NONE) {
+        const int k = ctx->field.kind;
+        if (r->signal_bins < 0 || !(r->signal_dt > 0.0) || !std::isfinite(r->signal_dt) ||
+            !std::isfinite(r->signal_t0) ||
+            (r->signal_kind == GT_W_PLATE && k != GT_FIELD_PLATE) ||
+            (r->signal_kind == GT_W_COAX && k != GT_FIELD_COAX && k != GT_FIELD_GRID) ||
+            (r->signal_kind == GT_W_MAP && k != GT_FIELD_GRID))
+            return GT_ERR_ARG;
+        if (r->signal_bins > 0 && r->n_avalanches > 0 && !o->signal) return GT_ERR_ARG;
+        if (r->signal_kind == GT_W_COAX && ctx->field.inv_ln_ab == 0.0) return GT_ERR_ARG;
+    }
     if (r->block && (r->block % 32 != 0 ||
                      r->block > (r->precision == GT_FP64 ? max_block_fp64() : max_block_mixed())))
         return GT_ERR_ARG;
@@ -551,6 +570,12 @@ int avalanche_run(gt_ctx *ctx, const gt_run *r, const gt_endpoints *o, void *ws,
     // field of the volume (uniform and plate fields do not change)
     p.field_emax = p.substeps > 1 ? ctx->field.emax : 0.0;
     p.field_emax_f = (float)(p.field_emax * (1.0 + 1e-6));
+    p.signal_kind = r->signal_bins > 0 ? r->signal_kind : GT_W_NONE;
+    p.signal_bins = p.signal_kind != GT_W_NONE ? r->signal_bins : 0;
+    p.signal_t0 = r->signal_t0;
+    p.signal_dt = r->signal_dt;
+    p.signal_inv_dt = p.signal_bins ? 1.0 / r->signal_dt : 0.0;
+    p.signal = p.signal_bins ? o->signal : nullptr;
     p.size_limit = r->size_limit;
     p.spin_limit_ns = (long long)((r->spin_limit_ms > 0 ? r->spin_limit_ms : 60000.0) * 1e6);
     p.time_limit_ns = (long long)((r->time_limit_ms > 0 ? r->time_limit_ms : 600000.0) * 1e6);
@@ -598,6 +623,9 @@ int avalanche_run(gt_ctx *ctx, const gt_run *r, const gt_endpoints *o, void *ws,
         GT_CUDA(ctx, cudaMemsetAsync(p.ready, 0, sizeof(uint32_t) * (size_t)o->capacity, s));
     if (na > 0) {
         GT_CUDA(ctx, cudaMemsetAsync(o->tallies, 0, sizeof(uint64_t) * (size_t)na * (L + 1), s));
+        if (p.signal_bins)
+            GT_CUDA(ctx, cudaMemsetAsync(o->signal, 0,
+                                         sizeof(double) * (size_t)na * (size_t)p.signal_bins, s));
         GT_CUDA(ctx, cudaMemsetAsync(o->electrons, 0, sizeof(uint64_t) * (size_t)na, s));
         if (r->size_limit)
             GT_CUDA(ctx, cudaMemsetAsync(p.created, 0, sizeof(unsigned long long) * (size_t)na, s));

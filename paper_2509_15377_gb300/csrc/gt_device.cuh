@@ -75,6 +75,8 @@ struct DevField {
     float box_lo_f[3], box_hi_f[3];      // map-box pre-test limits (inside by 1e-5)
     float cell_hi_f[3], node_hi_f[3];    // n - 2 and n - 1 per axis
     double emax;                         // largest |E| of the volume (COAX, GRID; else 0)
+    double inv_gap;                      // PLATE: 1 / gap (anode weighting potential)
+    double ln_tube, inv_ln_ab;           // COAX/GRID wire: ln b, 1 / ln(a/b)
 };
 
 struct Header {  // at the start of the work space, 256 bytes
@@ -131,6 +133,10 @@ struct RunParams {
     float window_f;
     int substeps;           // field evaluations per flight (1: held field)
     int crossing;           // 1: leaving electrons end at the first crossing
+    int signal_kind;        // readout electrode (GT_W_*), GT_W_NONE: no signal
+    int signal_bins;
+    double signal_t0, signal_dt, signal_inv_dt;
+    double *signal;         // [n_avalanches][signal_bins]
     double field_emax;      // > 0: bound |E| by this in the banded majorant
     float field_emax_f;
     uint64_t size_limit;
@@ -741,6 +747,57 @@ __device__ __forceinline__ int outside32(const DevField &f, float zg, float zc, 
     return 0;
 }
 
+// --------------------------------------------------- induced signal
+// Shockley-Ramo: an electron moving from r_a to r_b induces
+// phi_w(r_b) - phi_w(r_a) (units of e) on the readout electrode, phi_w its
+// weighting potential; the signal of a time bin is that difference between
+// the electron's positions at the bin's edges (or its birth and end).
+__device__ __forceinline__ double weighting64(const RunParams &p, double x, double y, double z)
+{
+    const DevField &f = p.field;
+    if (p.signal_kind == GT_W_PLATE) return z * f.inv_gap;
+    if (p.signal_kind == GT_W_COAX) return (0.5 * log(x * x + y * y) - f.ln_tube) * f.inv_ln_ab;
+    // GT_W_MAP: trilinear interpolation of the nodes' 4th component
+    const double q[3] = {x, y, z};
+    const int n[3] = {f.nx, f.ny, f.nz};
+    int i[3];
+    double w[3];
+#pragma unroll
+    for (int d = 0; d < 3; ++d) {
+        const double g = (q[d] - f.origin[d]) * f.inv_spacing[d];
+        int k = (int)floor(g);
+        k = k < 0 ? 0 : (k > n[d] - 2 ? n[d] - 2 : k);
+        i[d] = k;
+        w[d] = g - k;
+    }
+    double phi = 0.0;
+#pragma unroll
+    for (int c = 0; c < 8; ++c) {
+        const int di = c & 1, dj = (c >> 1) & 1, dk = (c >> 2) & 1;
+        const double wt = (di ? w[0] : 1.0 - w[0]) * (dj ? w[1] : 1.0 - w[1]) *
+                          (dk ? w[2] : 1.0 - w[2]);
+        const float4 e = __ldg(f.grid + (((int64_t)(i[2] + dk) * f.ny + (i[1] + dj)) * f.nx +
+                                         (i[0] + di)));
+        phi += wt * (double)e.w;
+    }
+    return phi;
+}
+
+// Index of the first bin edge t0 + j dt after time t (0 before the window).
+__device__ __forceinline__ int signal_next(const RunParams &p, double t)
+{
+    const double x = (t - p.signal_t0) / p.signal_dt;
+    if (!(x >= 0.0)) return 0;
+    return x >= (double)p.signal_bins ? p.signal_bins + 1 : (int)floor(x) + 1;
+}
+
+// Adds phi_b - phi_last to bin `next - 1` (if any) of avalanche `aval`.
+__device__ __forceinline__ void signal_add(const RunParams &p, int aval, int next, double d)
+{
+    if (next >= 1 && next <= p.signal_bins)
+        atomicAdd(p.signal + (int64_t)aval * p.signal_bins + (next - 1), d);
+}
+
 // ============================================================ FP64 electron
 struct Fp64Electron {
     static constexpr bool kTwoPhase = false;
@@ -760,6 +817,40 @@ struct Fp64Electron {
     int aval;
     uint64_t uid;
     int64_t slot;
+    int sg_next;       // induced signal: next bin edge
+    double sg_phi;     // weighting potential at the last edge (or birth)
+
+    __device__ __forceinline__ void signal_start(const RunParams &p)
+    {
+        if (!p.signal_bins) return;
+        sg_next = signal_next(p, t);
+        sg_phi = sg_next >= 1 ? weighting64(p, x, y, z) : 0.0;
+    }
+
+    // Bin edges passed by the step from (x0.., v0..) at ts to te.
+    __device__ void signal_step(const RunParams &p, double x0, double y0, double z0, double vx0,
+                                double vy0, double vz0, double ax, double ay, double az,
+                                double ts, double te)
+    {
+        while (sg_next <= p.signal_bins) {
+            const double tb = p.signal_t0 + (double)sg_next * p.signal_dt;
+            if (tb > te) return;
+            const double sx = x, sy = y, sz = z, svx = vx, svy = vy, svz = vz;
+            x = x0; y = y0; z = z0; vx = vx0; vy = vy0; vz = vz0;
+            move(p, ax, ay, az, tb - ts);
+            const double ph = weighting64(p, x, y, z);
+            x = sx; y = sy; z = sz; vx = svx; vy = svy; vz = svz;
+            signal_add(p, aval, sg_next, ph - sg_phi);
+            sg_phi = ph;
+            ++sg_next;
+        }
+    }
+
+    // The electron ends (or is parked): the part of its current bin.
+    __device__ __forceinline__ void signal_end(const RunParams &p) const
+    {
+        if (p.signal_bins) signal_add(p, aval, sg_next, weighting64(p, x, y, z) - sg_phi);
+    }
 
     __device__ __forceinline__ void position(const RunParams &, double &ox_, double &oy_,
                                              double &oz_, double &ot_) const
@@ -767,7 +858,7 @@ struct Fp64Electron {
         ox_ = x; oy_ = y; oz_ = z; ot_ = t;
     }
 
-    template <int FK>
+    template <int FK, bool GEO = true>
     __device__ void load_birth(const RunParams &p, int64_t s)
     {
         slot = s;
@@ -778,6 +869,7 @@ struct Fp64Electron {
         plate_e = p.aval_field ? p.aval_field[aval] : p.field.e0;
         nf = nreal = nnull = 0;
         status = 0;
+        if (GEO) signal_start(p);
     }
 
     template <int FK>
@@ -835,6 +927,7 @@ struct Fp64Electron {
                     }
                 }
             }
+            const double te = sub == ns - 1 ? t_end : t + (sub + 1) * h;  // this step's end
             if (p.crossing && st) {
                 double lo = 0.0, hi = tc;
                 for (int it = 0; it < 60; ++it) {
@@ -849,10 +942,14 @@ struct Fp64Electron {
                 x = x0; y = y0; z = z0; vx = vx0; vy = vy0; vz = vz0;
                 move(p, ax, ay, az, hi);
                 t_end = t + sub * h + hi;
+                if (p.signal_bins)
+                    signal_step(p, x0, y0, z0, vx0, vy0, vz0, ax, ay, az, t + sub * h, t_end);
                 return boundary64<FK>(p.field, x, y, z);
             }
+            if (p.signal_bins)
+                signal_step(p, x0, y0, z0, vx0, vy0, vz0, ax, ay, az, t + sub * h, te);
             if (st) {
-                if (sub < ns - 1) t_end = t + (sub + 1) * h;
+                if (sub < ns - 1) t_end = te;
                 return st;
             }
         }
@@ -899,7 +996,7 @@ struct Fp64Electron {
         }
         double t_end = timed ? p.t_max : t + dt;
         int st;
-        if (p.substeps > 1 || p.crossing) {
+        if (p.substeps > 1 || p.crossing || p.signal_bins) {
             st = fly_steps<FK>(p, dt, ex, ey, ez, t_end);
         } else {
             move(p, ax, ay, az, dt);
@@ -978,15 +1075,16 @@ struct Fp64Electron {
         p.nflight[slot] = nf;
     }
 
-    template <int FK>
-    __device__ void save(const RunParams &, const Stack &s, int64_t i)
+    template <int FK, bool GEO = true>
+    __device__ void save(const RunParams &p, const Stack &s, int64_t i)
     {
+        if (GEO) signal_end(p);  // the part so far; restore() starts again from here
         s.x[i] = x; s.y[i] = y; s.z[i] = z; s.t[i] = t;
         s.vx[i] = vx; s.vy[i] = vy; s.vz[i] = vz;
         s.nf[i] = nf; s.nreal[i] = nreal; s.uid[i] = uid; s.slot[i] = slot;
     }
 
-    template <int FK>
+    template <int FK, bool GEO = true>
     __device__ void restore(const RunParams &p, const Stack &s, int64_t i, int av)
     {
         x = s.x[i]; y = s.y[i]; z = s.z[i]; t = s.t[i];
@@ -996,6 +1094,7 @@ struct Fp64Electron {
         plate_e = p.aval_field ? p.aval_field[aval] : p.field.e0;
         nnull = 0;
         status = 0;
+        if (GEO) signal_start(p);
     }
 };
 
@@ -1037,8 +1136,73 @@ struct MixedElectron {
     bool timed;
     uint64_t uid;
     int64_t slot;
+    int sg_next;             // induced signal: next bin edge
+    double sg_phi;           // weighting potential at the last edge (or birth)
+    float sg_toff;           // time offset of the next edge (slightly early)
 
     __device__ __forceinline__ void bind(const Tables &tb) { b = tb.base + threadIdx.x; }
+
+    // FP32 offset time at which the next bin edge may come (an FP32
+    // pre-test; the edge itself is placed in FP64).
+    __device__ __forceinline__ void signal_limit(const RunParams &p)
+    {
+        if (!p.signal_bins || sg_next > p.signal_bins) {
+            sg_toff = 3.0e38f;
+            return;
+        }
+        const float g = (float)(p.signal_t0 + (double)sg_next * p.signal_dt - b[3 * blockDim.x]);
+        sg_toff = g - (fabsf(g) * 1e-6f + 1e-12f);
+    }
+
+    __device__ __forceinline__ void signal_start(const RunParams &p)
+    {
+        if (!p.signal_bins) return;
+        double x, y, z, t;
+        position(p, x, y, z, t);
+        sg_next = signal_next(p, t);
+        sg_phi = sg_next >= 1 ? weighting64(p, x, y, z) : 0.0;
+        signal_limit(p);
+    }
+
+    // Bin edges passed by the step that started at offsets (so.., sot) with
+    // velocity sv and acceleration a and ended now (at t_max if `at_tmax`).
+    __device__ void signal_step(const RunParams &p, float sox, float soy, float soz, float sot,
+                                float svx, float svy, float svz, float ax, float ay, float az,
+                                bool at_tmax)
+    {
+        const unsigned S = blockDim.x;
+        const double ts = b[3 * S] + (double)sot;
+        const double te = at_tmax ? p.t_max : b[3 * S] + (double)ot;
+        while (sg_next <= p.signal_bins) {
+            const double tb = p.signal_t0 + (double)sg_next * p.signal_dt;
+            if (tb > te) break;
+            const float h = (float)(tb - ts);
+            float dx, dy, dz;
+            if (!p.field.has_b) {
+                dx = h * fmaf(0.5f * h, ax, svx);
+                dy = h * fmaf(0.5f * h, ay, svy);
+                dz = h * fmaf(0.5f * h, az, svz);
+            } else {
+                float wx = svx, wy = svy, wz = svz;
+                lorentz_step<float>(p.field.w_f, ax, ay, az, h, wx, wy, wz, dx, dy, dz);
+            }
+            const double ph = weighting64(p, b[0] + (double)(sox + dx), b[S] + (double)(soy + dy),
+                                          b[2 * S] + (double)(soz + dz));
+            signal_add(p, aval, sg_next, ph - sg_phi);
+            sg_phi = ph;
+            ++sg_next;
+        }
+        signal_limit(p);
+    }
+
+    // The electron ends (or is parked): the part of its current bin.
+    __device__ __forceinline__ void signal_end(const RunParams &p) const
+    {
+        if (!p.signal_bins) return;
+        double x, y, z, t;
+        position(p, x, y, z, t);
+        signal_add(p, aval, sg_next, weighting64(p, x, y, z) - sg_phi);
+    }
 
     __device__ __forceinline__ void position(const RunParams &, double &x_, double &y_,
                                              double &z_, double &t_) const
@@ -1056,6 +1220,7 @@ struct MixedElectron {
         const unsigned S = blockDim.x;
         set_base<FK>(p, b[0] + (double)ox, b[S] + (double)oy, b[2 * S] + (double)oz,
                      b[3 * S] + (double)ot);
+        if (p.signal_bins) signal_limit(p);
     }
 
     // New FP64 base (X, Y, Z, T) with zero offsets, and the pre-test limits.
@@ -1083,7 +1248,7 @@ struct MixedElectron {
         }
     }
 
-    template <int FK>
+    template <int FK, bool GEO = true>
     __device__ void load_birth(const RunParams &p, int64_t s)
     {
         slot = s;
@@ -1095,6 +1260,7 @@ struct MixedElectron {
         status = 0;
         timed = false;
         set_base<FK>(p, p.x0[s], p.y0[s], p.z0[s], p.t0[s]);
+        if (GEO) signal_start(p);
     }
 
     template <int FK>
@@ -1157,6 +1323,7 @@ struct MixedElectron {
     template <int FK>
     __device__ int fly_steps(const RunParams &p, float dt, float ex, float ey, float ez)
     {
+        const bool sig = p.signal_bins != 0;
         const int ns = p.substeps > 1 ? p.substeps : 1;
         const float h = ns > 1 ? dt / (float)ns : dt;
         const unsigned S = blockDim.x;
@@ -1205,10 +1372,15 @@ struct MixedElectron {
                 move(p, ax, ay, az, hi);
                 ot = sot + hi;
                 timed = false;  // the electron left before the time limit
+                if (sig && ot >= sg_toff)
+                    signal_step(p, sox, soy, soz, sot, svx, svy, svz, ax, ay, az, false);
                 const int sc = outside32<FK>(p.field, zg, zc, px + ox, py + oy,
                                              FK == GT_FIELD_PLATE ? oz : pz + oz);
                 return sc ? sc : st;
             }
+            if (sig && ot >= sg_toff)
+                signal_step(p, sox, soy, soz, sot, svx, svy, svz, ax, ay, az,
+                            timed && sub == ns - 1);
             if (st) return st;
         }
         return 0;
@@ -1255,7 +1427,7 @@ struct MixedElectron {
             timed = c.y != 0.0f;
         }
         int st;
-        if (GEO && (p.substeps > 1 || p.crossing)) {
+        if (GEO && (p.substeps > 1 || p.crossing || p.signal_bins)) {
             st = fly_steps<FK>(p, dt, ex, ey, ez);
         } else {
             move(p, ax, ay, az, dt);
@@ -1400,15 +1572,16 @@ struct MixedElectron {
         p.nflight[slot] = nf;
     }
 
-    template <int FK>
+    template <int FK, bool GEO = true>
     __device__ void save(const RunParams &p, const Stack &s, int64_t i)
     {
+        if (GEO) signal_end(p);  // the part so far; restore() starts again from here
         position(p, s.x[i], s.y[i], s.z[i], s.t[i]);
         s.vx[i] = vx; s.vy[i] = vy; s.vz[i] = vz;
         s.nf[i] = nf; s.nreal[i] = nreal; s.uid[i] = uid; s.slot[i] = slot;
     }
 
-    template <int FK>
+    template <int FK, bool GEO = true>
     __device__ void restore(const RunParams &p, const Stack &s, int64_t i, int av)
     {
         vx = (float)s.vx[i]; vy = (float)s.vy[i]; vz = (float)s.vz[i];
@@ -1419,6 +1592,7 @@ struct MixedElectron {
         status = 0;
         timed = false;
         set_base<FK>(p, s.x[i], s.y[i], s.z[i], s.t[i]);
+        if (GEO) signal_start(p);
     }
 };
 

@@ -137,10 +137,11 @@ __device__ __forceinline__ unsigned long long flush_tally(const RunParams &p, co
 }
 
 // An electron has finished: write its endpoint and move its counts.
-template <class E>
+template <bool GEO, class E>
 __device__ __forceinline__ void finish(const RunParams &p, const Tables &tb, const E &e,
                                        BlockState &bs)
 {
+    if (GEO) e.signal_end(p);  // induced signals are built only into GEO kernels
     e.write_end(p);
     const unsigned long long real = flush_tally(p, tb, e.aval, e.nnull);
     atomicAdd(&bs.flights, (unsigned long long)e.nf);
@@ -217,11 +218,11 @@ __global__ void __launch_bounds__(MAXT) k_batched(const RunParams p)
         int retired = 0;
         if (!has && ticket >= 0 && ticket < p.capacity) {
             if (ld_acquire_u32(p.ready + ticket)) {
-                e.template load_birth<FK>(p, ticket);
+                e.template load_birth<FK, GEO>(p, ticket);
                 ticket = -1;
                 has = true;
                 if (e.template check_start<FK>(p) & EV_RETIRE) {
-                    finish(p, tb, e, bs);
+                    finish<GEO>(p, tb, e, bs);
                     has = false;
                     retired = 1;
                 }
@@ -275,7 +276,7 @@ __global__ void __launch_bounds__(MAXT) k_batched(const RunParams p)
                     const bool go = has && !pd.real;
                     if (MP != 1 && !__any_sync(FULL, go)) break;
                     if (go && (e.template advance<FK, GEO>(p, tb, pd) & EV_RETIRE)) {
-                        finish(p, tb, e, bs);
+                        finish<GEO>(p, tb, e, bs);
                         has = false;
                         ++retired;
                     }
@@ -286,7 +287,7 @@ __global__ void __launch_bounds__(MAXT) k_batched(const RunParams p)
                 if (__any_sync(FULL, ev & EV_CHILD))
                     retired += push_children(p, (ev & EV_CHILD) != 0, e, ch, lane);
                 if (ev & EV_RETIRE) {
-                    finish(p, tb, e, bs);
+                    finish<GEO>(p, tb, e, bs);
                     has = false;
                     ++retired;
                 }
@@ -300,7 +301,7 @@ __global__ void __launch_bounds__(MAXT) k_batched(const RunParams p)
                 if (__any_sync(FULL, ev & EV_CHILD))
                     retired += push_children(p, (ev & EV_CHILD) != 0, e, ch, lane);
                 if (ev & EV_RETIRE) {
-                    finish(p, tb, e, bs);
+                    finish<GEO>(p, tb, e, bs);
                     has = false;
                     ++retired;
                 }
@@ -338,7 +339,7 @@ __global__ void __launch_bounds__(MAXT)
 
     E e;
     e.bind(tb);
-    e.template restore<FK>(p, cur, i, aval);
+    e.template restore<FK, GEO>(p, cur, i, aval);
     const uint32_t nf0 = e.nf, nr0 = e.nreal;
     typename E::ChildT ch;
     int ev = EV_NONE;
@@ -374,10 +375,11 @@ __global__ void __launch_bounds__(MAXT)
     atomicAdd(&p.hdr->real, (unsigned long long)(e.nreal - nr0));
     atomicAdd(&p.hdr->nul, (unsigned long long)e.nnull);
     if (ev & EV_RETIRE) {
+        if (GEO) e.signal_end(p);
         e.write_end(p);
         cur.alive[i] = 0;
     } else {
-        e.template save<FK>(p, cur, i);
+        e.template save<FK, GEO>(p, cur, i);
         cur.alive[i] = 1;
     }
 }

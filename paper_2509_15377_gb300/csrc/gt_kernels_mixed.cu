@@ -25,8 +25,9 @@ template cudaError_t configure_mixed_t<false, false>(size_t);
 template int occupancy_batched_mixed_t<false, false>(int, bool, int, size_t);
 
 // Variants: the basic gas; gases with anisotropy, attachment or a sharing
-// law (PHYS); runs with sub-steps or exact crossings (GEO, with PHYS).
-static bool geo(const RunParams &p) { return p.substeps > 1 || p.crossing; }
+// law (PHYS); runs with sub-steps, exact crossings or induced signals (GEO,
+// with PHYS).
+static bool geo(const RunParams &p) { return p.substeps > 1 || p.crossing || p.signal_bins; }
 static bool phys(const RunParams &p) { return p.gas.any_special != 0; }
 
 cudaError_t launch_batched_mixed(const RunParams &p, bool smem_table, int grid, int block,
