@@ -215,9 +215,19 @@ def run_ours(args) -> None:
                             round(q["real_per_ms"] / 1e6, 4)] for q in pts],
                 "points_unit": "[block, refill_period, flights_per_phase, 1e9 real collisions/s]"}
 
+    # the timed steps replay the batched run as a captured CUDA graph (a new
+    # seed per step: different avalanches, same work); --no-graph calls
+    # avalanche_run instead
+    graph = None if args.no_graph else av.graph(prim_dev, opt, cap)
+    step_no = [0]
+
     def step(prim):
         flush.fill_(1)
-        return av.run(prim, opt, cap, stream=stream, allow=(A.GT_OK,))
+        step_no[0] += 1
+        if graph is None:
+            return av.run(prim, opt, cap, stream=stream, allow=(A.GT_OK,))
+        graph.launch(seed + 7919 * step_no[0], stream=stream)
+        return graph.stats(allow=(A.GT_OK,))
 
     for _ in range(args.warmup):
         step(prim_dev)
@@ -396,6 +406,8 @@ def run_ours(args) -> None:
                    "refill_period": stats[-1]["refill_period"],
                    "flights_per_phase": stats[-1]["flights_per_phase"],
                    "autotune": tune,
+                   "launch": "avalanche_run per step" if args.no_graph else
+                             "captured CUDA graph replay per step (new seed each)",
                    "l2": "flushed (256 MB write) before every step"},
         "flights_per_s": sum_over_ranks(float(flights), dev) / t_max_rank,
         "null_fraction": 1.0 - real / max(flights, 1),
@@ -516,6 +528,8 @@ def parse(argv=None):
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-plain", action="store_true")
     ap.add_argument("--no-autotune", action="store_true")
+    ap.add_argument("--no-graph", action="store_true",
+                    help="time avalanche_run calls instead of captured graph replays")
     ap.add_argument("--majorant", default="banded", choices=["banded", "global"])
     ap.add_argument("--window", type=float, default=2.0)
     ap.add_argument("--tune-avalanches", type=int, default=1024)

@@ -358,6 +358,34 @@ int avalanche_run(gt_ctx *ctx, const gt_run *run, const gt_endpoints *out, void 
 int avalanche_run_static(gt_ctx *ctx, const gt_run *run, const gt_endpoints *out, void *stream,
                          gt_stats *stats);
 
+/* ---- captured launch graphs ------------------------------------------
+ * The device work of one batched run -- zeroing the outputs and the run
+ * header, seeding the queue, the persistent transport, the per-avalanche
+ * electron counts and the copy of the run's status -- recorded once as a
+ * CUDA graph and replayed with one launch.  The run must be GT_BATCHED with
+ * primaries in device memory; every replay reads the primaries and writes
+ * the outputs at the addresses given to gt_graph_create (the caller may
+ * refill the primaries between replays; n_primaries and n_avalanches are
+ * fixed).  The graph keeps the run's launch shape.
+ *   gt_graph_create   records the graph (nothing runs); errors as
+ *                     avalanche_run, GT_ERR_UNSUPPORTED for GT_PLAIN or host
+ *                     primaries;
+ *   gt_graph_launch   enqueues a replay on `stream` with `seed` (a seed that
+ *                     differs from the last one records the graph again and
+ *                     updates it in place, tens of microseconds on the host);
+ *   gt_graph_stats    waits for the last replay and returns its summary and
+ *                     status (as avalanche_run; GT_ERR_STATE before a launch);
+ *   gt_graph_destroy  releases it (after its replays have finished).
+ * A graph belongs to one context and must not be used from two threads at
+ * once; its replays, like runs, must not overlap on the same outputs. */
+typedef struct gt_graph gt_graph;
+
+int gt_graph_create(gt_ctx *ctx, const gt_run *run, const gt_endpoints *out, void *workspace,
+                    size_t workspace_bytes, gt_graph **graph);
+int gt_graph_launch(gt_graph *graph, uint64_t seed, void *stream);
+int gt_graph_stats(gt_graph *graph, gt_stats *stats);
+int gt_graph_destroy(gt_graph *graph);
+
 /* ---- autotuning of the batched launch shape ---------------------------
  * The batched kernel's throughput depends on the threads per CTA (more
  * resident warps against fewer registers each) and on the flights per

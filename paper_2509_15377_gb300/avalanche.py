@@ -105,7 +105,8 @@ class gt_tune_point(C.Structure):
 EXPORTS = ("gt_abi_version", "gt_strerror", "gt_abi_sizes", "gt_last_cuda_error", "gt_create",
            "gt_destroy", "gas_table_upload", "gt_gas_nu_max", "field_setup",
            "gt_workspace_bytes", "avalanche_run", "avalanche_run_static", "gt_autotune",
-           "avalanche_observables")
+           "avalanche_observables", "gt_graph_create", "gt_graph_launch", "gt_graph_stats",
+           "gt_graph_destroy")
 
 _lib = None
 
@@ -139,6 +140,11 @@ def load(path: str = LIB_PATH):
         "gt_autotune": ([vp, C.POINTER(gt_run), C.POINTER(gt_endpoints), vp, sz, vp,
                          C.POINTER(gt_tune_point), i32, C.POINTER(i32),
                          C.POINTER(gt_tune_point)], C.c_int),
+        "gt_graph_create": ([vp, C.POINTER(gt_run), C.POINTER(gt_endpoints), vp, sz,
+                             C.POINTER(vp)], C.c_int),
+        "gt_graph_launch": ([vp, C.c_uint64, vp], C.c_int),
+        "gt_graph_stats": ([vp, C.POINTER(gt_stats)], C.c_int),
+        "gt_graph_destroy": ([vp], C.c_int),
     }
     for name, (args, res) in sig.items():
         f = getattr(lib, name)
@@ -447,6 +453,17 @@ class Avalanche:
                            allow)
         return st.as_dict()
 
+    def graph(self, prim: dict, opt: RunOptions, capacity: int) -> "Graph":
+        """Record a batched run with device primaries as a CUDA graph
+        (gt_graph_create); replay it with Graph.launch(seed)."""
+        r = self.make_run(prim, opt)
+        self.alloc(capacity, r.n_avalanches, r)
+        o = self.endpoints_struct(capacity)
+        h = C.c_void_p()
+        _check(load().gt_graph_create(self.ctx, C.byref(r), C.byref(o), self.ws.data_ptr(),
+                                      self.ws.numel(), C.byref(h)), "gt_graph_create", self.ctx)
+        return Graph(self, h)
+
     def autotune(self, prim: dict, opt: RunOptions, capacity: int, stream=None):
         """Pick the batched launch shape for this precision and field kind
         (remembered by the context for runs that leave it at 0)."""
@@ -486,3 +503,34 @@ class Avalanche:
         avalanche_observables(self.ctx, o, n_endpoints, prim.n_avalanches, n_prim_t.data_ptr(),
                               collect_status, drift_status, gap, obs.data_ptr(), s.cuda_stream)
         return obs.cpu().numpy()
+
+
+class Graph:
+    """A batched run recorded as a CUDA graph (gt_graph_* in the C ABI)."""
+
+    def __init__(self, owner: "Avalanche", handle: C.c_void_p):
+        self.owner = owner
+        self.h = handle
+
+    def launch(self, seed: int, stream=None) -> None:
+        torch = self.owner.torch
+        s = stream if stream is not None else torch.cuda.current_stream(self.owner.device)
+        _check(load().gt_graph_launch(self.h, seed & (2**64 - 1), s.cuda_stream),
+               "gt_graph_launch", self.owner.ctx)
+
+    def stats(self, allow=PARTIAL_OK) -> dict:
+        st = gt_stats()
+        rc = load().gt_graph_stats(self.h, C.byref(st))
+        _check(rc, "gt_graph_stats", self.owner.ctx, allow)
+        return st.as_dict()
+
+    def close(self) -> None:
+        if self.h:
+            load().gt_graph_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

@@ -518,23 +518,27 @@ static int finish_status(const Header &h)
     return GT_OK;
 }
 
-int avalanche_run(gt_ctx *ctx, const gt_run *r, const gt_endpoints *o, void *ws, size_t ws_bytes,
-                  void *stream, gt_stats *stats)
+// A run's parameters and launch shape, decided on the host.
+struct RunPlan {
+    RunParams p{};
+    SeedArgs sa{};
+    int block = 0, grid = 0;
+    size_t smem = 0;
+    bool fp64 = false, smem_table = false;
+};
+
+// Fills the plan of a validated run.  Host primaries are staged into the
+// work space with copies on stream s (the only device work here).
+static int plan_run(gt_ctx *ctx, const gt_run *r, const gt_endpoints *o, void *ws,
+                    cudaStream_t s, RunPlan &pl)
 {
-    if (!ctx) return GT_ERR_ARG;
-    int rc = validate_run(ctx, r, o, ws, ws_bytes);
-    if (rc != GT_OK) return rc;
-    DeviceGuard dg(ctx->device);
-    if (!dg.ok) return GT_ERR_CUDA;
-    cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
     const Layout Ly = layout_for(r, o->capacity);
     char *base = static_cast<char *>(ws);
     const int64_t np = r->n_primaries;
     const int na = r->n_avalanches;
     const int L = ctx->gas.n_levels;
-    int launches = 0;
-
-    RunParams p{};
+    RunParams &p = pl.p;
+    SeedArgs &sa = pl.sa;
     p.gas = ctx->gas;
     p.field = ctx->field;
     p.x0 = o->x0; p.y0 = o->y0; p.z0 = o->z0; p.t0 = o->t0; p.e0 = o->e0;
@@ -582,7 +586,6 @@ int avalanche_run(gt_ctx *ctx, const gt_run *r, const gt_endpoints *o, void *ws,
     p.n_avalanches = na;
 
     // primaries: stage host arrays in the work space (inside the run)
-    SeedArgs sa{};
     sa.n = np;
     sa.unfilled_slot = (r->debug_flags & GT_DEBUG_UNFILLED_SLOT) ? 1 : 0;
     p.aval_field = r->aval_field;
@@ -630,9 +633,6 @@ int avalanche_run(gt_ctx *ctx, const gt_run *r, const gt_endpoints *o, void *ws,
         if (r->size_limit)
             GT_CUDA(ctx, cudaMemsetAsync(p.created, 0, sizeof(unsigned long long) * (size_t)na, s));
     }
-    GT_CUDA(ctx, launch_seed(p, sa, s));
-    ++launches;
-
     const bool fp64 = r->precision == GT_FP64;
     const int tuned_b = ctx->tuned_block[prec_i][ctx->field.kind & 3][maj_i];
     const int block = r->block ? r->block
@@ -644,22 +644,112 @@ int avalanche_run(gt_ctx *ctx, const gt_run *r, const gt_endpoints *o, void *ws,
     const bool smem_table = !fp64 && smem_tab <= smem_cap;
     const size_t smem = shared_bytes(L, ctx->gas.n_nodes, block, smem_table, band_entries);
     if (smem > smem_cap) return GT_ERR_UNSUPPORTED;
-    int iterations = 0, grid = 0;
-    unsigned host_err = 0;  // aborts decided on the host (plain mode)
-    double transport_ms = 0.0;
-    const int K = p.refill_period;
-
+    pl.block = block;
+    pl.smem = smem;
+    pl.fp64 = fp64;
+    pl.smem_table = smem_table;
     if (r->mode == GT_BATCHED) {
         const int occ = fp64 ? occupancy_batched_fp64(ctx->field.kind, block, smem)
                              : occupancy_batched_mixed(ctx->field.kind, smem_table, block, smem);
         if (occ < 1) return GT_ERR_UNSUPPORTED;
-        grid = r->grid ? r->grid : ctx->sms * occ;
-        GT_CUDA(ctx, cudaEventRecord(ctx->ev0, s));
-        GT_CUDA(ctx, fp64 ? launch_batched_fp64(p, grid, block, smem, s)
-                          : launch_batched_mixed(p, smem_table, grid, block, smem, s));
-        GT_CUDA(ctx, cudaEventRecord(ctx->ev1, s));
-        ++launches;
+        pl.grid = r->grid ? r->grid : ctx->sms * occ;
+    }
+    return GT_OK;
+}
+
+// Outputs, queue flags and the run header start from zero; then the
+// primaries are seeded.
+static int enqueue_start(gt_ctx *ctx, const RunPlan &pl, const gt_endpoints *o, int na,
+                         cudaStream_t s)
+{
+    const RunParams &p = pl.p;
+    const int L = ctx->gas.n_levels;
+    GT_CUDA(ctx, cudaMemsetAsync(p.hdr, 0, sizeof(Header), s));
+    if (o->capacity > 0)
+        GT_CUDA(ctx, cudaMemsetAsync(p.ready, 0, sizeof(uint32_t) * (size_t)o->capacity, s));
+    if (na > 0) {
+        GT_CUDA(ctx, cudaMemsetAsync(o->tallies, 0, sizeof(uint64_t) * (size_t)na * (L + 1), s));
+        if (p.signal_bins)
+            GT_CUDA(ctx, cudaMemsetAsync(o->signal, 0,
+                                         sizeof(double) * (size_t)na * (size_t)p.signal_bins, s));
+        GT_CUDA(ctx, cudaMemsetAsync(o->electrons, 0, sizeof(uint64_t) * (size_t)na, s));
+        if (p.size_limit)
+            GT_CUDA(ctx, cudaMemsetAsync(p.created, 0, sizeof(unsigned long long) * (size_t)na, s));
+    }
+    GT_CUDA(ctx, launch_seed(p, pl.sa, s));
+    return GT_OK;
+}
+
+// The rest of a batched run: the persistent transport between ev0 and ev1,
+// the per-avalanche electron counts and the header copied to h_hdr.  No
+// host synchronisation: the sequence can be captured in a CUDA graph (with
+// `capture`, the events become event-record nodes of the graph).
+static int enqueue_batched(gt_ctx *ctx, const RunPlan &pl, cudaStream_t s, cudaEvent_t ev0,
+                           cudaEvent_t ev1, Header *h_hdr, bool capture = false)
+{
+    const RunParams &p = pl.p;
+    const unsigned evf = capture ? cudaEventRecordExternal : cudaEventRecordDefault;
+    GT_CUDA(ctx, cudaEventRecordWithFlags(ev0, s, evf));
+    GT_CUDA(ctx, pl.fp64 ? launch_batched_fp64(p, pl.grid, pl.block, pl.smem, s)
+                         : launch_batched_mixed(p, pl.smem_table, pl.grid, pl.block, pl.smem, s));
+    GT_CUDA(ctx, cudaEventRecordWithFlags(ev1, s, evf));
+    GT_CUDA(ctx, launch_count_electrons(p, ctx->sms, s));
+    GT_CUDA(ctx, cudaMemcpyAsync(h_hdr, p.hdr, sizeof(Header), cudaMemcpyDeviceToHost, s));
+    return GT_OK;
+}
+
+static void fill_stats(const Header &h, const RunPlan &pl, int64_t capacity, double transport_ms,
+                       int launches, int iterations, int grid, int rc, gt_stats *stats)
+{
+    if (!stats) return;
+    stats->n_endpoints = (int64_t)std::min<unsigned long long>(h.tail, (unsigned long long)capacity);
+    stats->n_dropped = (int64_t)h.dropped;
+    stats->real_collisions = h.real;
+    stats->null_collisions = h.nul;
+    stats->flights = h.flights;
+    stats->transport_ms = transport_ms;
+    stats->launches = launches;
+    stats->iterations = iterations;
+    stats->status = rc;
+    stats->block = pl.block;
+    stats->refill_period = pl.p.refill_period;
+    stats->grid = grid;
+    stats->flights_per_phase = pl.p.flights_per_phase;
+}
+
+int avalanche_run(gt_ctx *ctx, const gt_run *r, const gt_endpoints *o, void *ws, size_t ws_bytes,
+                  void *stream, gt_stats *stats)
+{
+    if (!ctx) return GT_ERR_ARG;
+    int rc = validate_run(ctx, r, o, ws, ws_bytes);
+    if (rc != GT_OK) return rc;
+    DeviceGuard dg(ctx->device);
+    if (!dg.ok) return GT_ERR_CUDA;
+    cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+    RunPlan pl;
+    if ((rc = plan_run(ctx, r, o, ws, s, pl)) != GT_OK) return rc;
+    const RunParams &p = pl.p;
+    const Layout Ly = layout_for(r, o->capacity);
+    char *base = static_cast<char *>(ws);
+    const int64_t np = r->n_primaries;
+    const int na = r->n_avalanches;
+    const int L = ctx->gas.n_levels;
+    const bool fp64 = pl.fp64;
+    const bool smem_table = pl.smem_table;
+    const int block = pl.block;
+    const int band_entries = ctx->gas.n_bands * ctx->gas.band_levels;
+    if ((rc = enqueue_start(ctx, pl, o, na, s)) != GT_OK) return rc;
+    int launches = 1;
+    int iterations = 0, grid = 0;
+    unsigned host_err = 0;  // aborts decided on the host (plain mode)
+    double transport_ms = 0.0;
+
+    if (r->mode == GT_BATCHED) {
+        grid = pl.grid;
+        if ((rc = enqueue_batched(ctx, pl, s, ctx->ev0, ctx->ev1, ctx->h_hdr)) != GT_OK) return rc;
+        launches += 2;
         iterations = 1;
+        GT_CUDA(ctx, cudaStreamSynchronize(s));
     } else {
         // one avalanche at a time: seed, then generations until none is active
         std::vector<int32_t> av((size_t)np);
@@ -738,32 +828,166 @@ int avalanche_run(gt_ctx *ctx, const gt_run *r, const gt_endpoints *o, void *ws,
         if (stop) host_err = ctx->h_hdr->error & (ERR_TIMEOUT | ERR_BADARG);
     }
 
-    GT_CUDA(ctx, launch_count_electrons(p, ctx->sms, s));
-    ++launches;
-    GT_CUDA(ctx, cudaMemcpyAsync(ctx->h_hdr, p.hdr, sizeof(Header), cudaMemcpyDeviceToHost, s));
-    GT_CUDA(ctx, cudaStreamSynchronize(s));
+    if (r->mode != GT_BATCHED) {
+        GT_CUDA(ctx, launch_count_electrons(p, ctx->sms, s));
+        ++launches;
+        GT_CUDA(ctx, cudaMemcpyAsync(ctx->h_hdr, p.hdr, sizeof(Header), cudaMemcpyDeviceToHost, s));
+        GT_CUDA(ctx, cudaStreamSynchronize(s));
+    }
     float ms = 0.f;
     GT_CUDA(ctx, cudaEventElapsedTime(&ms, ctx->ev0, ctx->ev1));
     transport_ms = ms;
     Header &h = *ctx->h_hdr;
     h.error |= host_err;
     rc = finish_status(h);
-    if (stats) {
-        stats->n_endpoints = (int64_t)std::min<unsigned long long>(h.tail, (unsigned long long)o->capacity);
-        stats->n_dropped = (int64_t)h.dropped;
-        stats->real_collisions = h.real;
-        stats->null_collisions = h.nul;
-        stats->flights = h.flights;
-        stats->transport_ms = transport_ms;
-        stats->launches = launches;
-        stats->iterations = iterations;
-        stats->status = rc;
-        stats->block = block;
-        stats->refill_period = K;
-        stats->grid = grid;
-        stats->flights_per_phase = p.flights_per_phase;
-    }
+    fill_stats(h, pl, o->capacity, transport_ms, launches, iterations, grid, rc, stats);
     return rc;
+}
+
+
+// ---------------------------------------------------------------- graphs
+struct gt_graph {
+    gt_ctx *ctx = nullptr;
+    RunPlan pl;
+    gt_endpoints o{};
+    int na = 0;
+    cudaStream_t cap = nullptr;    // capture only: nothing runs on it
+    cudaGraphExec_t exec = nullptr;
+    cudaEvent_t ev0 = nullptr, ev1 = nullptr, ev2 = nullptr;  // transport start/end, run end
+    Header *h_hdr = nullptr;       // pinned, written by the graph's last copy
+    uint64_t seed = 0;
+    bool launched = false;
+};
+
+namespace {
+
+void graph_free(gt_graph *g)
+{
+    if (!g) return;
+    if (g->exec) cudaGraphExecDestroy(g->exec);
+    if (g->ev0) cudaEventDestroy(g->ev0);
+    if (g->ev1) cudaEventDestroy(g->ev1);
+    if (g->ev2) cudaEventDestroy(g->ev2);
+    if (g->h_hdr) cudaFreeHost(g->h_hdr);
+    if (g->cap) cudaStreamDestroy(g->cap);
+    delete g;
+}
+
+// Records the run's device work into a new graph.
+int graph_capture(gt_graph *g, cudaGraph_t *graph)
+{
+    gt_ctx *ctx = g->ctx;
+    GT_CUDA(ctx, cudaStreamBeginCapture(g->cap, cudaStreamCaptureModeThreadLocal));
+    int rc = enqueue_start(ctx, g->pl, &g->o, g->na, g->cap);
+    if (rc == GT_OK) rc = enqueue_batched(ctx, g->pl, g->cap, g->ev0, g->ev1, g->h_hdr, true);
+    if (rc == GT_OK && cudaEventRecordWithFlags(g->ev2, g->cap, cudaEventRecordExternal) !=
+                           cudaSuccess)
+        rc = cuda_fail(ctx, cudaGetLastError(), "cudaEventRecordWithFlags");
+    cudaGraph_t out = nullptr;
+    const cudaError_t e = cudaStreamEndCapture(g->cap, &out);
+    if (rc != GT_OK) {
+        if (out) cudaGraphDestroy(out);
+        return rc;
+    }
+    if (e != cudaSuccess) return cuda_fail(ctx, e, "cudaStreamEndCapture");
+    *graph = out;
+    return GT_OK;
+}
+
+}  // namespace
+
+int gt_graph_create(gt_ctx *ctx, const gt_run *run, const gt_endpoints *out, void *ws,
+                    size_t ws_bytes, gt_graph **graph)
+{
+    if (!ctx || !graph) return GT_ERR_ARG;
+    *graph = nullptr;
+    int rc = validate_run(ctx, run, out, ws, ws_bytes);
+    if (rc != GT_OK) return rc;
+    if (run->mode != GT_BATCHED || !run->primaries_on_device) return GT_ERR_UNSUPPORTED;
+    DeviceGuard dg(ctx->device);
+    if (!dg.ok) return GT_ERR_CUDA;
+    gt_graph *g = new (std::nothrow) gt_graph();
+    if (!g) return GT_ERR_CUDA;
+    g->ctx = ctx;
+    g->o = *out;
+    g->na = run->n_avalanches;
+    g->seed = run->seed;
+    cudaGraph_t gr = nullptr;
+    if (cudaStreamCreateWithFlags(&g->cap, cudaStreamNonBlocking) != cudaSuccess ||
+        cudaEventCreate(&g->ev0) != cudaSuccess || cudaEventCreate(&g->ev1) != cudaSuccess ||
+        cudaEventCreate(&g->ev2) != cudaSuccess ||
+        cudaMallocHost((void **)&g->h_hdr, sizeof(Header)) != cudaSuccess) {
+        rc = cuda_fail(ctx, cudaGetLastError(), "gt_graph_create");
+    } else {
+        rc = plan_run(ctx, run, out, ws, g->cap, g->pl);
+    }
+    if (rc == GT_OK) rc = graph_capture(g, &gr);
+    if (rc == GT_OK) {
+        const cudaError_t e = cudaGraphInstantiate(&g->exec, gr, 0);
+        if (e != cudaSuccess) rc = cuda_fail(ctx, e, "cudaGraphInstantiate");
+    }
+    if (gr) cudaGraphDestroy(gr);
+    if (rc != GT_OK) {
+        graph_free(g);
+        return rc;
+    }
+    *graph = g;
+    return GT_OK;
+}
+
+int gt_graph_launch(gt_graph *g, uint64_t seed, void *stream)
+{
+    if (!g) return GT_ERR_ARG;
+    gt_ctx *ctx = g->ctx;
+    DeviceGuard dg(ctx->device);
+    if (!dg.ok) return GT_ERR_CUDA;
+    if (seed != g->seed) {
+        // a new seed: record the run again and update the instantiated graph
+        g->pl.p.seed = seed;
+        cudaGraph_t gr = nullptr;
+        int rc = graph_capture(g, &gr);
+        if (rc != GT_OK) return rc;
+        cudaGraphExecUpdateResultInfo info;
+        if (cudaGraphExecUpdate(g->exec, gr, &info) != cudaSuccess) {
+            cudaGetLastError();
+            cudaGraphExecDestroy(g->exec);
+            g->exec = nullptr;
+            const cudaError_t e = cudaGraphInstantiate(&g->exec, gr, 0);
+            if (e != cudaSuccess) {
+                cudaGraphDestroy(gr);
+                return cuda_fail(ctx, e, "cudaGraphInstantiate");
+            }
+        }
+        cudaGraphDestroy(gr);
+        g->seed = seed;
+    }
+    GT_CUDA(ctx, cudaGraphLaunch(g->exec, reinterpret_cast<cudaStream_t>(stream)));
+    g->launched = true;
+    return GT_OK;
+}
+
+int gt_graph_stats(gt_graph *g, gt_stats *stats)
+{
+    if (!g || !stats) return GT_ERR_ARG;
+    if (!g->launched) return GT_ERR_STATE;
+    gt_ctx *ctx = g->ctx;
+    DeviceGuard dg(ctx->device);
+    if (!dg.ok) return GT_ERR_CUDA;
+    GT_CUDA(ctx, cudaEventSynchronize(g->ev2));
+    float ms = 0.f;
+    GT_CUDA(ctx, cudaEventElapsedTime(&ms, g->ev0, g->ev1));
+    const Header &h = *g->h_hdr;
+    const int rc = finish_status(h);
+    fill_stats(h, g->pl, g->o.capacity, ms, 3, 1, g->pl.grid, rc, stats);
+    return rc;
+}
+
+int gt_graph_destroy(gt_graph *g)
+{
+    if (!g) return GT_OK;
+    DeviceGuard dg(g->ctx->device);
+    graph_free(g);
+    return GT_OK;
 }
 
 int gt_autotune(gt_ctx *ctx, const gt_run *run, const gt_endpoints *out, void *ws,

@@ -14,16 +14,9 @@ __global__ void k_seed(const RunParams p, const SeedArgs a)
 {
     const long long stride = (long long)gridDim.x * blockDim.x;
     const long long i0 = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-    if (i0 == 0) {
+    if (i0 == 0) {  // the header was zeroed before this launch
         Header *h = p.hdr;
-        h->head = 0ull;
         h->tail = (unsigned long long)a.n + (a.unfilled_slot ? 1ull : 0ull);
-        h->done = 0ull;
-        h->dropped = 0ull;
-        h->flights = h->real = h->nul = 0ull;
-        h->error = 0u;
-        h->n_new[0] = h->n_new[1] = 0ull;
-        h->n_next[0] = h->n_next[1] = 0ull;
         h->t_start = globaltimer();
     }
     for (long long i = i0; i < a.n; i += stride) {

@@ -8,7 +8,7 @@ import pytest
 import oracle
 from paper_2509_15377_gb300 import avalanche as A
 from paper_2509_15377_gb300 import workloads as W
-from tests.gpu_helpers import assert_same_electrons, run_gpu
+from tests.gpu_helpers import assert_same_electrons, by_uid, run_gpu
 
 pytestmark = pytest.mark.gpu
 
@@ -164,3 +164,38 @@ def test_argument_errors(av):
     w = W.plate(n_avalanches=8, seed=0)
     av.set_gas(w.gas)
     av.set_field(w.field)
+
+
+def test_graph_replays_equal_runs(av):
+    """A captured graph replays the batched run: with the run's seed it
+    gives the same electrons and tallies as avalanche_run (FP64, bitwise
+    by id), a new seed gives the run with that seed, and the summary and
+    status come back through gt_graph_stats."""
+    w = W.plate(n_avalanches=64, e_field=40_000.0, seed=111)
+    av.set_gas(w.gas)
+    av.set_field(w.field)
+    p = av.primaries_device(w.primaries)
+    cap = 400_000
+    opt = A.RunOptions(seed=5, t_max=w.t_max, precision=A.GT_FP64, mode=A.GT_BATCHED)
+    ref5 = av.run(p, opt, cap)
+    a5 = av.fetch(ref5["n_endpoints"])
+    ref6 = av.run(p, A.RunOptions(**{**opt.__dict__, "seed": 6}), cap)
+    a6 = av.fetch(ref6["n_endpoints"])
+    g = av.graph(p, opt, cap)
+    try:
+        for seed, st_ref, ref in ((5, ref5, a5), (6, ref6, a6), (5, ref5, a5)):
+            g.launch(seed)
+            st = g.stats()
+            assert st["n_endpoints"] == st_ref["n_endpoints"]
+            assert st["real_collisions"] == st_ref["real_collisions"]
+            out = av.fetch(st["n_endpoints"])
+            assert np.array_equal(out["tallies"], ref["tallies"])
+            assert np.array_equal(out["electrons"], ref["electrons"])
+            o, r = by_uid(out), by_uid(ref)
+            for k in ("x1", "y1", "z1", "t1", "e1", "status"):
+                assert np.array_equal(o[k], r[k]), k
+    finally:
+        g.close()
+    with pytest.raises(A.GtError) as e:
+        av.graph(av.primaries_pinned(w.primaries), opt, cap)
+    assert e.value.code == A.GT_ERR_UNSUPPORTED
