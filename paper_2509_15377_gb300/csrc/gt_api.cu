@@ -333,6 +333,11 @@ int gas_table_upload(gt_ctx *ctx, const gt_gas *g)
     d.cum32 = ctx->d_cum32;
     d.n_bands = B;
     d.band_levels = J + 1;
+    // non-decreasing band bounds (a rising total rate): the largest bound
+    // over a band range is its top band's, one lookup
+    d.bands_monotone = 1;
+    for (int b = 1; b < B; ++b)
+        if (band[b] < band[b - 1]) d.bands_monotone = 0;
     d.inv_band_width = 1.0 / (bn * g->d_eps);
     d.inv_band_width_f = (float)d.inv_band_width;
     d.last_band_f = (float)(B - 1);

@@ -44,6 +44,7 @@ struct DevGas {
     // hold range maxima, level j, entry b = max over bands b .. b + 2^j - 1
     // (a sparse table: the maximum over any band range is two lookups).
     int n_bands, band_levels;
+    int bands_monotone;          // band bounds non-decreasing: the range maximum is the top band's
     double inv_band_width;       // 1 / (n d_eps)
     float inv_band_width_f, last_band_f;
     const double *band64;        // [band_levels][n_bands]
@@ -439,13 +440,12 @@ __device__ __forceinline__ int select_below_total32(const float *c0, int stride,
                                                     float Rv)
 {
     const float *c1 = c0 + stride;
-    const int m = L - 1;
+    const int m = L - 1;  // < GT_MAX_LEVELS = 32: at most five halvings
     int pos = 0;
-    if (m > 0) {
-        for (int step = 1 << (31 - __clz(m)); step > 0; step >>= 1) {
-            const int j = pos + step - 1;
-            if (j < m && fmaf(f, c1[j] - c0[j], c0[j]) <= Rv) pos += step;
-        }
+#pragma unroll
+    for (int step = 16; step > 0; step >>= 1) {
+        const int j = pos + step - 1;
+        if (j < m && fmaf(f, c1[j] - c0[j], c0[j]) <= Rv) pos += step;
     }
     return pos;
 }
@@ -515,7 +515,7 @@ __device__ __forceinline__ void reach64(int has_b, double emax, double eps0, dou
 template <int FK>
 __device__ __forceinline__ void reach32(int has_b, float emax, float eps0, float vx, float vy,
                                         float vz, float ex, float ey, float ez, float plate_e,
-                                        float tau, float &lo, float &hi)
+                                        float tau, float &lo, float &hi, bool need_lo = true)
 {
     if (emax > 0.0f) {
         const float D = emax * fmaf(0.5f * kAccelF * emax * tau, tau,
@@ -531,7 +531,7 @@ __device__ __forceinline__ void reach32(int has_b, float emax, float eps0, float
         const float margin = 1e-5f * (eps0 + fabsf(vE) * tau + q);
         hi = eps0 + fmaxf(gw, 0.0f) + margin;
         float l = eps0;
-        if (vE > 0.0f) {
+        if (need_lo && vE > 0.0f) {
             const float ts = __fdividef(vE, kAccelF * E2);
             l = ts < tau ? fmaf(-0.5f * vE, ts, eps0) : eps0 + gw;
         }
@@ -979,8 +979,10 @@ struct Fp64Electron {
             const double tau = p.window / __ldg(p.gas.band64 + band_index64(p.gas, eps0));
             double lo, hi;
             reach64(p.field.has_b, p.field_emax, eps0, vx, vy, vz, ex, ey, ez, tau, lo, hi);
-            nu = band_range_max(p.gas.band64, p.gas.n_bands, band_index64(p.gas, lo),
-                                band_index64(p.gas, hi));
+            nu = p.gas.bands_monotone
+                     ? __ldg(p.gas.band64 + band_index64(p.gas, hi))
+                     : band_range_max(p.gas.band64, p.gas.n_bands, band_index64(p.gas, lo),
+                                      band_index64(p.gas, hi));
             dt = -log(u01d(w.x)) / nu;
             if (dt >= tau) {
                 dt = tau;
@@ -1410,9 +1412,11 @@ struct MixedElectron {
             const float tau = __fdividef(p.window_f, tb.band32[band_index32(p.gas, eps0)]);
             float lo, hi;
             reach32<FK>(p.field.has_b, p.field_emax_f, eps0, vx, vy, vz, ex, ey, ez, plate_e, tau,
-                        lo, hi);
-            nu = band_range_max(tb.band32, p.gas.n_bands, band_index32(p.gas, lo),
-                                band_index32(p.gas, hi));
+                        lo, hi, !p.gas.bands_monotone);
+            nu = p.gas.bands_monotone
+                     ? tb.band32[band_index32(p.gas, hi)]
+                     : band_range_max(tb.band32, p.gas.n_bands, band_index32(p.gas, lo),
+                                      band_index32(p.gas, hi));
             dt = -__fdividef(__logf(u01f(w.x)), nu);
             if (dt >= tau) {
                 dt = tau;

@@ -285,11 +285,13 @@ def coax_grid_map(n: int = 256, half_width: float = 0.15, length: float = 1.0,
                  origin=(-half_width, -half_width, 0.0), spacing=(sp, sp, length / (n - 1)))
 
 
-def grid_stress(n_avalanches: int = 256, n: int = 256, voltage: float = 1500.0,
+def grid_stress(n_avalanches: int = 256, n: int = 256, voltage: float = 1810.0,
                 r_start: float = 0.1, k_exc: float = ARGON_LIKE_K_EXC, t_max: float = 1000.0,
                 seed: int = 0) -> Workload:
     """Coax-sampled regular-grid map; one primary per avalanche at
-    r = r_start, random phi, mid-length."""
+    r = r_start, random phi, mid-length.  The default voltage gives a mean
+    gain near 1e5 with the argon-like gas (oracle: 1.14e5 +- 0.12e5 at
+    1820 V over 64 avalanches, 6.9e4 +- 1.1e4 at 1775 V over 16)."""
     rng = np.random.default_rng(seed)
     phi = rng.uniform(0.0, 2.0 * math.pi, n_avalanches)
     f = coax_grid_map(n=n, voltage=voltage)
