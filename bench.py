@@ -41,7 +41,7 @@ WORKLOAD = "plate_batched_4096"
 # (profiles/k_batched_mixed_plate_batched_4096.md).  Lanes switched off by
 # divergence are not counted, so divergence, stalls and queue work all show
 # as lost efficiency.
-LANE_INST_PER_FLIGHT = 485.3
+LANE_INST_PER_FLIGHT = 444.1
 SM_COUNT = 152
 ISSUE_PER_SM_PER_CLK = 4       # warp schedulers per SM, one instruction each per clock
 LANES_PER_WARP = 32
@@ -49,7 +49,7 @@ LANES_PER_WARP = 32
 # dram__bytes_write.sum on the 256-avalanche case, divided by its
 # electrons; traffic grows with electrons, so it is scaled to a launch by
 # the electrons the launch stores).  None once the kernel has changed.
-DRAM_BYTES_PER_ELECTRON = None
+DRAM_BYTES_PER_ELECTRON = 212.8
 
 
 # ---------------------------------------------------------------- sharding
