@@ -307,6 +307,9 @@ def run_ours(args) -> None:
     physical = None
     if rank == 0 and not args.no_plain:
         av.set_gas(W.argon_like_physical_gas())
+        tune_sample = av.primaries_device(w.primaries.subset(list(range(args.tune_avalanches))))
+        if not args.no_autotune:  # each kernel build has its own best shape
+            av.autotune(tune_sample, opt, cap, stream=stream)
         p_real, p_ms, p_fl = 0, 0.0, 0
         for _ in range(2):
             flush.fill_(1)
@@ -318,10 +321,13 @@ def run_ours(args) -> None:
                                drift_status=W.ANODE, gap=w.field.gap)
         physical = {"gas": "argon-like + screened-Coulomb anisotropy, OPB sharing, attachment",
                     "value_kernel_time": p_real / (p_ms / 1e3), "unit": UNIT,
-                    "flights_per_real": p_fl / max(p_real, 1), "gain": p_obs[0]}
+                    "flights_per_real": p_fl / max(p_real, 1), "gain": p_obs[0],
+                    "shape": [p_st["block"], p_st["refill_period"], p_st["flights_per_phase"]]}
         av.set_gas(w.gas)
         # the basic gas with exact boundary crossings (the general kernel)
         c_opt = dataclasses.replace(opt, crossing=1)
+        if not args.no_autotune:
+            av.autotune(tune_sample, c_opt, cap, stream=stream)
         c_real, c_ms = 0, 0.0
         for _ in range(2):
             flush.fill_(1)
@@ -329,7 +335,9 @@ def run_ours(args) -> None:
             c_real += c_st["real_collisions"]
             c_ms += c_st["transport_ms"]
         physical["crossing"] = {"value_kernel_time": c_real / (c_ms / 1e3), "unit": UNIT,
-                                "note": "basic gas, endpoints at the first boundary crossing"}
+                                "note": "basic gas, endpoints at the first boundary crossing",
+                                "shape": [c_st["block"], c_st["refill_period"],
+                                          c_st["flights_per_phase"]]}
         # the basic gas with the anode's induced signal, 2000 bins of 50 ps
         s_opt = dataclasses.replace(opt, signal_kind=W.W_PLATE, signal_bins=2000,
                                     signal_t0=0.0, signal_dt=0.05)

@@ -396,8 +396,10 @@ int gt_graph_destroy(gt_graph *graph);
  * MIXED 512/768/1024 threads x refill period 4/8/16/32 x flights per
  * phase 1/2/4/6 (48); FP64 128/256/512 threads x refill period 8/16/32/64
  * (12).  The fastest shape is remembered by the context for the run's
- * precision, field kind and majorant, and used by later runs that leave
- * block / refill_period / flights_per_phase at 0.
+ * precision, field kind, majorant and kernel build (the basic gas; a gas
+ * with anisotropy, attachment or a sharing law; a run with sub-steps,
+ * crossings or signals), and used by later runs that leave block /
+ * refill_period / flights_per_phase at 0.
  * points (may be NULL) receives up to max_points measurements, *n_points
  * their number; *best the chosen shape.  Errors as avalanche_run; a
  * candidate that fails is skipped. */

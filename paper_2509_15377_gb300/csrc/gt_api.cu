@@ -35,9 +35,11 @@ struct gt_ctx {
     size_t obs_partials_cap = 0;
     // autotuned batched launch shape per [precision][field kind] (0 = none)
     // autotuned launch shapes per [precision][field kind][majorant]
-    int tuned_block[2][4][2] = {};
-    int tuned_k[2][4][2] = {};
-    int tuned_m[2][4][2] = {};
+    // [precision][field kind][majorant][kernel build: basic, general gas,
+    // sub-steps/crossings/signals]
+    int tuned_block[2][4][2][3] = {};
+    int tuned_k[2][4][2][3] = {};
+    int tuned_m[2][4][2][3] = {};
     char last_error[256] = {0};
 };
 
@@ -137,6 +139,16 @@ Stack carve_stack(char *&p, int64_t cap)
 }
 
 int default_block(int precision) { return precision == GT_FP64 ? 256 : 512; }
+
+// Which build of the mixed kernels a run uses (their launch shapes are tuned
+// apart): 0 the basic gas, 1 the general gas (anisotropy, attachment, a
+// sharing law), 2 sub-steps, crossings or signals (any gas).
+int run_variant(const gt_ctx *ctx, const gt_run *r)
+{
+    if (r->substeps > 1 || r->crossing || (r->signal_kind != GT_W_NONE && r->signal_bins > 0))
+        return 2;
+    return ctx->gas.any_special ? 1 : 0;
+}
 
 bool finite_pos(double x) { return std::isfinite(x) && x > 0.0; }
 
@@ -562,8 +574,9 @@ static int plan_run(gt_ctx *ctx, const gt_run *r, const gt_endpoints *o, void *w
     p.coll_limit = r->coll_limit;
     const int prec_i = r->precision == GT_FP64 ? 0 : 1;
     const int maj_i = r->majorant == GT_MAJORANT_BANDED ? 1 : 0;
-    const int tuned_k = ctx->tuned_k[prec_i][ctx->field.kind & 3][maj_i];
-    const int tuned_m = ctx->tuned_m[prec_i][ctx->field.kind & 3][maj_i];
+    const int var_i = run_variant(ctx, r);
+    const int tuned_k = ctx->tuned_k[prec_i][ctx->field.kind & 3][maj_i][var_i];
+    const int tuned_m = ctx->tuned_m[prec_i][ctx->field.kind & 3][maj_i][var_i];
     p.refill_period = r->refill_period > 0 ? r->refill_period
                                            : (tuned_k > 0 ? tuned_k : (prec_i ? 16 : 32));
     // most banded flights end in a real collision, so a round flies once;
@@ -639,7 +652,7 @@ static int plan_run(gt_ctx *ctx, const gt_run *r, const gt_endpoints *o, void *w
             GT_CUDA(ctx, cudaMemsetAsync(p.created, 0, sizeof(unsigned long long) * (size_t)na, s));
     }
     const bool fp64 = r->precision == GT_FP64;
-    const int tuned_b = ctx->tuned_block[prec_i][ctx->field.kind & 3][maj_i];
+    const int tuned_b = ctx->tuned_block[prec_i][ctx->field.kind & 3][maj_i][var_i];
     const int block = r->block ? r->block
                                : (r->mode == GT_BATCHED && tuned_b > 0 ? tuned_b
                                                                        : default_block(r->precision));
@@ -1045,9 +1058,10 @@ int gt_autotune(gt_ctx *ctx, const gt_run *run, const gt_endpoints *out, void *w
     if (n_points) *n_points = n;
     if (top.block == 0) return GT_ERR_UNSUPPORTED;
     const int pi = fp64 ? 0 : 1, mi = r.majorant == GT_MAJORANT_BANDED ? 1 : 0;
-    ctx->tuned_block[pi][ctx->field.kind & 3][mi] = top.block;
-    ctx->tuned_k[pi][ctx->field.kind & 3][mi] = top.refill_period;
-    ctx->tuned_m[pi][ctx->field.kind & 3][mi] = top.flights_per_phase;
+    const int vi = run_variant(ctx, &r);
+    ctx->tuned_block[pi][ctx->field.kind & 3][mi][vi] = top.block;
+    ctx->tuned_k[pi][ctx->field.kind & 3][mi][vi] = top.refill_period;
+    ctx->tuned_m[pi][ctx->field.kind & 3][mi][vi] = top.flights_per_phase;
     *best = top;
     return GT_OK;
 }
