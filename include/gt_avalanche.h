@@ -393,8 +393,8 @@ int gt_graph_destroy(gt_graph *graph);
  * their electron finishes).  gt_autotune runs `run` in GT_BATCHED mode once
  * per candidate shape (after one warm-up run) and measures real collisions
  * per millisecond of transport kernel time (CUDA events).  Candidates:
- * MIXED 512/768/1024 threads x refill period 4/8/16/32 x flights per
- * phase 1/2/4/6 (48); FP64 128/256/512 threads x refill period 8/16/32/64
+ * MIXED 512/768/896/1024 threads x refill period 4/8/16/32 x flights per
+ * phase 1/2/4/6 (64); FP64 128/256/512 threads x refill period 8/16/32/64
  * (12).  The fastest shape is remembered by the context for the run's
  * precision, field kind, majorant and kernel build (the basic gas; a gas
  * with anisotropy, attachment or a sharing law; a run with sub-steps,

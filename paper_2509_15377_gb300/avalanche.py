@@ -256,12 +256,12 @@ def avalanche_run_static(ctx, run: gt_run, out: gt_endpoints, stream_ptr: int,
 def gt_autotune(ctx, run: gt_run, out: gt_endpoints, workspace_ptr: int, workspace_nbytes: int,
                 stream_ptr: int):
     """Measure every candidate launch shape; returns (best, [points])."""
-    pts = (gt_tune_point * 64)()
+    pts = (gt_tune_point * 128)()
     n = C.c_int32()
     best = gt_tune_point()
     _check(load().gt_autotune(ctx, C.byref(run), C.byref(out), workspace_ptr, workspace_nbytes,
-                              stream_ptr, pts, 64, C.byref(n), C.byref(best)), "gt_autotune", ctx)
-    return best.as_dict(), [pts[i].as_dict() for i in range(min(n.value, 64))]
+                              stream_ptr, pts, 128, C.byref(n), C.byref(best)), "gt_autotune", ctx)
+    return best.as_dict(), [pts[i].as_dict() for i in range(min(n.value, 128))]
 
 
 def avalanche_observables(ctx, out: gt_endpoints, n_endpoints: int, n_avalanches: int,

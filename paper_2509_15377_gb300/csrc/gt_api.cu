@@ -1017,7 +1017,7 @@ int gt_autotune(gt_ctx *ctx, const gt_run *run, const gt_endpoints *out, void *w
     r.mode = GT_BATCHED;
     const bool fp64 = r.precision == GT_FP64;
     // candidate shapes: threads per CTA x refill period (x flights per phase)
-    static const int blocks_mixed[] = {512, 768, 1024};
+    static const int blocks_mixed[] = {512, 768, 896, 1024};
     static const int blocks_fp64[] = {128, 256, 512};
     static const int ks_mixed[] = {4, 8, 16, 32};
     static const int ks_fp64[] = {8, 16, 32, 64};
@@ -1026,7 +1026,7 @@ int gt_autotune(gt_ctx *ctx, const gt_run *run, const gt_endpoints *out, void *w
     const int *blocks = fp64 ? blocks_fp64 : blocks_mixed;
     const int *ks = fp64 ? ks_fp64 : ks_mixed;
     const int *ms = fp64 ? ms_fp64 : ms_mixed;
-    const int nb = 3, nk = 4, nm = fp64 ? 1 : 4;
+    const int nb = fp64 ? 3 : 4, nk = 4, nm = fp64 ? 1 : 4;
     gt_stats st{};
     r.block = blocks[0];
     r.refill_period = ks[1];

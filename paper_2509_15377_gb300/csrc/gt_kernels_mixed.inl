@@ -14,7 +14,7 @@
 
 namespace gt {
 
-// The batched kernel is built for three launch bounds: more resident warps
+// The batched kernel is built for four launch bounds: more resident warps
 // per SM against fewer registers per thread (the FP32 table in shared
 // memory limits an SM to one CTA).
 constexpr int kMaxThreadsMixed = 1024;
@@ -35,6 +35,7 @@ static cudaError_t batched(const RunParams &p, int grid, int block, size_t smem,
 {
     if (block <= 512) return batched_t<FK, TAB, 512, PHYS, GEO>(p, grid, block, smem, s);
     if (block <= 768) return batched_t<FK, TAB, 768, PHYS, GEO>(p, grid, block, smem, s);
+    if (block <= 896) return batched_t<FK, TAB, 896, PHYS, GEO>(p, grid, block, smem, s);
     return batched_t<FK, TAB, 1024, PHYS, GEO>(p, grid, block, smem, s);
 }
 
@@ -99,6 +100,9 @@ static cudaError_t configure_mp(size_t max_smem)
     if ((e = allow_dynamic_smem(k_batched<MixedElectron, FK, TAB, 768, MP, PHYS, GEO>, max_smem)) !=
         cudaSuccess)
         return e;
+    if ((e = allow_dynamic_smem(k_batched<MixedElectron, FK, TAB, 896, MP, PHYS, GEO>, max_smem)) !=
+        cudaSuccess)
+        return e;
     return allow_dynamic_smem(k_batched<MixedElectron, FK, TAB, 1024, MP, PHYS, GEO>, max_smem);
 }
 
@@ -141,6 +145,9 @@ static int occ(int block, size_t smem)
     else if (block <= 768)
         e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(
             &n, k_batched<MixedElectron, FK, TAB, 768, 0, PHYS, GEO>, block, smem);
+    else if (block <= 896)
+        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(
+            &n, k_batched<MixedElectron, FK, TAB, 896, 0, PHYS, GEO>, block, smem);
     else
         e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(
             &n, k_batched<MixedElectron, FK, TAB, 1024, 0, PHYS, GEO>, block, smem);
