@@ -657,6 +657,21 @@ __device__ __forceinline__ float ionisation_share32(float w, float rest, float u
     return w <= 0.0f ? u * rest : w * tanf(u * atanf(rest / (2.0f * w)));
 }
 
+// The new electron of an ionisation (mixed precision): its share of the
+// remainder rest = eps - I and its velocity in an isotropic direction, from
+// the collision's second random block.  Returned as (vx, vy, vz, share); out
+// of line, so that the step's inlined code carries one Philox block, not two.
+static __device__ __noinline__ float4 new_electron32(uint64_t seed, int aval, uint64_t uid,
+                                                     uint32_t flight, float rest, float split_w)
+{
+    const uint4 w2 = draw(seed, aval, uid, flight, 1u);
+    const float es = ionisation_share32(split_w, rest, u01f(w2.x));
+    float sx, sy, sz;
+    isotropic32(u01f(w2.y), u01f(w2.z), sx, sy, sz);
+    const float ss = sqrtf(kTwoAccelF * es);
+    return make_float4(ss * sx, ss * sy, ss * sz, es);
+}
+
 // Store the birth record of a new electron in queue slot s: position and
 // time are the parent's at the ionising collision (read from the parent),
 // energy, velocity and id from the child record.
@@ -1526,15 +1541,11 @@ struct MixedElectron {
             float eps_new = fmaxf(eps - tb.thr_f[lvl], 0.0f);
             if (type == GT_LEVEL_IONISATION) {
                 const uint32_t flight = nf - 1u;
-                const uint4 w2 = draw(p.seed, aval, uid, flight, 1u);
-                const float es = PHYS ? ionisation_share32(p.gas.split_w_f, eps_new, u01f(w2.x))
-                                      : u01f(w2.x) * eps_new;
-                eps_new = eps_new - es;
-                float sx, sy, sz;
-                isotropic32(u01f(w2.y), u01f(w2.z), sx, sy, sz);
-                const float ss = sqrtf(kTwoAccelF * es);
-                ch.e = es;
-                ch.vx = ss * sx; ch.vy = ss * sy; ch.vz = ss * sz;
+                const float4 c = new_electron32(p.seed, aval, uid, flight, eps_new,
+                                                PHYS ? p.gas.split_w_f : 0.0f);
+                eps_new = eps_new - c.w;
+                ch.e = c.w;
+                ch.vx = c.x; ch.vy = c.y; ch.vz = c.z;
                 ch.uid = child_uid(uid, flight);
                 ev = EV_CHILD;
             }
