@@ -365,6 +365,7 @@ int gas_table_upload(gt_ctx *ctx, const gt_gas *g)
     }
     d.split_w = g->split_w;
     d.split_w_f = (float)g->split_w;
+    d.level0_elastic = g->level_type[0] == GT_LEVEL_ELASTIC ? 1 : 0;
     d.any_special = d.any_aniso || g->split_w > 0.0;
     for (int j = 0; j < L; ++j)
         if (d.type[j] == GT_LEVEL_ATTACHMENT) d.any_special = 1;

@@ -45,6 +45,7 @@ struct DevGas {
     // (a sparse table: the maximum over any band range is two lookups).
     int n_bands, band_levels;
     int bands_monotone;          // band bounds non-decreasing: the range maximum is the top band's
+    int level0_elastic;          // level 0 is an elastic level
     double inv_band_width;       // 1 / (n d_eps)
     float inv_band_width_f, last_band_f;
     const double *band64;        // [band_levels][n_bands]
@@ -1498,8 +1499,13 @@ struct MixedElectron {
     {
         pd.real = false;
         const float eps = pd.eps;
-        const int lvl = select_below_total32(tb.cum32 + pd.k * tb.stride32, tb.stride32,
-                                             p.gas.n_levels, pd.f, pd.R);
+        const float *c0 = tb.cum32 + pd.k * tb.stride32;
+        // most real collisions are elastic (level 0 when it is the elastic
+        // level): when every colliding lane's R lies below the level-0 sum,
+        // the warp skips the search
+        const bool lvl0 = p.gas.level0_elastic &&
+                          __all_sync(__activemask(), pd.R < fmaf(pd.f, c0[tb.stride32] - c0[0], c0[0]));
+        const int lvl = lvl0 ? 0 : select_below_total32(c0, tb.stride32, p.gas.n_levels, pd.f, pd.R);
         const int type = tb.type[lvl];
         if (type != GT_LEVEL_ELASTIC) {
             const float th = tb.thr_f[lvl];
