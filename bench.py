@@ -36,12 +36,22 @@ WORKLOAD = "plate_batched_4096"
 # Roofline of the batched transport kernel (bound: instruction issue of the
 # SM's ALU/FMA pipes).  Algorithmic work per flight = lane instructions of
 # the straight-line step: ncu smsp__thread_inst_executed.sum / flights on
-# `bench.py --calibrate --steps 1 --block 1024 --refill-period 32
-# --flights-per-phase 1` with the default banded majorant
-# (profiles/k_batched_mixed_plate_batched_4096.md).  Lanes switched off by
-# divergence are not counted, so divergence, stalls and queue work all show
-# as lost efficiency.
-LANE_INST_PER_FLIGHT = 444.1
+# `bench.py --calibrate --steps 1 --block B --refill-period 32
+# --flights-per-phase 1` with the default banded majorant, per launch bound
+# B (the spill code differs; profiles/k_batched_mixed_plate_batched_4096.md).
+# Lanes switched off by divergence are not counted, so divergence, stalls
+# and queue work all show as lost efficiency.
+LANE_INST_PER_FLIGHT_BY_BLOCK = {768: 411.0, 896: 403.8, 1024: 424.8}
+
+
+def lane_inst_per_flight(block: int) -> float:
+    """The calibration of the launch bound a block size runs under."""
+    for bound in sorted(LANE_INST_PER_FLIGHT_BY_BLOCK):
+        if block <= bound:
+            return LANE_INST_PER_FLIGHT_BY_BLOCK[bound]
+    return LANE_INST_PER_FLIGHT_BY_BLOCK[max(LANE_INST_PER_FLIGHT_BY_BLOCK)]
+
+
 SM_COUNT = 152
 ISSUE_PER_SM_PER_CLK = 4       # warp schedulers per SM, one instruction each per clock
 LANES_PER_WARP = 32
@@ -49,7 +59,7 @@ LANES_PER_WARP = 32
 # dram__bytes_write.sum on the 256-avalanche case, divided by its
 # electrons; traffic grows with electrons, so it is scaled to a launch by
 # the electrons the launch stores).  None once the kernel has changed.
-DRAM_BYTES_PER_ELECTRON = 212.8
+DRAM_BYTES_PER_ELECTRON = 202.1
 
 
 # ---------------------------------------------------------------- sharding
@@ -390,7 +400,8 @@ def run_ours(args) -> None:
     peak_clk = clk.get("sm_max_mhz") or 2070.0
     # G lane-instructions/s: SMs x schedulers x lanes x max SM clock
     peak = SM_COUNT * ISSUE_PER_SM_PER_CLK * LANES_PER_WARP * peak_clk * 1e6 / 1e9
-    achieved = LANE_INST_PER_FLIGHT * fl_per_launch / (kms / 1e3) / 1e9
+    lipf = lane_inst_per_flight(stats[-1]["block"])
+    achieved = lipf * fl_per_launch / (kms / 1e3) / 1e9
     electrons_per_launch = statistics.mean(s["n_endpoints"] for s in stats)
     roof = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "Glane-inst/s",
             "frac": achieved / peak,
@@ -399,7 +410,7 @@ def run_ours(args) -> None:
             "traffic_unit": "bytes per launch (ncu, scaled from the 256-avalanche capture)",
             "kernel": "k_batched<MixedElectron, PLATE, smem table>", "kernel_ms": kms,
             "flights_per_launch": fl_per_launch,
-            "lane_inst_per_flight": LANE_INST_PER_FLIGHT,
+            "lane_inst_per_flight": lipf,
             "peak_note": "152 SMs x 4 schedulers x 32 lanes x max SM clock (measured max)",
             "clock_frac": (clk.get("sm_mhz") or peak_clk) / peak_clk}
     line = {
