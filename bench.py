@@ -41,7 +41,7 @@ WORKLOAD = "plate_batched_4096"
 # B (the spill code differs; profiles/k_batched_mixed_plate_batched_4096.md).
 # Lanes switched off by divergence are not counted, so divergence, stalls
 # and queue work all show as lost efficiency.
-LANE_INST_PER_FLIGHT_BY_BLOCK = {768: 411.0, 896: 403.8, 1024: 424.8}
+LANE_INST_PER_FLIGHT_BY_BLOCK = {768: 413.3, 896: 402.1, 1024: 423.8}
 
 
 def lane_inst_per_flight(block: int) -> float:
@@ -59,7 +59,7 @@ LANES_PER_WARP = 32
 # dram__bytes_write.sum on the 256-avalanche case, divided by its
 # electrons; traffic grows with electrons, so it is scaled to a launch by
 # the electrons the launch stores).  None once the kernel has changed.
-DRAM_BYTES_PER_ELECTRON = 202.1
+DRAM_BYTES_PER_ELECTRON = 199.8
 
 
 # ---------------------------------------------------------------- sharding

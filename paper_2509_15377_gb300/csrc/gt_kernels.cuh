@@ -46,6 +46,7 @@ struct BlockState {
     unsigned long long flights, real, nul;
     unsigned long long last_done[32], last_tail[32], t_progress[32];
     unsigned int sleep_ns[32];
+    unsigned long long t_start;  // %globaltimer at the start of the run
 };
 
 template <bool SMEM_TABLE>
@@ -82,7 +83,10 @@ __device__ __forceinline__ Tables stage_tables(const RunParams &p, unsigned char
             s_cum[k * S + j] = p.gas.cum32[i];
         }
     }
-    if (threadIdx.x == 0) bs.flights = bs.real = bs.nul = 0ull;
+    if (threadIdx.x == 0) {
+        bs.flights = bs.real = bs.nul = 0ull;
+        bs.t_start = p.hdr->t_start;
+    }
     if (threadIdx.x < 32) {
         bs.last_done[threadIdx.x] = ~0ull;
         bs.last_tail[threadIdx.x] = ~0ull;
@@ -179,7 +183,7 @@ __device__ __forceinline__ int push_children(const RunParams &p, bool want, cons
         return 1;
     }
     store_birth(p, (int64_t)s, parent, ch);
-    __threadfence();
+    // the release store orders the record's stores before the flag
     st_release_u32(p.ready + s, 1u);
     return 0;
 }
@@ -199,12 +203,12 @@ __global__ void __launch_bounds__(MAXT) k_batched(const RunParams p)
     bool has = false;
     long long ticket = -1;
 
-    for (;;) {
-        // a run-wide abort (time budget or a wait that gave up)
-        unsigned err = 0;
-        if (lane == 0) err = *reinterpret_cast<volatile unsigned *>(&p.hdr->error);
-        if (__shfl_sync(FULL, err, 0) & (ERR_TIMEOUT | ERR_BADARG)) break;
+    // a run whose arguments failed the device checks stops at once
+    unsigned err0 = 0;
+    if (lane == 0) err0 = *reinterpret_cast<volatile unsigned *>(&p.hdr->error);
+    const bool stop0 = (__shfl_sync(FULL, err0, 0) & (ERR_TIMEOUT | ERR_BADARG)) != 0;
 
+    for (; !stop0;) {
         // lanes without an electron take queue tickets: one atomic per warp
         const bool need = !has && ticket < 0;
         const unsigned m = __ballot_sync(FULL, need);
@@ -241,16 +245,19 @@ __global__ void __launch_bounds__(MAXT) k_batched(const RunParams p)
             if (lane == 0) {
                 const unsigned long long d = ld_acquire_u64(&p.hdr->done);
                 const unsigned long long tl = ld_acquire_u64(&p.hdr->tail);
+                const unsigned err = *reinterpret_cast<volatile unsigned *>(&p.hdr->error);
                 const unsigned long long now = globaltimer();
                 if (d == tl) {
                     verdict = 1;
+                } else if (err & (ERR_TIMEOUT | ERR_BADARG)) {
+                    verdict = 2;
                 } else if (d != bs.last_done[wid] || tl != bs.last_tail[wid]) {
                     bs.last_done[wid] = d;
                     bs.last_tail[wid] = tl;
                     bs.t_progress[wid] = now;
                     bs.sleep_ns[wid] = 64u;
                 } else if ((long long)(now - bs.t_progress[wid]) > p.spin_limit_ns ||
-                           (long long)(now - p.hdr->t_start) > p.time_limit_ns) {
+                           (long long)(now - bs.t_start) > p.time_limit_ns) {
                     atomicOr(&p.hdr->error, ERR_TIMEOUT);
                     verdict = 2;
                 }
@@ -315,8 +322,17 @@ __global__ void __launch_bounds__(MAXT) k_batched(const RunParams p)
             __threadfence();
             if (lane == 0) atomicAdd(&p.hdr->done, (unsigned long long)r);
         }
-        if (lane == 0 && (long long)(globaltimer() - p.hdr->t_start) > p.time_limit_ns)
-            atomicOr(&p.hdr->error, ERR_TIMEOUT);
+        // the run-wide checks: the time budget, and an abort from any warp
+        unsigned stop = 0;
+        if (lane == 0) {
+            const unsigned err = *reinterpret_cast<volatile unsigned *>(&p.hdr->error);
+            if ((long long)(globaltimer() - bs.t_start) > p.time_limit_ns) {
+                atomicOr(&p.hdr->error, ERR_TIMEOUT);
+                stop = 1u;
+            }
+            stop |= err & (ERR_TIMEOUT | ERR_BADARG);
+        }
+        if (__shfl_sync(FULL, stop, 0)) break;
     }
     flush_block_stats(p, bs);
 }
