@@ -46,7 +46,11 @@
  *   flight ............. RK4 integration of the Lorentz force; the energy
  *                        ledger (kinetic energy change = field work).
  *   field .............. closed-form coaxial field; trilinear exact on affine
- *                        maps.
+ *                        maps; the tetrahedral mesh: its elements tile the
+ *                        box (volumes, one element per interior point),
+ *                        linear interpolation exact on affine nodal values
+ *                        and equal to the nodal value at a node, a mesh of a
+ *                        constant field transports like the uniform field.
  *   table/selection .... brute-force level frequencies vs rate/nu_max.
  *   transport .......... drift velocity eE/(m nu) and the closed-form
  *                        transverse spread for a constant-rate elastic gas;
@@ -80,7 +84,7 @@ enum {
     OR_CATHODE = 2,      /* plate: z < 0 */
     OR_WIRE = 3,         /* coax / grid: r <= wire radius */
     OR_TUBE = 4,         /* coax: r >= tube radius */
-    OR_OUT_OF_MAP = 5,   /* grid: outside the map box */
+    OR_OUT_OF_MAP = 5,   /* grid: outside the map box; mesh: in no element */
     OR_TIME = 6,         /* time limit reached */
     OR_COLL_LIMIT = 7,   /* real-collision limit reached */
     OR_FLIGHT_LIMIT = 8, /* 2^32-1 flights (counter exhausted) */
@@ -89,7 +93,7 @@ enum {
 
 /* level types: Fig. 2 "Collision is ionisation or attachment?" */
 enum { OR_ELASTIC = 0, OR_EXCITATION = 1, OR_IONISATION = 2, OR_ATTACHMENT = 3 };
-enum { OR_UNIFORM = 0, OR_PLATE = 1, OR_COAX = 2, OR_GRID = 3 };
+enum { OR_UNIFORM = 0, OR_PLATE = 1, OR_COAX = 2, OR_GRID = 3, OR_MESH = 4 };
 
 typedef struct {
     int32_t n_levels;
@@ -114,6 +118,10 @@ typedef struct {
     int32_t nx, ny, nz;        /* GRID nodes */
     double origin[3], spacing[3];
     const float *grid;         /* GRID: host float4 (Ex,Ey,Ez,-) per node, x fastest */
+    int64_t n_mesh_nodes, n_tets;  /* MESH: nodes and tetrahedra */
+    const double *mesh_nodes;  /* MESH: [n_mesh_nodes][3] node positions (cm) */
+    const int32_t *mesh_tets;  /* MESH: [n_tets][4] node indices */
+    const float *mesh_values;  /* MESH: [n_mesh_nodes][4] (Ex, Ey, Ez, weighting potential) */
 } or_field;
 
 typedef struct {
@@ -206,6 +214,64 @@ static void grid_node(const or_field *f, int i, int j, int k, double e[3])
     e[0] = p[0]; e[1] = p[1]; e[2] = p[2];
 }
 
+/* Field maps on a tetrahedral mesh (Sec. 3.1: the field maps are finite-element
+ * solutions on tetrahedral meshes; a point's element is searched, then the
+ * element's nodal values are interpolated).  The element of r is the
+ * lowest-index closed tetrahedron (every barycentric coordinate >= 0) that
+ * contains it, found by trying every element; the barycentric coordinates
+ * come from Cramer's rule on the edge vectors from the element's first
+ * node.  Returns the element, or -1 when r is in none. */
+static double triple(const double a[3], const double b[3], const double c[3])
+{
+    return a[0] * (b[1] * c[2] - b[2] * c[1]) - a[1] * (b[0] * c[2] - b[2] * c[0]) +
+           a[2] * (b[0] * c[1] - b[1] * c[0]);
+}
+
+int64_t or_mesh_locate(const or_field *f, const double r[3], double lam[4])
+{
+    for (int64_t t = 0; t < f->n_tets; ++t) {
+        const int32_t *q = f->mesh_tets + 4 * t;
+        const double *v[4];
+        for (int i = 0; i < 4; ++i) v[i] = f->mesh_nodes + 3 * (int64_t)q[i];
+        int out = 0;
+        for (int d = 0; d < 3 && !out; ++d) {
+            double lo = v[0][d], hi = v[0][d];
+            for (int i = 1; i < 4; ++i) {
+                if (v[i][d] < lo) lo = v[i][d];
+                if (v[i][d] > hi) hi = v[i][d];
+            }
+            out = r[d] < lo || r[d] > hi;
+        }
+        if (out) continue;
+        double e1[3], e2[3], e3[3], dr[3];
+        for (int d = 0; d < 3; ++d) {
+            e1[d] = v[1][d] - v[0][d];
+            e2[d] = v[2][d] - v[0][d];
+            e3[d] = v[3][d] - v[0][d];
+            dr[d] = r[d] - v[0][d];
+        }
+        const double det = triple(e1, e2, e3);
+        const double l1 = triple(dr, e2, e3) / det;
+        const double l2 = triple(e1, dr, e3) / det;
+        const double l3 = triple(e1, e2, dr) / det;
+        const double l0 = 1.0 - l1 - l2 - l3;
+        if (l0 >= 0.0 && l1 >= 0.0 && l2 >= 0.0 && l3 >= 0.0) {
+            lam[0] = l0; lam[1] = l1; lam[2] = l2; lam[3] = l3;
+            return t;
+        }
+    }
+    return -1;
+}
+
+/* Component c of the mesh's nodal values interpolated at r in element t. */
+static double mesh_interp(const or_field *f, int64_t t, const double lam[4], int c)
+{
+    const int32_t *q = f->mesh_tets + 4 * t;
+    double x = 0.0;
+    for (int i = 0; i < 4; ++i) x += lam[i] * (double)f->mesh_values[4 * (int64_t)q[i] + c];
+    return x;
+}
+
 void or_field_eval(const or_field *f, double plate_e, const double r[3], double e[3])
 {
     e[0] = e[1] = e[2] = 0.0;
@@ -219,6 +285,11 @@ void or_field_eval(const or_field *f, double plate_e, const double r[3], double 
         double s = f->voltage / (log(f->tube_r / f->wire_r) * r2);
         e[0] = s * r[0];
         e[1] = s * r[1];
+    } else if (f->kind == OR_MESH) { /* linear interpolation in the element */
+        double lam[4];
+        const int64_t t = or_mesh_locate(f, r, lam);
+        if (t >= 0)
+            for (int c = 0; c < 3; ++c) e[c] = mesh_interp(f, t, lam, c);
     } else { /* OR_GRID: trilinear interpolation of the node values */
         int n[3] = {f->nx, f->ny, f->nz};
         int idx[3];
@@ -263,6 +334,11 @@ int or_boundary(const or_field *f, const double r[3])
             double hi = f->origin[d] + (n[d] - 1) * f->spacing[d];
             if (r[d] < f->origin[d] || r[d] > hi) return OR_OUT_OF_MAP;
         }
+    } else if (f->kind == OR_MESH) {
+        double r2 = r[0] * r[0] + r[1] * r[1];
+        if (f->wire_r > 0.0 && r2 <= f->wire_r * f->wire_r) return OR_WIRE;
+        double lam[4];
+        if (or_mesh_locate(f, r, lam) < 0) return OR_OUT_OF_MAP;
     }
     return 0;
 }
@@ -366,6 +442,15 @@ static double field_emax(const or_field *f)
         }
         return m;
     }
+    if (f->kind == OR_MESH) { /* |E| is convex in an element: its largest value is at a node */
+        double m = 0.0;
+        for (int64_t i = 0; i < f->n_mesh_nodes; ++i) {
+            const float *p = f->mesh_values + 4 * i;
+            double e = sqrt((double)p[0] * p[0] + (double)p[1] * p[1] + (double)p[2] * p[2]);
+            if (e > m) m = e;
+        }
+        return m;
+    }
     return 0.0;
 }
 
@@ -384,6 +469,11 @@ static double weighting_potential(const or_field *f, int kind, const double r[3]
     if (kind == OR_W_COAX) {                        /* wire at r = a, tube at r = b */
         double rr = sqrt(r[0] * r[0] + r[1] * r[1]);
         return log(rr / f->tube_r) / log(f->wire_r / f->tube_r);
+    }
+    if (kind == OR_W_MAP && f->kind == OR_MESH) { /* linear in the element */
+        double lam[4];
+        const int64_t t = or_mesh_locate(f, r, lam);
+        return t >= 0 ? mesh_interp(f, t, lam, 3) : 0.0;
     }
     if (kind == OR_W_MAP) { /* trilinear interpolation of the nodes' 4th component */
         int n[3] = {f->nx, f->ny, f->nz};
@@ -1057,6 +1147,13 @@ int or_run(const or_gas *g, const or_field *f, const or_run_args *a, or_result *
     *res = NULL;
     if (a->n_avalanches < 0 || a->n_primaries < 0) return -3;
     if (f->kind == OR_GRID && (f->nx < 2 || f->ny < 2 || f->nz < 2 || !f->grid)) return -3;
+    if (f->kind == OR_MESH) {
+        if (f->n_tets < 1 || f->n_mesh_nodes < 4 || !f->mesh_nodes || !f->mesh_tets ||
+            !f->mesh_values)
+            return -3;
+        for (int64_t i = 0; i < 4 * f->n_tets; ++i)
+            if (f->mesh_tets[i] < 0 || f->mesh_tets[i] >= f->n_mesh_nodes) return -3;
+    }
     for (int64_t p = 0; p < a->n_primaries; ++p)
         if (a->aval[p] < 0 || a->aval[p] >= a->n_avalanches) return -3;
     if (a->substeps < 0 || a->crossing < 0 || a->crossing > 1) return -3;
@@ -1064,8 +1161,9 @@ int or_run(const or_gas *g, const or_field *f, const or_run_args *a, or_result *
     if (a->signal_kind != OR_W_NONE &&
         (a->signal_bins < 0 || !(a->signal_dt > 0.0) || !isfinite(a->signal_t0) ||
          (a->signal_kind == OR_W_PLATE && f->kind != OR_PLATE) ||
-         (a->signal_kind == OR_W_COAX && f->kind != OR_COAX && f->kind != OR_GRID) ||
-         (a->signal_kind == OR_W_MAP && f->kind != OR_GRID)))
+         (a->signal_kind == OR_W_COAX && f->kind != OR_COAX && f->kind != OR_GRID &&
+          f->kind != OR_MESH) ||
+         (a->signal_kind == OR_W_MAP && f->kind != OR_GRID && f->kind != OR_MESH)))
         return -3;
     or_table tb;
     if (table_build(g, &tb)) return -2;

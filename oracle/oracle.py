@@ -24,7 +24,7 @@ _lock = threading.Lock()
 _lib = None
 
 __all__ = ["build", "philox4x32_10", "splitmix64_mix", "child_uid", "flight", "elastic", "field_eval",
-           "boundary", "select", "majorant", "scatter", "ionisation_share",
+           "boundary", "mesh_locate", "select", "majorant", "scatter", "ionisation_share",
            "weighting_potential", "run",
            "default_threads"]
 
@@ -52,7 +52,9 @@ class _Field(C.Structure):
     _fields_ = [("kind", C.c_int32), ("e0", C.c_double), ("gap", C.c_double),
                 ("wire_r", C.c_double), ("tube_r", C.c_double), ("voltage", C.c_double),
                 ("b", C.c_double * 3), ("nx", C.c_int32), ("ny", C.c_int32), ("nz", C.c_int32),
-                ("origin", C.c_double * 3), ("spacing", C.c_double * 3), ("grid", C.c_void_p)]
+                ("origin", C.c_double * 3), ("spacing", C.c_double * 3), ("grid", C.c_void_p),
+                ("n_mesh_nodes", C.c_int64), ("n_tets", C.c_int64), ("mesh_nodes", C.c_void_p),
+                ("mesh_tets", C.c_void_p), ("mesh_values", C.c_void_p)]
 
 
 class _Run(C.Structure):
@@ -92,6 +94,8 @@ def _load():
             lib.or_field_eval.restype = None
             lib.or_boundary.argtypes = [C.POINTER(_Field), C.c_void_p]
             lib.or_boundary.restype = C.c_int
+            lib.or_mesh_locate.argtypes = [C.POINTER(_Field), C.c_void_p, C.c_void_p]
+            lib.or_mesh_locate.restype = C.c_int64
             lib.or_select.argtypes = [C.POINTER(_Gas), C.c_double, C.c_double,
                                       C.POINTER(C.c_double)]
             lib.or_select.restype = C.c_int
@@ -150,6 +154,13 @@ def _field_struct(field, keep):
         keep.append(g)
         f.nz, f.ny, f.nx = g.shape[0], g.shape[1], g.shape[2]
         f.grid = _ptr(g).value
+    if getattr(field, "mesh_tets", None) is not None:
+        nodes = np.ascontiguousarray(field.mesh_nodes, np.float64)
+        tets = np.ascontiguousarray(field.mesh_tets, np.int32)
+        vals = np.ascontiguousarray(field.mesh_values, np.float32)
+        keep.extend([nodes, tets, vals])
+        f.n_mesh_nodes, f.n_tets = nodes.shape[0], tets.shape[0]
+        f.mesh_nodes, f.mesh_tets, f.mesh_values = _ptr(nodes).value, _ptr(tets).value, _ptr(vals).value
     return f
 
 
@@ -238,6 +249,17 @@ def select(gas, eps: float, u1: float):
     if j == -2:
         raise ValueError("bad gas table")
     return j, nm.value
+
+
+def mesh_locate(field, r):
+    """Element of a tetrahedral-mesh field that holds r (the lowest index,
+    -1 for none) and r's barycentric coordinates in it."""
+    keep = []
+    f = _field_struct(field, keep)
+    r = np.ascontiguousarray(r, np.float64)
+    lam = np.zeros(4, np.float64)
+    t = _load().or_mesh_locate(C.byref(f), _ptr(r), _ptr(lam))
+    return int(t), lam
 
 
 def weighting_potential(field, kind: int, r) -> float:

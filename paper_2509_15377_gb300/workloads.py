@@ -24,7 +24,7 @@ import numpy as np
 # Level kinds of a gas table (interface values of the C ABI).
 ELASTIC, EXCITATION, IONISATION, ATTACHMENT = 0, 1, 2, 3
 # Field kinds (interface values of the C ABI).
-UNIFORM, PLATE, COAX, GRID = 0, 1, 2, 3
+UNIFORM, PLATE, COAX, GRID, MESH = 0, 1, 2, 3, 4
 # Electron status codes written to the endpoints (non-zero = finished).
 STATUS_NAMES = {
     0: "active", 1: "anode", 2: "cathode", 3: "wire", 4: "tube",
@@ -81,6 +81,9 @@ class Field:
     grid: Optional[np.ndarray] = None   # GRID float32 [nz, ny, nx, 4]
     origin: tuple = (0.0, 0.0, 0.0)
     spacing: tuple = (1.0, 1.0, 1.0)
+    mesh_nodes: Optional[np.ndarray] = None   # MESH float64 [n, 3] node positions (cm)
+    mesh_tets: Optional[np.ndarray] = None    # MESH int32 [m, 4] node indices
+    mesh_values: Optional[np.ndarray] = None  # MESH float32 [n, 4] (Ex, Ey, Ez, weighting potential)
 
 
 @dataclasses.dataclass
@@ -283,6 +286,95 @@ def coax_grid_map(n: int = 256, half_width: float = 0.15, length: float = 1.0,
     sp = 2.0 * half_width / (n - 1)
     return Field(GRID, wire_r=wire_r, tube_r=tube_r, voltage=voltage, grid=np.ascontiguousarray(grid),
                  origin=(-half_width, -half_width, 0.0), spacing=(sp, sp, length / (n - 1)))
+
+
+# The six tetrahedra of a cube that share its main diagonal, corner c = the
+# bits (x, y, z): one per order in which the three axes are stepped from
+# corner 0 to corner 7.  Every cube cut the same way gives a conforming mesh.
+_CUBE_TETS = ((0, 1, 3, 7), (0, 1, 5, 7), (0, 2, 3, 7), (0, 2, 6, 7), (0, 4, 5, 7), (0, 4, 6, 7))
+
+
+def box_mesh(cells, lo, hi, jitter: float = 0.15, seed: int = 0):
+    """A synthetic FEM-like tetrahedral mesh of the box [lo, hi]: a lattice of
+    cells[0] x cells[1] x cells[2] cubes, each cut into six tetrahedra, with
+    every node moved by up to `jitter` lattice spacings along each axis in
+    which it is not on the box's surface (the box faces stay planar).
+    Returns (nodes float64 [n, 3], tets int32 [m, 4]), every tetrahedron
+    positively oriented."""
+    cells = tuple(int(c) for c in cells)
+    lo = np.asarray(lo, np.float64)
+    hi = np.asarray(hi, np.float64)
+    rng = np.random.default_rng(seed)
+    axes = [np.linspace(lo[d], hi[d], cells[d] + 1) for d in range(3)]
+    I, J, K = np.meshgrid(np.arange(cells[0] + 1), np.arange(cells[1] + 1), np.arange(cells[2] + 1),
+                          indexing="ij")
+    idx = np.stack([I.ravel(), J.ravel(), K.ravel()], axis=1)
+    nodes = np.stack([axes[d][idx[:, d]] for d in range(3)], axis=1)
+    h = (hi - lo) / np.asarray(cells, np.float64)
+    for d in range(3):
+        inner = (idx[:, d] > 0) & (idx[:, d] < cells[d])
+        nodes[inner, d] += rng.uniform(-jitter, jitter, int(inner.sum())) * h[d]
+
+    def node(i, j, k):
+        return (i * (cells[1] + 1) + j) * (cells[2] + 1) + k
+
+    ci, cj, ck = np.meshgrid(np.arange(cells[0]), np.arange(cells[1]), np.arange(cells[2]),
+                             indexing="ij")
+    ci, cj, ck = ci.ravel(), cj.ravel(), ck.ravel()
+    corner = np.stack([node(ci + (c & 1), cj + ((c >> 1) & 1), ck + ((c >> 2) & 1))
+                       for c in range(8)], axis=1)
+    tets = np.concatenate([corner[:, list(t)] for t in _CUBE_TETS], axis=0).astype(np.int32)
+    v = nodes[tets]
+    det = np.einsum("ij,ij->i", v[:, 1] - v[:, 0], np.cross(v[:, 2] - v[:, 0], v[:, 3] - v[:, 0]))
+    flip = det < 0
+    tets[flip, 2], tets[flip, 3] = tets[flip, 3].copy(), tets[flip, 2].copy()
+    if np.min(np.abs(det)) <= 0.05 * float(np.prod(h)):
+        raise ValueError("jitter too large: a tetrahedron is nearly flat")
+    return nodes, tets
+
+
+def coax_mesh_map(cells: int = 8, half_width: float = 0.15, length: float = 1.0,
+                  jitter: float = 0.15, wire_r: float = 25e-4, tube_r: float = 0.5,
+                  voltage: float = 1500.0, seed: int = 0) -> Field:
+    """The coaxial field on a jittered tetrahedral mesh of [-w, w]^2 x
+    [0, length] (cells^3 cubes, six tetrahedra each), sampled at the nodes
+    as coax_grid_map samples its grid (r clamped at the wire radius); the
+    4th nodal value is the wire's weighting potential."""
+    nodes, tets = box_mesh((cells, cells, cells), (-half_width, -half_width, 0.0),
+                           (half_width, half_width, length), jitter, seed)
+    x, y = nodes[:, 0], nodes[:, 1]
+    r2 = np.maximum(x * x + y * y, wire_r * wire_r)
+    s = voltage / (math.log(tube_r / wire_r) * r2)
+    vals = np.zeros((nodes.shape[0], 4), np.float32)
+    vals[:, 0] = s * x
+    vals[:, 1] = s * y
+    vals[:, 3] = np.log(np.sqrt(r2) / tube_r) / math.log(wire_r / tube_r)
+    return Field(MESH, wire_r=wire_r, tube_r=tube_r, voltage=voltage, mesh_nodes=nodes,
+                 mesh_tets=tets, mesh_values=vals)
+
+
+def uniform_mesh_map(e0: float, half_width: float, cells: int = 6, jitter: float = 0.15,
+                     seed: int = 0) -> Field:
+    """E = (0, 0, -e0) given at the nodes of a jittered tetrahedral mesh of
+    the cube [-w, w]^3: inside it the same field as Field(UNIFORM, e0)."""
+    nodes, tets = box_mesh((cells, cells, cells), (-half_width,) * 3, (half_width,) * 3, jitter, seed)
+    vals = np.zeros((nodes.shape[0], 4), np.float32)
+    vals[:, 2] = -e0
+    return Field(MESH, mesh_nodes=nodes, mesh_tets=tets, mesh_values=vals)
+
+
+def mesh_coax(n_avalanches: int = 64, cells: int = 8, voltage: float = 1810.0,
+              r_start: float = 0.1, k_exc: float = ARGON_LIKE_K_EXC, t_max: float = 1000.0,
+              seed: int = 0) -> Workload:
+    """The grid workload's geometry on a tetrahedral mesh: coax field sampled
+    at the nodes of a jittered mesh of the map box; one primary per
+    avalanche at r = r_start, random phi, mid-length."""
+    rng = np.random.default_rng(seed)
+    phi = rng.uniform(0.0, 2.0 * math.pi, n_avalanches)
+    f = coax_mesh_map(cells=cells, voltage=voltage, seed=seed)
+    prim = _primaries(rng, r_start * np.cos(phi), r_start * np.sin(phi),
+                      np.full(n_avalanches, 0.5), np.arange(n_avalanches), n_avalanches)
+    return Workload("mesh_coax", argon_like_gas(k_exc), f, prim, t_max, 0, seed)
 
 
 def grid_stress(n_avalanches: int = 256, n: int = 256, voltage: float = 1810.0,
