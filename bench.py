@@ -361,6 +361,42 @@ def run_ours(args) -> None:
                               "note": "basic gas, Shockley-Ramo anode signal per avalanche, "
                                       "2000 bins x 0.05 ns"}
 
+    # field maps of the coax geometry (the grid workload's box, 1810 V, one
+    # primary at r = 1 mm per avalanche): the regular 256^3 grid and a
+    # tetrahedral mesh of the same box (48^3 jittered cubes, six elements
+    # each), 64 avalanches, batched mixed, each kernel autotuned
+    maps = None
+    if rank == 0 and not args.no_plain:
+        maps = {}
+        for name, wl in (("grid", W.grid_stress(n_avalanches=64, n=256, seed=seed)),
+                         ("mesh", W.mesh_coax(n_avalanches=64, cells=48, seed=seed))):
+            av.set_gas(wl.gas)
+            av.set_field(wl.field)
+            m_opt = A.RunOptions(seed=seed, t_max=wl.t_max, precision=A.GT_MIXED,
+                                 mode=A.GT_BATCHED, majorant=majorant, majorant_window=args.window)
+            m_dev = av.primaries_device(wl.primaries)
+            if not args.no_autotune:
+                av.autotune(av.primaries_device(wl.primaries.subset(list(range(16)))), m_opt, cap,
+                            stream=stream)
+            m_real, m_ms, m_fl = 0, 0.0, 0
+            for _ in range(2):
+                flush.fill_(1)
+                m_st = av.run(m_dev, m_opt, cap, stream=stream, allow=(A.GT_OK,))
+                m_real += m_st["real_collisions"]
+                m_ms += m_st["transport_ms"]
+                m_fl += m_st["flights"]
+            maps[name] = {"value_kernel_time": m_real / (m_ms / 1e3), "unit": UNIT,
+                          "flights_per_real": m_fl / max(m_real, 1),
+                          "electrons_per_avalanche": m_st["n_endpoints"] / 64.0,
+                          "shape": [m_st["block"], m_st["refill_period"], m_st["flights_per_phase"]]}
+            if name == "grid":
+                maps[name]["map"] = "256^3 float4 nodes, trilinear"
+            else:
+                maps[name]["map"] = (f"{wl.field.mesh_tets.shape[0]} tetrahedra, "
+                                     f"{wl.field.mesh_nodes.shape[0]} nodes, linear")
+        av.set_gas(w.gas)
+        av.set_field(w.field)
+
     # plain FP64 GPU path (the paper's structure: one avalanche at a time, one
     # launch per generation) on a sample, with both majorants
     plain = None
@@ -439,6 +475,7 @@ def run_ours(args) -> None:
         "plain_fp64": plain,
         "speedup_vs_plain_fp64": (value / plain["value"]) if plain else None,
         "physical_gas": physical,
+        "field_maps": maps,
         "roofline": roof,
         "cpu_baseline": cpu,
         "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": h2d,

@@ -42,7 +42,7 @@
 extern "C" {
 #endif
 
-#define GT_ABI_VERSION 2
+#define GT_ABI_VERSION 3
 #define GT_MAX_LEVELS 32 /* collision levels per gas table */
 
 /* ---- return codes ---------------------------------------------------- */
@@ -62,9 +62,9 @@ extern "C" {
 #define GT_ST_ACTIVE 0        /* not finished (only in a partial result) */
 #define GT_ST_ANODE 1         /* PLATE: z >= gap */
 #define GT_ST_CATHODE 2       /* PLATE: z < 0 */
-#define GT_ST_WIRE 3          /* COAX/GRID: x^2 + y^2 <= wire_r^2 */
+#define GT_ST_WIRE 3          /* COAX/GRID/MESH: x^2 + y^2 <= wire_r^2 */
 #define GT_ST_TUBE 4          /* COAX: x^2 + y^2 >= tube_r^2 */
-#define GT_ST_OUT_OF_MAP 5    /* GRID: outside the map box */
+#define GT_ST_OUT_OF_MAP 5    /* GRID: outside the map box; MESH: in no element */
 #define GT_ST_TIME 6          /* reached t_max */
 #define GT_ST_COLL_LIMIT 7    /* reached coll_limit real collisions */
 #define GT_ST_FLIGHT_LIMIT 8  /* 2^32 - 1 flights */
@@ -83,6 +83,7 @@ extern "C" {
 #define GT_FIELD_PLATE 1   /* E = (0, 0, -E_k) between z = 0 and z = gap */
 #define GT_FIELD_COAX 2    /* E = V / (r ln(b/a)) r-hat, wire radius a, tube b */
 #define GT_FIELD_GRID 3    /* trilinear interpolation of a regular float4 map */
+#define GT_FIELD_MESH 4    /* linear interpolation on a tetrahedral mesh (FEM-like map) */
 
 #define GT_FP64 0  /* every step in FP64 */
 #define GT_MIXED 1 /* FP32 kinematics, table and scattering; FP64 position and
@@ -143,6 +144,22 @@ typedef struct {
     const float *grid;         /* GRID device [nz][ny][nx] float4 (Ex, Ey, Ez, -),
                                   16-byte aligned; kept by pointer, must stay
                                   valid while runs use this field */
+    /* MESH (Sec. 3.1: field maps are finite-element solutions on tetrahedral
+     * meshes, searched for the element of a point).  Host arrays, copied by
+     * field_setup (the caller keeps ownership and may free them after the
+     * call).  A point's element is a closed tetrahedron that holds it (every
+     * barycentric coordinate >= 0); the field and the weighting potential are
+     * interpolated linearly from the element's four nodes.  A point in no
+     * element is out of the map (GT_ST_OUT_OF_MAP); wire_r > 0 adds the wire
+     * test of GRID.  Every element must have a non-zero volume.  field_setup
+     * builds the element records and a uniform bin structure over the mesh's
+     * box for the element search. */
+    int64_t n_mesh_nodes;      /* MESH nodes, >= 4 */
+    int64_t n_tets;            /* MESH elements, 1 .. 2^26 */
+    const double *mesh_nodes;  /* MESH host [n_mesh_nodes][3] positions (cm) */
+    const int32_t *mesh_tets;  /* MESH host [n_tets][4] node indices */
+    const float *mesh_values;  /* MESH host [n_mesh_nodes][4] (Ex, Ey, Ez, weighting
+                                  potential) at the nodes (V/cm; 1) */
 } gt_field;
 
 /* ---- one run --------------------------------------------------------- */
@@ -211,8 +228,9 @@ typedef struct {
 /* Readout electrodes for induced signals (their weighting potentials). */
 #define GT_W_NONE 0
 #define GT_W_PLATE 1 /* PLATE anode: phi_w = z / gap */
-#define GT_W_COAX 2  /* COAX (or GRID) wire: phi_w = ln(r / tube_r) / ln(wire_r / tube_r) */
-#define GT_W_MAP 3   /* GRID: trilinear interpolation of the map's 4th component */
+#define GT_W_COAX 2  /* COAX (or GRID, MESH) wire: phi_w = ln(r / tube_r) / ln(wire_r / tube_r) */
+#define GT_W_MAP 3   /* GRID: trilinear interpolation of the map's 4th component; MESH: the
+                        nodes' 4th value, linear in the element */
 
 /* Majorant of the null-collision flights.
  * GLOBAL: dt = -ln(u)/nu_max with one nu_max for all energies (Skullerud).

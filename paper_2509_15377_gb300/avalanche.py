@@ -30,7 +30,7 @@ GT_BATCHED, GT_PLAIN = 0, 1
 GT_DEBUG_UNFILLED_SLOT = 1
 GT_MAJORANT_GLOBAL, GT_MAJORANT_BANDED = 0, 1
 GT_OBS_COUNT = 8
-GT_ABI_VERSION = 2
+GT_ABI_VERSION = 3
 PARTIAL_OK = (GT_OK, GT_ERR_QUEUE_OVERFLOW, GT_ERR_TIMEOUT)
 
 
@@ -52,7 +52,9 @@ class gt_field(C.Structure):
     _fields_ = [("kind", C.c_int32), ("e0", C.c_double), ("gap", C.c_double),
                 ("wire_r", C.c_double), ("tube_r", C.c_double), ("voltage", C.c_double),
                 ("b", C.c_double * 3), ("nx", C.c_int32), ("ny", C.c_int32), ("nz", C.c_int32),
-                ("origin", C.c_double * 3), ("spacing", C.c_double * 3), ("grid", C.c_void_p)]
+                ("origin", C.c_double * 3), ("spacing", C.c_double * 3), ("grid", C.c_void_p),
+                ("n_mesh_nodes", C.c_int64), ("n_tets", C.c_int64), ("mesh_nodes", C.c_void_p),
+                ("mesh_tets", C.c_void_p), ("mesh_values", C.c_void_p)]
 
 
 class gt_run(C.Structure):
@@ -217,6 +219,15 @@ def field_setup(ctx, field: W.Field, grid_ptr: int = 0) -> None:
     if field.kind == W.GRID:
         f.nz, f.ny, f.nx = field.grid.shape[:3]
         f.grid = grid_ptr
+    keep = []
+    if field.kind == W.MESH:
+        nodes = np.ascontiguousarray(field.mesh_nodes, np.float64)
+        tets = np.ascontiguousarray(field.mesh_tets, np.int32)
+        vals = np.ascontiguousarray(field.mesh_values, np.float32)
+        keep.extend([nodes, tets, vals])  # host arrays, copied by field_setup
+        f.n_mesh_nodes, f.n_tets = nodes.shape[0], tets.shape[0]
+        f.mesh_nodes, f.mesh_tets, f.mesh_values = (nodes.ctypes.data, tets.ctypes.data,
+                                                    vals.ctypes.data)
     _check(load().field_setup(ctx, C.byref(f)), "field_setup", ctx)
 
 

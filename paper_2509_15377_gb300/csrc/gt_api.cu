@@ -37,9 +37,13 @@ struct gt_ctx {
     // autotuned launch shapes per [precision][field kind][majorant]
     // [precision][field kind][majorant][kernel build: basic, general gas,
     // sub-steps/crossings/signals]
-    int tuned_block[2][4][2][3] = {};
-    int tuned_k[2][4][2][3] = {};
-    int tuned_m[2][4][2][3] = {};
+    int tuned_block[2][5][2][3] = {};
+    int tuned_k[2][5][2][3] = {};
+    int tuned_m[2][5][2][3] = {};
+    // MESH field: element records and search bins (device, owned)
+    float *d_tet32 = nullptr;
+    double *d_tet64 = nullptr;
+    int *d_bin_start = nullptr, *d_bin_tets = nullptr;
     char last_error[256] = {0};
 };
 
@@ -230,6 +234,10 @@ int gt_destroy(gt_ctx *ctx)
         if (ctx->d_band32) cudaFree(ctx->d_band32);
         if (ctx->d_obs_counts) cudaFree(ctx->d_obs_counts);
         if (ctx->d_obs_partials) cudaFree(ctx->d_obs_partials);
+        if (ctx->d_tet32) cudaFree(ctx->d_tet32);
+        if (ctx->d_tet64) cudaFree(ctx->d_tet64);
+        if (ctx->d_bin_start) cudaFree(ctx->d_bin_start);
+        if (ctx->d_bin_tets) cudaFree(ctx->d_bin_tets);
         if (ctx->ev0) cudaEventDestroy(ctx->ev0);
         if (ctx->ev1) cudaEventDestroy(ctx->ev1);
         if (ctx->h_hdr) cudaFreeHost(ctx->h_hdr);
@@ -381,6 +389,209 @@ int gt_gas_nu_max(gt_ctx *ctx, double *nu_max)
     return GT_OK;
 }
 
+// MESH: element records (the layout the device reads, see kMeshRec) and a
+// uniform grid of bins over the mesh's box, each listing, in ascending
+// order, the elements whose bounding box (padded by a hair) meets it.
+// Built on the host once per field, then copied to the device.
+static int build_mesh(gt_ctx *ctx, const gt_field *f, DevField &d)
+{
+    const int64_t nn = f->n_mesh_nodes, nt = f->n_tets;
+    if (nn < 4 || nt < 1 || nt > ((int64_t)1 << 26) || nn > ((int64_t)1 << 30) ||
+        !f->mesh_nodes || !f->mesh_tets || !f->mesh_values || !(f->wire_r >= 0.0) ||
+        !std::isfinite(f->wire_r))
+        return GT_ERR_ARG;
+    double lo[3], hi[3];
+    for (int k = 0; k < 3; ++k) {
+        lo[k] = INFINITY;
+        hi[k] = -INFINITY;
+    }
+    double emax = 0.0;
+    for (int64_t i = 0; i < nn; ++i) {
+        for (int k = 0; k < 3; ++k) {
+            const double x = f->mesh_nodes[3 * i + k];
+            if (!std::isfinite(x)) return GT_ERR_ARG;
+            lo[k] = std::min(lo[k], x);
+            hi[k] = std::max(hi[k], x);
+        }
+        const float *v = f->mesh_values + 4 * i;
+        for (int k = 0; k < 4; ++k)
+            if (!std::isfinite(v[k])) return GT_ERR_ARG;
+        emax = std::max(emax, std::sqrt((double)v[0] * v[0] + (double)v[1] * v[1] +
+                                        (double)v[2] * v[2]));
+    }
+    double ext[3], mean_ext[3] = {0.0, 0.0, 0.0}, rmax = 0.0, mnorm = 0.0;
+    for (int k = 0; k < 3; ++k) {
+        ext[k] = hi[k] - lo[k];
+        if (!(ext[k] > 0.0)) return GT_ERR_ARG;
+        rmax = std::max(rmax, std::max(std::fabs(lo[k]), std::fabs(hi[k])));
+    }
+    std::vector<double> rec(kMeshRec * (size_t)nt, 0.0);
+    std::vector<double> box(6 * (size_t)nt);
+    for (int64_t t = 0; t < nt; ++t) {
+        const int32_t *q = f->mesh_tets + 4 * t;
+        const double *v[4];
+        const float *val[4];
+        for (int i = 0; i < 4; ++i) {
+            if (q[i] < 0 || q[i] >= nn) return GT_ERR_ARG;
+            v[i] = f->mesh_nodes + 3 * (int64_t)q[i];
+            val[i] = f->mesh_values + 4 * (int64_t)q[i];
+        }
+        double e[3][3], len = 0.0;
+        for (int i = 0; i < 3; ++i)
+            for (int k = 0; k < 3; ++k) {
+                e[i][k] = v[i + 1][k] - v[0][k];
+                len = std::max(len, std::fabs(e[i][k]));
+            }
+        // rows of the inverse of [e0 e1 e2] (columns): (e1 x e2, e2 x e0, e0 x e1) / det
+        double c[3][3];
+        for (int i = 0; i < 3; ++i) {
+            const double *a = e[(i + 1) % 3], *b = e[(i + 2) % 3];
+            c[i][0] = a[1] * b[2] - a[2] * b[1];
+            c[i][1] = a[2] * b[0] - a[0] * b[2];
+            c[i][2] = a[0] * b[1] - a[1] * b[0];
+        }
+        const double det = e[0][0] * c[0][0] + e[0][1] * c[0][1] + e[0][2] * c[0][2];
+        if (!(std::fabs(det) > 1e-12 * len * len * len)) return GT_ERR_ARG;
+        double *r = rec.data() + kMeshRec * t;
+        for (int k = 0; k < 3; ++k) r[k] = v[0][k];
+        double m[3][3];
+        for (int i = 0; i < 3; ++i) {
+            double rowsum = 0.0;
+            for (int k = 0; k < 3; ++k) {
+                m[i][k] = c[i][k] / det;
+                r[4 + 4 * i + k] = m[i][k];
+                rowsum += std::fabs(m[i][k]);
+            }
+            mnorm = std::max(mnorm, rowsum);
+        }
+        // value at v0 and gradient of each component: sum_i (V_{i+1} - V_0) M_row_i
+        for (int comp = 0; comp < 4; ++comp) {
+            double g[3] = {0.0, 0.0, 0.0};
+            for (int i = 0; i < 3; ++i) {
+                const double dv = (double)val[i + 1][comp] - (double)val[0][comp];
+                for (int k = 0; k < 3; ++k) g[k] += dv * m[i][k];
+            }
+            r[16 + comp] = (double)val[0][comp];
+            if (comp < 3) {
+                for (int k = 0; k < 3; ++k) r[20 + 4 * comp + k] = g[k];
+            } else {
+                for (int k = 0; k < 3; ++k) r[20 + 4 * k + 3] = g[k];
+            }
+        }
+        for (int k = 0; k < 3; ++k) {
+            double a = v[0][k], b = v[0][k];
+            for (int i = 1; i < 4; ++i) {
+                a = std::min(a, v[i][k]);
+                b = std::max(b, v[i][k]);
+            }
+            box[6 * t + k] = a;
+            box[6 * t + 3 + k] = b;
+            mean_ext[k] += (b - a) / (double)nt;
+        }
+    }
+    // bins about half an element's extent per axis, at most 2^24 in all
+    int nb[3];
+    double total = 1.0;
+    for (int k = 0; k < 3; ++k) {
+        const double want = mean_ext[k] > 0.0 ? 2.0 * ext[k] / mean_ext[k] : 1.0;
+        nb[k] = (int)std::min(std::max(std::ceil(want), 1.0), 1024.0);
+        total *= nb[k];
+    }
+    while (total > (double)(1 << 24)) {
+        total = 1.0;
+        for (int k = 0; k < 3; ++k) {
+            nb[k] = std::max(1, nb[k] / 2);
+            total *= nb[k];
+        }
+    }
+    const int64_t ncell = (int64_t)nb[0] * nb[1] * nb[2];
+    double h[3], inv[3];
+    for (int k = 0; k < 3; ++k) {
+        h[k] = ext[k] / nb[k];
+        inv[k] = nb[k] / ext[k];
+    }
+    std::vector<int64_t> count(ncell + 1, 0);
+    auto range = [&](int64_t t, int k, int &i0, int &i1) {
+        const double pad = 1e-6 * h[k];
+        i0 = (int)std::floor((box[6 * t + k] - pad - lo[k]) * inv[k]);
+        i1 = (int)std::floor((box[6 * t + 3 + k] + pad - lo[k]) * inv[k]);
+        i0 = std::min(std::max(i0, 0), nb[k] - 1);
+        i1 = std::min(std::max(i1, 0), nb[k] - 1);
+    };
+    for (int pass = 0; pass < 2; ++pass) {
+        if (pass == 1) {
+            for (int64_t c = 0; c < ncell; ++c) count[c + 1] += count[c];
+            if (count[ncell] > (int64_t)INT32_MAX) return GT_ERR_ARG;
+        }
+        std::vector<int64_t> next(pass == 1 ? count.begin() : count.end(), count.end());
+        std::vector<int> tets(pass == 1 ? (size_t)count[ncell] : 0);
+        for (int64_t t = 0; t < nt; ++t) {
+            int a[3], b[3];
+            for (int k = 0; k < 3; ++k) range(t, k, a[k], b[k]);
+            for (int z = a[2]; z <= b[2]; ++z)
+                for (int y = a[1]; y <= b[1]; ++y)
+                    for (int x = a[0]; x <= b[0]; ++x) {
+                        const int64_t c = ((int64_t)z * nb[1] + y) * nb[0] + x;
+                        if (pass == 0)
+                            ++count[c + 1];
+                        else
+                            tets[next[c]++] = (int)t;
+                    }
+        }
+        if (pass == 1) {
+            std::vector<int> start(ncell + 1);
+            for (int64_t c = 0; c <= ncell; ++c) start[c] = (int)count[c];
+            std::vector<float> rec32(rec.size());
+            for (size_t i = 0; i < rec.size(); ++i) rec32[i] = (float)rec[i];
+            DeviceGuard dg(ctx->device);
+            if (!dg.ok) return GT_ERR_CUDA;
+            if (ctx->d_tet32) cudaFree(ctx->d_tet32);
+            if (ctx->d_tet64) cudaFree(ctx->d_tet64);
+            if (ctx->d_bin_start) cudaFree(ctx->d_bin_start);
+            if (ctx->d_bin_tets) cudaFree(ctx->d_bin_tets);
+            ctx->d_tet32 = nullptr; ctx->d_tet64 = nullptr;
+            ctx->d_bin_start = nullptr; ctx->d_bin_tets = nullptr;
+            GT_CUDA(ctx, cudaMalloc((void **)&ctx->d_tet32, sizeof(float) * rec32.size()));
+            GT_CUDA(ctx, cudaMalloc((void **)&ctx->d_tet64, sizeof(double) * rec.size()));
+            GT_CUDA(ctx, cudaMalloc((void **)&ctx->d_bin_start, sizeof(int) * start.size()));
+            GT_CUDA(ctx, cudaMalloc((void **)&ctx->d_bin_tets,
+                                    sizeof(int) * std::max<size_t>(tets.size(), 1)));
+            GT_CUDA(ctx, cudaMemcpy(ctx->d_tet32, rec32.data(), sizeof(float) * rec32.size(),
+                                    cudaMemcpyHostToDevice));
+            GT_CUDA(ctx, cudaMemcpy(ctx->d_tet64, rec.data(), sizeof(double) * rec.size(),
+                                    cudaMemcpyHostToDevice));
+            GT_CUDA(ctx, cudaMemcpy(ctx->d_bin_start, start.data(), sizeof(int) * start.size(),
+                                    cudaMemcpyHostToDevice));
+            if (!tets.empty())
+                GT_CUDA(ctx, cudaMemcpy(ctx->d_bin_tets, tets.data(), sizeof(int) * tets.size(),
+                                        cudaMemcpyHostToDevice));
+        }
+    }
+    d.tet32 = reinterpret_cast<const float4 *>(ctx->d_tet32);
+    d.tet64 = ctx->d_tet64;
+    d.bin_start = ctx->d_bin_start;
+    d.bin_tets = ctx->d_bin_tets;
+    for (int k = 0; k < 3; ++k) {
+        d.origin[k] = lo[k];
+        d.hi[k] = hi[k];
+        d.bin_n[k] = nb[k];
+        d.bin_lo[k] = lo[k];
+        d.bin_inv[k] = inv[k];
+        d.bin_lo_f[k] = (float)lo[k];
+        d.bin_inv_f[k] = (float)inv[k];
+    }
+    // FP32 rounding of the position, the node and the record bound the
+    // error of an FP32 barycentric coordinate; 16x that is a sure margin
+    d.mesh_tol_f = (float)(16.0 * 1.1920928955078125e-7 * (1.0 + 2.0 * mnorm * rmax));
+    d.wire_r2 = f->wire_r * f->wire_r;
+    if (f->wire_r > 0.0 && f->tube_r > f->wire_r) {
+        d.ln_tube = std::log(f->tube_r);
+        d.inv_ln_ab = 1.0 / std::log(f->wire_r / f->tube_r);
+    }
+    d.emax = emax;
+    return GT_OK;
+}
+
 int field_setup(gt_ctx *ctx, const gt_field *f)
 {
     if (!ctx || !f) return GT_ERR_ARG;
@@ -438,6 +649,11 @@ int field_setup(gt_ctx *ctx, const gt_field *f)
             GT_CUDA(ctx, grid_emax(d.grid, (long long)f->nx * f->ny * f->nz, ctx->sms, &d.emax));
         }
         break;
+    case GT_FIELD_MESH: {
+        const int rc = build_mesh(ctx, f, d);
+        if (rc != GT_OK) return rc;
+        break;
+    }
     default:
         return GT_ERR_ARG;
     }
@@ -494,8 +710,9 @@ static int validate_run(gt_ctx *ctx, const gt_run *r, const gt_endpoints *o, voi
         if (r->signal_bins < 0 || !(r->signal_dt > 0.0) || !std::isfinite(r->signal_dt) ||
             !std::isfinite(r->signal_t0) ||
             (r->signal_kind == GT_W_PLATE && k != GT_FIELD_PLATE) ||
-            (r->signal_kind == GT_W_COAX && k != GT_FIELD_COAX && k != GT_FIELD_GRID) ||
-            (r->signal_kind == GT_W_MAP && k != GT_FIELD_GRID))
+            (r->signal_kind == GT_W_COAX && k != GT_FIELD_COAX && k != GT_FIELD_GRID &&
+             k != GT_FIELD_MESH) ||
+            (r->signal_kind == GT_W_MAP && k != GT_FIELD_GRID && k != GT_FIELD_MESH))
             return GT_ERR_ARG;
         if (r->signal_bins > 0 && r->n_avalanches > 0 && !o->signal) return GT_ERR_ARG;
         if (r->signal_kind == GT_W_COAX && ctx->field.inv_ln_ab == 0.0) return GT_ERR_ARG;
@@ -576,8 +793,8 @@ static int plan_run(gt_ctx *ctx, const gt_run *r, const gt_endpoints *o, void *w
     const int prec_i = r->precision == GT_FP64 ? 0 : 1;
     const int maj_i = r->majorant == GT_MAJORANT_BANDED ? 1 : 0;
     const int var_i = run_variant(ctx, r);
-    const int tuned_k = ctx->tuned_k[prec_i][ctx->field.kind & 3][maj_i][var_i];
-    const int tuned_m = ctx->tuned_m[prec_i][ctx->field.kind & 3][maj_i][var_i];
+    const int tuned_k = ctx->tuned_k[prec_i][ctx->field.kind][maj_i][var_i];
+    const int tuned_m = ctx->tuned_m[prec_i][ctx->field.kind][maj_i][var_i];
     p.refill_period = r->refill_period > 0 ? r->refill_period
                                            : (tuned_k > 0 ? tuned_k : (prec_i ? 16 : 32));
     // most banded flights end in a real collision, so a round flies once;
@@ -653,7 +870,7 @@ static int plan_run(gt_ctx *ctx, const gt_run *r, const gt_endpoints *o, void *w
             GT_CUDA(ctx, cudaMemsetAsync(p.created, 0, sizeof(unsigned long long) * (size_t)na, s));
     }
     const bool fp64 = r->precision == GT_FP64;
-    const int tuned_b = ctx->tuned_block[prec_i][ctx->field.kind & 3][maj_i][var_i];
+    const int tuned_b = ctx->tuned_block[prec_i][ctx->field.kind][maj_i][var_i];
     const int block = r->block ? r->block
                                : (r->mode == GT_BATCHED && tuned_b > 0 ? tuned_b
                                                                        : default_block(r->precision));
@@ -1060,9 +1277,9 @@ int gt_autotune(gt_ctx *ctx, const gt_run *run, const gt_endpoints *out, void *w
     if (top.block == 0) return GT_ERR_UNSUPPORTED;
     const int pi = fp64 ? 0 : 1, mi = r.majorant == GT_MAJORANT_BANDED ? 1 : 0;
     const int vi = run_variant(ctx, &r);
-    ctx->tuned_block[pi][ctx->field.kind & 3][mi][vi] = top.block;
-    ctx->tuned_k[pi][ctx->field.kind & 3][mi][vi] = top.refill_period;
-    ctx->tuned_m[pi][ctx->field.kind & 3][mi][vi] = top.flights_per_phase;
+    ctx->tuned_block[pi][ctx->field.kind][mi][vi] = top.block;
+    ctx->tuned_k[pi][ctx->field.kind][mi][vi] = top.refill_period;
+    ctx->tuned_m[pi][ctx->field.kind][mi][vi] = top.flights_per_phase;
     *best = top;
     return GT_OK;
 }

@@ -79,6 +79,16 @@ struct DevField {
     double emax;                         // largest |E| of the volume (COAX, GRID; else 0)
     double inv_gap;                      // PLATE: 1 / gap (anode weighting potential)
     double ln_tube, inv_ln_ab;           // COAX/GRID wire: ln b, 1 / ln(a/b)
+    // MESH: element records (kMeshRec values each, FP32 and FP64) and the
+    // uniform bins of the element search over the mesh's box (origin..hi)
+    const float4 *tet32;
+    const double *tet64;
+    const int *bin_start;                // [bins + 1] offsets into bin_tets
+    const int *bin_tets;                 // elements meeting each bin, ascending
+    int bin_n[3];
+    double bin_lo[3], bin_inv[3];        // box corner, bins per cm
+    float bin_lo_f[3], bin_inv_f[3];
+    float mesh_tol_f;                    // FP32 barycentric margin of a sure inside
 };
 
 struct Header {  // at the start of the work space, 256 bytes
@@ -244,6 +254,108 @@ struct Tables {
     int stride32;           // odd in shared memory: rows start on every bank
 };
 
+// ------------------------------------------------------ tetrahedral mesh
+// An element record (built by field_setup from the element's nodes), as
+// eight rows of four values: the first node v0; the rows of M, the inverse
+// of the edge matrix [v1 - v0, v2 - v0, v3 - v0], so that the barycentric
+// coordinates of r are l1..l3 = M (r - v0) and l0 = 1 - l1 - l2 - l3; the
+// field and weighting potential at v0; and their gradients in the element
+// (row c: dE_c/dx, dE_c/dy, dE_c/dz, dphi/dx_c), so that the linear
+// interpolation of the nodal values is E(r) = E(v0) + G (r - v0).
+constexpr int kMeshRec = 32;
+
+// Smallest barycentric coordinate of r in the element record q.
+__device__ __forceinline__ float tet_min32(const float4 *q, float x, float y, float z)
+{
+    const float4 v = __ldg(q), m0 = __ldg(q + 1), m1 = __ldg(q + 2), m2 = __ldg(q + 3);
+    const float dx = x - v.x, dy = y - v.y, dz = z - v.z;
+    const float l1 = fmaf(m0.x, dx, fmaf(m0.y, dy, m0.z * dz));
+    const float l2 = fmaf(m1.x, dx, fmaf(m1.y, dy, m1.z * dz));
+    const float l3 = fmaf(m2.x, dx, fmaf(m2.y, dy, m2.z * dz));
+    return fminf(fminf(l1, l2), fminf(l3, 1.0f - l1 - l2 - l3));
+}
+
+__device__ __forceinline__ double tet_min64(const double *q, double x, double y, double z)
+{
+    const double dx = x - q[0], dy = y - q[1], dz = z - q[2];
+    const double l1 = q[4] * dx + q[5] * dy + q[6] * dz;
+    const double l2 = q[8] * dx + q[9] * dy + q[10] * dz;
+    const double l3 = q[12] * dx + q[13] * dy + q[14] * dz;
+    return fmin(fmin(l1, l2), fmin(l3, 1.0 - l1 - l2 - l3));
+}
+
+// Bin of r (-1 when r is clearly outside the mesh's box; a point on the box
+// or within rounding of it goes to the nearest bin).
+template <typename R>
+__device__ __forceinline__ int mesh_bin(const int n[3], const R lo[3], const R inv[3], R x, R y,
+                                        R z)
+{
+    const R q[3] = {x, y, z};
+    int c = 0;
+#pragma unroll
+    for (int d = 2; d >= 0; --d) {
+        const R g = (q[d] - lo[d]) * inv[d];
+        if (!(g > (R)(-1e-3)) || !(g < (R)n[d] + (R)(1e-3))) return -1;
+        int k = (int)g;
+        k = k < 0 ? 0 : (k >= n[d] ? n[d] - 1 : k);
+        c = c * n[d] + k;
+    }
+    return c;
+}
+
+// Element search: the hint when it holds r with every barycentric
+// coordinate >= tol, else the first (lowest-index) element of r's bin that
+// does; -1 if none.
+__device__ __forceinline__ int mesh_find32(const DevField &f, float x, float y, float z, int hint,
+                                           float tol)
+{
+    if (hint >= 0 && tet_min32(f.tet32 + (kMeshRec / 4) * (int64_t)hint, x, y, z) >= tol)
+        return hint;
+    const int c = mesh_bin<float>(f.bin_n, f.bin_lo_f, f.bin_inv_f, x, y, z);
+    if (c < 0) return -1;
+    const int e = __ldg(f.bin_start + c + 1);
+    for (int i = __ldg(f.bin_start + c); i < e; ++i) {
+        const int t = __ldg(f.bin_tets + i);
+        if (tet_min32(f.tet32 + (kMeshRec / 4) * (int64_t)t, x, y, z) >= tol) return t;
+    }
+    return -1;
+}
+
+__device__ __forceinline__ int mesh_find64(const DevField &f, double x, double y, double z,
+                                           int hint, double tol)
+{
+    if (hint >= 0 && tet_min64(f.tet64 + kMeshRec * (int64_t)hint, x, y, z) >= tol) return hint;
+    const int c = mesh_bin<double>(f.bin_n, f.bin_lo, f.bin_inv, x, y, z);
+    if (c < 0) return -1;
+    const int e = f.bin_start[c + 1];
+    for (int i = f.bin_start[c]; i < e; ++i) {
+        const int t = f.bin_tets[i];
+        if (tet_min64(f.tet64 + kMeshRec * (int64_t)t, x, y, z) >= tol) return t;
+    }
+    return -1;
+}
+
+// Field of element record q at r (linear interpolation of the nodal values).
+__device__ __forceinline__ void mesh_field32(const float4 *q, float x, float y, float z, float &ex,
+                                             float &ey, float &ez)
+{
+    const float4 v = __ldg(q), e = __ldg(q + 4), gx = __ldg(q + 5), gy = __ldg(q + 6),
+                 gz = __ldg(q + 7);
+    const float dx = x - v.x, dy = y - v.y, dz = z - v.z;
+    ex = fmaf(gx.x, dx, fmaf(gx.y, dy, fmaf(gx.z, dz, e.x)));
+    ey = fmaf(gy.x, dx, fmaf(gy.y, dy, fmaf(gy.z, dz, e.y)));
+    ez = fmaf(gz.x, dx, fmaf(gz.y, dy, fmaf(gz.z, dz, e.z)));
+}
+
+// Field (c = 0..2) or weighting potential (c = 3) of FP64 element record q at r.
+__device__ __forceinline__ double mesh_value64(const double *q, int c, double x, double y, double z)
+{
+    const double dx = x - q[0], dy = y - q[1], dz = z - q[2];
+    if (c == 3) return q[19] + q[23] * dx + q[27] * dy + q[31] * dz;
+    const double *g = q + 20 + 4 * c;
+    return q[16 + c] + g[0] * dx + g[1] * dy + g[2] * dz;
+}
+
 // --------------------------------------------------------------- fields
 template <int FK>
 __device__ __forceinline__ void field64(const DevField &f, double plate_e, double x, double y,
@@ -256,6 +368,16 @@ __device__ __forceinline__ void field64(const DevField &f, double plate_e, doubl
     } else if (FK == GT_FIELD_COAX) {
         const double s = f.coax_k / (x * x + y * y);
         ex = s * x; ey = s * y; ez = 0.0;
+    } else if (FK == GT_FIELD_MESH) {
+        const int t = mesh_find64(f, x, y, z, -1, 0.0);
+        if (t < 0) {
+            ex = ey = ez = 0.0;
+        } else {
+            const double *q = f.tet64 + kMeshRec * (int64_t)t;
+            ex = mesh_value64(q, 0, x, y, z);
+            ey = mesh_value64(q, 1, x, y, z);
+            ez = mesh_value64(q, 2, x, y, z);
+        }
     } else {
         const double p[3] = {x, y, z};
         const int n[3] = {f.nx, f.ny, f.nz};
@@ -293,6 +415,13 @@ __device__ __forceinline__ void field32(const DevField &f, float plate_e, float 
     } else if (FK == GT_FIELD_COAX) {
         const float s = __fdividef(f.coax_k_f, x * x + y * y);
         ex = s * x; ey = s * y; ez = 0.f;
+    } else if (FK == GT_FIELD_MESH) {
+        const int t = mesh_find32(f, x, y, z, -1, -f.mesh_tol_f);
+        if (t < 0) {
+            ex = ey = ez = 0.f;
+        } else {
+            mesh_field32(f.tet32 + (kMeshRec / 4) * (int64_t)t, x, y, z, ex, ey, ez);
+        }
     } else {
         // cell (clamped to the last one) and weights without int/float
         // conversions: floor(g) by a round-down add of 2^23
@@ -346,6 +475,10 @@ __device__ __forceinline__ int boundary64(const DevField &f, double x, double y,
         if (x < f.origin[0] || x > f.hi[0] || y < f.origin[1] || y > f.hi[1] ||
             z < f.origin[2] || z > f.hi[2])
             return GT_ST_OUT_OF_MAP;
+    } else if (FK == GT_FIELD_MESH) {
+        const double r2 = x * x + y * y;
+        if (f.wire_r2 > 0.0 && r2 <= f.wire_r2) return GT_ST_WIRE;
+        if (mesh_find64(f, x, y, z, -1, 0.0) < 0) return GT_ST_OUT_OF_MAP;
     }
     return 0;
 }
@@ -759,6 +892,10 @@ __device__ __forceinline__ int outside32(const DevField &f, float zg, float zc, 
         if (x < (float)f.origin[0] || x > (float)f.hi[0] || y < (float)f.origin[1] ||
             y > (float)f.hi[1] || z < (float)f.origin[2] || z > (float)f.hi[2])
             return GT_ST_OUT_OF_MAP;
+    } else if (FK == GT_FIELD_MESH) {
+        const float r2 = x * x + y * y;
+        if (f.wire_r2 > 0.0 && r2 <= (float)f.wire_r2) return GT_ST_WIRE;
+        if (mesh_find32(f, x, y, z, -1, 0.0f) < 0) return GT_ST_OUT_OF_MAP;
     }
     return 0;
 }
@@ -773,6 +910,10 @@ __device__ __forceinline__ double weighting64(const RunParams &p, double x, doub
     const DevField &f = p.field;
     if (p.signal_kind == GT_W_PLATE) return z * f.inv_gap;
     if (p.signal_kind == GT_W_COAX) return (0.5 * log(x * x + y * y) - f.ln_tube) * f.inv_ln_ab;
+    if (f.kind == GT_FIELD_MESH) {  // GT_W_MAP on a mesh: linear in the element
+        const int t = mesh_find64(f, x, y, z, -1, 0.0);
+        return t < 0 ? 0.0 : mesh_value64(f.tet64 + kMeshRec * (int64_t)t, 3, x, y, z);
+    }
     // GT_W_MAP: trilinear interpolation of the nodes' 4th component
     const double q[3] = {x, y, z};
     const int n[3] = {f.nx, f.ny, f.nz};
@@ -1157,8 +1298,27 @@ struct MixedElectron {
     int sg_next;             // induced signal: next bin edge
     double sg_phi;           // weighting potential at the last edge (or birth)
     float sg_toff;           // time offset of the next edge (slightly early)
+    int elem;                // MESH: the element holding the position (-1: unknown)
 
     __device__ __forceinline__ void bind(const Tables &tb) { b = tb.base + threadIdx.x; }
+
+    // Field at the current position.  On a mesh, the element found by the
+    // last boundary test holds the position (searched once for a new electron).
+    template <int FK>
+    __device__ __forceinline__ void efield(const RunParams &p, float &ex, float &ey, float &ez)
+    {
+        if (FK == GT_FIELD_MESH) {
+            const float x = px + ox, y = py + oy, z = pz + oz;
+            if (elem < 0) elem = mesh_find32(p.field, x, y, z, -1, -p.field.mesh_tol_f);
+            if (elem < 0) {
+                ex = ey = ez = 0.f;
+                return;
+            }
+            mesh_field32(p.field.tet32 + (kMeshRec / 4) * (int64_t)elem, x, y, z, ex, ey, ez);
+        } else {
+            field32<FK>(p.field, plate_e, px + ox, py + oy, pz + oz, ex, ey, ez);
+        }
+    }
 
     // FP32 offset time at which the next bin edge may come (an FP32
     // pre-test; the edge itself is placed in FP64).
@@ -1249,10 +1409,10 @@ struct MixedElectron {
         const unsigned S = blockDim.x;
         b[0] = X; b[S] = Y; b[2 * S] = Z; b[3 * S] = T;
         ox = oy = oz = ot = 0.f;
-        if (FK == GT_FIELD_COAX || FK == GT_FIELD_GRID) {
+        if (FK == GT_FIELD_COAX || FK == GT_FIELD_GRID || FK == GT_FIELD_MESH) {
             px = (float)X; py = (float)Y;
         }
-        if (FK == GT_FIELD_GRID) pz = (float)Z;
+        if (FK == GT_FIELD_GRID || FK == GT_FIELD_MESH) pz = (float)Z;
         if (FK == GT_FIELD_PLATE) {
             const float hi = (float)(p.field.gap - Z), lo = -(float)Z;
             zhi = hi - (fabsf(hi) * 1e-6f + 1e-12f);
@@ -1277,6 +1437,7 @@ struct MixedElectron {
         nf = nreal = nnull = 0;
         status = 0;
         timed = false;
+        elem = -1;
         set_base<FK>(p, p.x0[s], p.y0[s], p.z0[s], p.t0[s]);
         if (GEO) signal_start(p);
     }
@@ -1290,10 +1451,32 @@ struct MixedElectron {
 
     // FP32 pre-test with a margin, then the FP64 boundary test of X + ox.
     template <int FK>
-    __device__ __forceinline__ int boundary(const RunParams &p) const
+    __device__ __forceinline__ int boundary(const RunParams &p)
     {
         bool maybe;
         if (FK == GT_FIELD_UNIFORM) {
+            return 0;
+        } else if (FK == GT_FIELD_MESH) {
+            // inside for sure when an element holds the FP32 position with a
+            // margin (the cached element first); else decided in FP64
+            const DevField &f = p.field;
+            const float rx = px + ox, ry = py + oy, rz = pz + oz;
+            const bool near = (rx * rx + ry * ry <= f.wire_r2_hi_f) || (rx < f.box_lo_f[0]) ||
+                              (rx > f.box_hi_f[0]) || (ry < f.box_lo_f[1]) ||
+                              (ry > f.box_hi_f[1]) || (rz < f.box_lo_f[2]) || (rz > f.box_hi_f[2]);
+            if (!near) {
+                const int t = mesh_find32(f, rx, ry, rz, elem, f.mesh_tol_f);
+                if (t >= 0) {
+                    elem = t;
+                    return 0;
+                }
+            }
+            const unsigned S = blockDim.x;
+            const double x = b[0] + (double)ox, y = b[S] + (double)oy, z = b[2 * S] + (double)oz;
+            if (f.wire_r2 > 0.0 && x * x + y * y <= f.wire_r2) return GT_ST_WIRE;
+            const int t = mesh_find64(f, x, y, z, elem, 0.0);
+            if (t < 0) return GT_ST_OUT_OF_MAP;
+            elem = t;
             return 0;
         } else if (FK == GT_FIELD_PLATE) {
             maybe = (oz >= zhi) || (oz < zlo);
@@ -1346,7 +1529,7 @@ struct MixedElectron {
         const float h = ns > 1 ? dt / (float)ns : dt;
         const unsigned S = blockDim.x;
         for (int sub = 0; sub < ns; ++sub) {
-            if (sub > 0) field32<FK>(p.field, plate_e, px + ox, py + oy, pz + oz, ex, ey, ez);
+            if (sub > 0) efield<FK>(p, ex, ey, ez);
             const float ax = -kAccelF * ex, ay = -kAccelF * ey, az = -kAccelF * ez;
             const float sox = ox, soy = oy, soz = oz, sot = ot, svx = vx, svy = vy, svz = vz;
             move(p, ax, ay, az, h);
@@ -1418,7 +1601,7 @@ struct MixedElectron {
         }
         const uint4 w = draw(p.seed, aval, uid, nf, 0u);
         float ex, ey, ez;
-        field32<FK>(p.field, plate_e, px + ox, py + oy, pz + oz, ex, ey, ez);
+        efield<FK>(p, ex, ey, ez);
         const float ax = -kAccelF * ex, ay = -kAccelF * ey, az = -kAccelF * ez;
         float nu = p.gas.nu_max_f, dt;
         bool pseudo = false;
@@ -1612,6 +1795,7 @@ struct MixedElectron {
         nnull = 0;
         status = 0;
         timed = false;
+        elem = -1;
         set_base<FK>(p, s.x[i], s.y[i], s.z[i], s.t[i]);
         if (GEO) signal_start(p);
     }

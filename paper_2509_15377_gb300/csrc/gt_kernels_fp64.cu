@@ -34,6 +34,7 @@ cudaError_t launch_batched_fp64(const RunParams &p, int grid, int block, size_t 
     case GT_FIELD_UNIFORM: return batched<GT_FIELD_UNIFORM>(p, grid, block, smem, s);
     case GT_FIELD_PLATE: return batched<GT_FIELD_PLATE>(p, grid, block, smem, s);
     case GT_FIELD_COAX: return batched<GT_FIELD_COAX>(p, grid, block, smem, s);
+    case GT_FIELD_MESH: return batched<GT_FIELD_MESH>(p, grid, block, smem, s);
     default: return batched<GT_FIELD_GRID>(p, grid, block, smem, s);
     }
 }
@@ -45,6 +46,7 @@ cudaError_t launch_plain_fp64(const RunParams &p, const PlainArgs &a, int block,
     case GT_FIELD_UNIFORM: return plain<GT_FIELD_UNIFORM>(p, a, block, smem, s);
     case GT_FIELD_PLATE: return plain<GT_FIELD_PLATE>(p, a, block, smem, s);
     case GT_FIELD_COAX: return plain<GT_FIELD_COAX>(p, a, block, smem, s);
+    case GT_FIELD_MESH: return plain<GT_FIELD_MESH>(p, a, block, smem, s);
     default: return plain<GT_FIELD_GRID>(p, a, block, smem, s);
     }
 }
@@ -63,6 +65,7 @@ cudaError_t configure_fp64(size_t max_smem)
     if ((e = configure_one<GT_FIELD_UNIFORM>(max_smem)) != cudaSuccess) return e;
     if ((e = configure_one<GT_FIELD_PLATE>(max_smem)) != cudaSuccess) return e;
     if ((e = configure_one<GT_FIELD_COAX>(max_smem)) != cudaSuccess) return e;
+    if ((e = configure_one<GT_FIELD_MESH>(max_smem)) != cudaSuccess) return e;
     return configure_one<GT_FIELD_GRID>(max_smem);
 }
 
@@ -84,6 +87,7 @@ int occupancy_batched_fp64(int field_kind, int block, size_t smem)
     case GT_FIELD_UNIFORM: return occ<GT_FIELD_UNIFORM>(block, smem);
     case GT_FIELD_PLATE: return occ<GT_FIELD_PLATE>(block, smem);
     case GT_FIELD_COAX: return occ<GT_FIELD_COAX>(block, smem);
+    case GT_FIELD_MESH: return occ<GT_FIELD_MESH>(block, smem);
     default: return occ<GT_FIELD_GRID>(block, smem);
     }
 }

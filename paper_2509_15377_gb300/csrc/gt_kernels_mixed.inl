@@ -58,6 +58,7 @@ static cudaError_t batched_fk(const RunParams &p, int grid, int block, size_t sm
     case GT_FIELD_UNIFORM: return batched<GT_FIELD_UNIFORM, TAB, PHYS, GEO>(p, grid, block, smem, s);
     case GT_FIELD_PLATE: return batched<GT_FIELD_PLATE, TAB, PHYS, GEO>(p, grid, block, smem, s);
     case GT_FIELD_COAX: return batched<GT_FIELD_COAX, TAB, PHYS, GEO>(p, grid, block, smem, s);
+    case GT_FIELD_MESH: return batched<GT_FIELD_MESH, TAB, PHYS, GEO>(p, grid, block, smem, s);
     default: return batched<GT_FIELD_GRID, TAB, PHYS, GEO>(p, grid, block, smem, s);
     }
 }
@@ -70,6 +71,7 @@ static cudaError_t plain_fk(const RunParams &p, const PlainArgs &a, int block, s
     case GT_FIELD_UNIFORM: return plain<GT_FIELD_UNIFORM, TAB, PHYS, GEO>(p, a, block, smem, s);
     case GT_FIELD_PLATE: return plain<GT_FIELD_PLATE, TAB, PHYS, GEO>(p, a, block, smem, s);
     case GT_FIELD_COAX: return plain<GT_FIELD_COAX, TAB, PHYS, GEO>(p, a, block, smem, s);
+    case GT_FIELD_MESH: return plain<GT_FIELD_MESH, TAB, PHYS, GEO>(p, a, block, smem, s);
     default: return plain<GT_FIELD_GRID, TAB, PHYS, GEO>(p, a, block, smem, s);
     }
 }
@@ -123,6 +125,7 @@ static cudaError_t configure_tab(size_t max_smem)
     if ((e = configure_one<GT_FIELD_UNIFORM, TAB, PHYS, GEO>(max_smem)) != cudaSuccess) return e;
     if ((e = configure_one<GT_FIELD_PLATE, TAB, PHYS, GEO>(max_smem)) != cudaSuccess) return e;
     if ((e = configure_one<GT_FIELD_COAX, TAB, PHYS, GEO>(max_smem)) != cudaSuccess) return e;
+    if ((e = configure_one<GT_FIELD_MESH, TAB, PHYS, GEO>(max_smem)) != cudaSuccess) return e;
     return configure_one<GT_FIELD_GRID, TAB, PHYS, GEO>(max_smem);
 }
 
@@ -161,6 +164,7 @@ static int occ_fk(int field_kind, int block, size_t smem)
     case GT_FIELD_UNIFORM: return occ<GT_FIELD_UNIFORM, TAB, PHYS, GEO>(block, smem);
     case GT_FIELD_PLATE: return occ<GT_FIELD_PLATE, TAB, PHYS, GEO>(block, smem);
     case GT_FIELD_COAX: return occ<GT_FIELD_COAX, TAB, PHYS, GEO>(block, smem);
+    case GT_FIELD_MESH: return occ<GT_FIELD_MESH, TAB, PHYS, GEO>(block, smem);
     default: return occ<GT_FIELD_GRID, TAB, PHYS, GEO>(block, smem);
     }
 }

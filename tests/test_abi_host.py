@@ -43,7 +43,7 @@ def test_struct_layouts_match(lib):
     assert list(sizes) == [C.sizeof(s) for s in (A.gt_gas, A.gt_field, A.gt_run,
                                                     A.gt_endpoints, A.gt_stats)]
     assert lib.gt_abi_sizes(sizes, 4) == A.GT_ERR_ARG
-    assert lib.gt_abi_version() == 2
+    assert lib.gt_abi_version() == 3
 
 
 def test_error_strings(lib):
