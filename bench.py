@@ -178,6 +178,68 @@ def oracle_baseline(w, seed: int, n_aval: int, args) -> dict:
 
 
 # ---------------------------------------------------------------- our arm
+def field_map_lines(av, args, seed: int, cap: int, stream, flush, majorant) -> dict:
+    """Field maps of the coax geometry (the grid workload's box, 1810 V, one
+    primary at r = 1 mm per avalanche): the regular 256^3 grid and a
+    tetrahedral mesh of the same box (48^3 jittered cubes graded towards the
+    wire, six elements each), batched mixed, each kernel autotuned unless a
+    launch shape is given."""
+    from paper_2509_15377_gb300 import avalanche as A
+    from paper_2509_15377_gb300 import workloads as W
+    maps = {}
+    n_map = args.map_avalanches
+    chosen = [m for m in args.maps.split(",") if m]
+    for name in chosen:
+        if name == "grid":
+            wl = W.grid_stress(n_avalanches=n_map, n=256, seed=seed)
+        else:
+            wl = W.mesh_coax(n_avalanches=n_map, cells=48, seed=seed, grading=4.0)
+        av.set_gas(wl.gas)
+        av.set_field(wl.field)
+        m_opt = A.RunOptions(seed=seed, t_max=wl.t_max, precision=A.GT_MIXED, mode=A.GT_BATCHED,
+                             block=args.block, refill_period=args.refill_period,
+                             flights_per_phase=args.flights_per_phase, majorant=majorant,
+                             majorant_window=args.window)
+        m_dev = av.primaries_device(wl.primaries)
+        if not args.no_autotune and not (args.block or args.refill_period or args.flights_per_phase):
+            av.autotune(av.primaries_device(wl.primaries.subset(list(range(min(16, n_map))))),
+                        m_opt, cap, stream=stream)
+        m_real, m_ms, m_fl = 0, 0.0, 0
+        for _ in range(2):
+            flush.fill_(1)
+            m_st = av.run(m_dev, m_opt, cap, stream=stream, allow=(A.GT_OK,))
+            m_real += m_st["real_collisions"]
+            m_ms += m_st["transport_ms"]
+            m_fl += m_st["flights"]
+        maps[name] = {"value_kernel_time": m_real / (m_ms / 1e3), "unit": UNIT,
+                      "flights_per_real": m_fl / max(m_real, 1), "avalanches": n_map,
+                      "electrons_per_avalanche": m_st["n_endpoints"] / n_map,
+                      "shape": [m_st["block"], m_st["refill_period"], m_st["flights_per_phase"]]}
+        if name == "grid":
+            maps[name]["map"] = "256^3 float4 nodes, trilinear"
+        else:
+            maps[name]["map"] = (f"{wl.field.mesh_tets.shape[0]} tetrahedra, "
+                                 f"{wl.field.mesh_nodes.shape[0]} nodes, linear, "
+                                 "graded towards the wire (sinh, a = 4)")
+    return maps
+
+
+def run_maps_only(args) -> None:
+    """Only the field-map lines (a profiling aid): prints their JSON."""
+    import torch
+    import __graft_entry__
+    __graft_entry__.build()
+    from paper_2509_15377_gb300 import avalanche as A
+    torch.cuda.set_device(0)
+    av = A.Avalanche(0)
+    stream = torch.cuda.current_stream()
+    flush = torch.empty(256 * 1024 * 1024, dtype=torch.uint8, device="cuda:0")
+    majorant = A.GT_MAJORANT_BANDED if args.majorant == "banded" else A.GT_MAJORANT_GLOBAL
+    maps = field_map_lines(av, args, 0, args.capacity, stream, flush, majorant)
+    print(json.dumps({"field_maps": maps}))
+    av.close()
+
+
 def run_ours(args) -> None:
     import torch
     import torch.distributed as dist
@@ -361,39 +423,9 @@ def run_ours(args) -> None:
                               "note": "basic gas, Shockley-Ramo anode signal per avalanche, "
                                       "2000 bins x 0.05 ns"}
 
-    # field maps of the coax geometry (the grid workload's box, 1810 V, one
-    # primary at r = 1 mm per avalanche): the regular 256^3 grid and a
-    # tetrahedral mesh of the same box (48^3 jittered cubes, six elements
-    # each), 64 avalanches, batched mixed, each kernel autotuned
     maps = None
     if rank == 0 and not args.no_plain:
-        maps = {}
-        for name, wl in (("grid", W.grid_stress(n_avalanches=64, n=256, seed=seed)),
-                         ("mesh", W.mesh_coax(n_avalanches=64, cells=48, seed=seed))):
-            av.set_gas(wl.gas)
-            av.set_field(wl.field)
-            m_opt = A.RunOptions(seed=seed, t_max=wl.t_max, precision=A.GT_MIXED,
-                                 mode=A.GT_BATCHED, majorant=majorant, majorant_window=args.window)
-            m_dev = av.primaries_device(wl.primaries)
-            if not args.no_autotune:
-                av.autotune(av.primaries_device(wl.primaries.subset(list(range(16)))), m_opt, cap,
-                            stream=stream)
-            m_real, m_ms, m_fl = 0, 0.0, 0
-            for _ in range(2):
-                flush.fill_(1)
-                m_st = av.run(m_dev, m_opt, cap, stream=stream, allow=(A.GT_OK,))
-                m_real += m_st["real_collisions"]
-                m_ms += m_st["transport_ms"]
-                m_fl += m_st["flights"]
-            maps[name] = {"value_kernel_time": m_real / (m_ms / 1e3), "unit": UNIT,
-                          "flights_per_real": m_fl / max(m_real, 1),
-                          "electrons_per_avalanche": m_st["n_endpoints"] / 64.0,
-                          "shape": [m_st["block"], m_st["refill_period"], m_st["flights_per_phase"]]}
-            if name == "grid":
-                maps[name]["map"] = "256^3 float4 nodes, trilinear"
-            else:
-                maps[name]["map"] = (f"{wl.field.mesh_tets.shape[0]} tetrahedra, "
-                                     f"{wl.field.mesh_nodes.shape[0]} nodes, linear")
+        maps = field_map_lines(av, args, seed, cap, stream, flush, majorant)
         av.set_gas(w.gas)
         av.set_field(w.field)
 
@@ -589,6 +621,10 @@ def parse(argv=None):
     ap.add_argument("--majorant", default="banded", choices=["banded", "global"])
     ap.add_argument("--window", type=float, default=2.0)
     ap.add_argument("--tune-avalanches", type=int, default=1024)
+    ap.add_argument("--maps-only", action="store_true",
+                    help="only the grid / mesh field-map lines (profiling aid)")
+    ap.add_argument("--maps", default="grid,mesh")
+    ap.add_argument("--map-avalanches", type=int, default=256)
     ap.add_argument("--calibrate", action="store_true",
                     help="run the straight-line calibration workload (for ncu)")
     return ap.parse_args(argv)
@@ -596,7 +632,9 @@ def parse(argv=None):
 
 def main(argv=None):
     args = parse(argv)
-    if args.calibrate:
+    if args.maps_only:
+        run_maps_only(args)
+    elif args.calibrate:
         run_calibration(args)
     elif args.impl == "reference":
         run_reference(args)

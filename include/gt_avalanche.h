@@ -371,7 +371,7 @@ int avalanche_run(gt_ctx *ctx, const gt_run *run, const gt_endpoints *out, void 
  * at zero, so the contents left by the previous call do not matter. */
 #define GT_STATIC_MAX_ELECTRONS (1 << 18)
 #define GT_STATIC_MAX_AVALANCHES 16384
-#define GT_STATIC_SCRATCH_BYTES 7471616 /* ~7.1 MiB */
+#define GT_STATIC_SCRATCH_BYTES 8520192 /* ~8.1 MiB */
 
 int avalanche_run_static(gt_ctx *ctx, const gt_run *run, const gt_endpoints *out, void *stream,
                          gt_stats *stats);

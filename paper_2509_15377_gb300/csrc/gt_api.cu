@@ -43,6 +43,7 @@ struct gt_ctx {
     // MESH field: element records and search bins (device, owned)
     float *d_tet32 = nullptr;
     double *d_tet64 = nullptr;
+    int *d_tet_nb = nullptr;
     int *d_bin_start = nullptr, *d_bin_tets = nullptr;
     char last_error[256] = {0};
 };
@@ -82,7 +83,7 @@ size_t align256(size_t x) { return (x + 255) & ~(size_t)255; }
 
 // Work-space layout.  Every region starts on a 256-byte boundary.
 struct Layout {
-    size_t hdr, ready, bvx, bvy, bvz, created, afield, prim, order, stacks, total;
+    size_t hdr, ready, bvx, bvy, bvz, belem, created, afield, prim, order, stacks, total;
     size_t stack_entry_bytes;
 };
 
@@ -98,6 +99,7 @@ Layout layout_for(const gt_run *run, int64_t capacity)
     L.bvx = off; off = align256(off + sizeof(double) * (size_t)capacity);
     L.bvy = off; off = align256(off + sizeof(double) * (size_t)capacity);
     L.bvz = off; off = align256(off + sizeof(double) * (size_t)capacity);
+    L.belem = off; off = align256(off + sizeof(int32_t) * (size_t)capacity);
     const size_t na = (size_t)std::max(run->n_avalanches, 1);
     L.created = off; off = align256(off + sizeof(unsigned long long) * na);
     L.afield = off;
@@ -236,6 +238,7 @@ int gt_destroy(gt_ctx *ctx)
         if (ctx->d_obs_partials) cudaFree(ctx->d_obs_partials);
         if (ctx->d_tet32) cudaFree(ctx->d_tet32);
         if (ctx->d_tet64) cudaFree(ctx->d_tet64);
+        if (ctx->d_tet_nb) cudaFree(ctx->d_tet_nb);
         if (ctx->d_bin_start) cudaFree(ctx->d_bin_start);
         if (ctx->d_bin_tets) cudaFree(ctx->d_bin_tets);
         if (ctx->ev0) cudaEventDestroy(ctx->ev0);
@@ -419,11 +422,10 @@ static int build_mesh(gt_ctx *ctx, const gt_field *f, DevField &d)
         emax = std::max(emax, std::sqrt((double)v[0] * v[0] + (double)v[1] * v[1] +
                                         (double)v[2] * v[2]));
     }
-    double ext[3], mean_ext[3] = {0.0, 0.0, 0.0}, rmax = 0.0, mnorm = 0.0;
+    double ext[3], mean_ext[3] = {0.0, 0.0, 0.0};
     for (int k = 0; k < 3; ++k) {
         ext[k] = hi[k] - lo[k];
         if (!(ext[k] > 0.0)) return GT_ERR_ARG;
-        rmax = std::max(rmax, std::max(std::fabs(lo[k]), std::fabs(hi[k])));
     }
     std::vector<double> rec(kMeshRec * (size_t)nt, 0.0);
     std::vector<double> box(6 * (size_t)nt);
@@ -454,16 +456,32 @@ static int build_mesh(gt_ctx *ctx, const gt_field *f, DevField &d)
         if (!(std::fabs(det) > 1e-12 * len * len * len)) return GT_ERR_ARG;
         double *r = rec.data() + kMeshRec * t;
         for (int k = 0; k < 3; ++k) r[k] = v[0][k];
-        double m[3][3];
+        double m[3][3], tx[3];
+        for (int k = 0; k < 3; ++k) {  // the element's extent along each axis
+            double a = v[0][k], b = v[0][k];
+            for (int i = 1; i < 4; ++i) {
+                a = std::min(a, v[i][k]);
+                b = std::max(b, v[i][k]);
+            }
+            tx[k] = b - a;
+        }
+        // FP32 margin: with u = 2^-23, a coordinate l_i = M_i (r - v0) computed
+        // from the FP32 position, node and record errs by at most
+        // u sum_k |M_ik| (2 |v0_k| + 3 extent_k); l_0 by the sum of those;
+        // twice the largest, plus a few roundings of l itself
+        const double u = 1.1920928955078125e-7;
+        double err0 = 3.0 * u, errmax = 0.0;
         for (int i = 0; i < 3; ++i) {
-            double rowsum = 0.0;
+            double ei = 0.0;
             for (int k = 0; k < 3; ++k) {
                 m[i][k] = c[i][k] / det;
                 r[4 + 4 * i + k] = m[i][k];
-                rowsum += std::fabs(m[i][k]);
+                ei += std::fabs(m[i][k]) * u * (2.0 * std::fabs(v[0][k]) + 3.0 * tx[k]);
             }
-            mnorm = std::max(mnorm, rowsum);
+            err0 += ei;
+            errmax = std::max(errmax, ei);
         }
+        r[3] = 2.0 * (std::max(errmax, err0) + 4.0 * u);
         // value at v0 and gradient of each component: sum_i (V_{i+1} - V_0) M_row_i
         for (int comp = 0; comp < 4; ++comp) {
             double g[3] = {0.0, 0.0, 0.0};
@@ -487,6 +505,42 @@ static int build_mesh(gt_ctx *ctx, const gt_field *f, DevField &d)
             box[6 * t + k] = a;
             box[6 * t + 3 + k] = b;
             mean_ext[k] += (b - a) / (double)nt;
+        }
+    }
+    // face neighbours: the faces sorted by their node triple, equal
+    // neighbours paired (a face met more than twice is not a mesh)
+    std::vector<int> nbr(4 * (size_t)nt, -1);
+    {
+        struct Face {
+            int32_t a, b, c;
+            int64_t slot;  // 4 t + the node the face is opposite to
+        };
+        std::vector<Face> faces(4 * (size_t)nt);
+        for (int64_t t = 0; t < nt; ++t)
+            for (int i = 0; i < 4; ++i) {
+                int32_t n[3], k = 0;
+                for (int j = 0; j < 4; ++j)
+                    if (j != i) n[k++] = f->mesh_tets[4 * t + j];
+                std::sort(n, n + 3);
+                faces[4 * t + i] = Face{n[0], n[1], n[2], 4 * t + i};
+            }
+        std::sort(faces.begin(), faces.end(), [](const Face &x, const Face &y) {
+            if (x.a != y.a) return x.a < y.a;
+            if (x.b != y.b) return x.b < y.b;
+            return x.c < y.c;
+        });
+        auto same = [](const Face &x, const Face &y) {
+            return x.a == y.a && x.b == y.b && x.c == y.c;
+        };
+        for (size_t i = 0; i < faces.size();) {
+            size_t j = i + 1;
+            while (j < faces.size() && same(faces[i], faces[j])) ++j;
+            if (j - i > 2) return GT_ERR_ARG;
+            if (j - i == 2) {
+                nbr[faces[i].slot] = (int)(faces[i + 1].slot / 4);
+                nbr[faces[i + 1].slot] = (int)(faces[i].slot / 4);
+            }
+            i = j;
         }
     }
     // bins about half an element's extent per axis, at most 2^24 in all
@@ -547,12 +601,16 @@ static int build_mesh(gt_ctx *ctx, const gt_field *f, DevField &d)
             if (!dg.ok) return GT_ERR_CUDA;
             if (ctx->d_tet32) cudaFree(ctx->d_tet32);
             if (ctx->d_tet64) cudaFree(ctx->d_tet64);
+            if (ctx->d_tet_nb) cudaFree(ctx->d_tet_nb);
             if (ctx->d_bin_start) cudaFree(ctx->d_bin_start);
             if (ctx->d_bin_tets) cudaFree(ctx->d_bin_tets);
-            ctx->d_tet32 = nullptr; ctx->d_tet64 = nullptr;
+            ctx->d_tet32 = nullptr; ctx->d_tet64 = nullptr; ctx->d_tet_nb = nullptr;
             ctx->d_bin_start = nullptr; ctx->d_bin_tets = nullptr;
             GT_CUDA(ctx, cudaMalloc((void **)&ctx->d_tet32, sizeof(float) * rec32.size()));
             GT_CUDA(ctx, cudaMalloc((void **)&ctx->d_tet64, sizeof(double) * rec.size()));
+            GT_CUDA(ctx, cudaMalloc((void **)&ctx->d_tet_nb, sizeof(int) * nbr.size()));
+            GT_CUDA(ctx, cudaMemcpy(ctx->d_tet_nb, nbr.data(), sizeof(int) * nbr.size(),
+                                    cudaMemcpyHostToDevice));
             GT_CUDA(ctx, cudaMalloc((void **)&ctx->d_bin_start, sizeof(int) * start.size()));
             GT_CUDA(ctx, cudaMalloc((void **)&ctx->d_bin_tets,
                                     sizeof(int) * std::max<size_t>(tets.size(), 1)));
@@ -569,6 +627,7 @@ static int build_mesh(gt_ctx *ctx, const gt_field *f, DevField &d)
     }
     d.tet32 = reinterpret_cast<const float4 *>(ctx->d_tet32);
     d.tet64 = ctx->d_tet64;
+    d.tet_nb = reinterpret_cast<const int4 *>(ctx->d_tet_nb);
     d.bin_start = ctx->d_bin_start;
     d.bin_tets = ctx->d_bin_tets;
     for (int k = 0; k < 3; ++k) {
@@ -580,9 +639,6 @@ static int build_mesh(gt_ctx *ctx, const gt_field *f, DevField &d)
         d.bin_lo_f[k] = (float)lo[k];
         d.bin_inv_f[k] = (float)inv[k];
     }
-    // FP32 rounding of the position, the node and the record bound the
-    // error of an FP32 barycentric coordinate; 16x that is a sure margin
-    d.mesh_tol_f = (float)(16.0 * 1.1920928955078125e-7 * (1.0 + 2.0 * mnorm * rmax));
     d.wire_r2 = f->wire_r * f->wire_r;
     if (f->wire_r > 0.0 && f->tube_r > f->wire_r) {
         d.ln_tube = std::log(f->tube_r);
@@ -786,6 +842,7 @@ static int plan_run(gt_ctx *ctx, const gt_run *r, const gt_endpoints *o, void *w
     p.bvx = reinterpret_cast<double *>(base + Ly.bvx);
     p.bvy = reinterpret_cast<double *>(base + Ly.bvy);
     p.bvz = reinterpret_cast<double *>(base + Ly.bvz);
+    p.belem = reinterpret_cast<int32_t *>(base + Ly.belem);
     p.created = reinterpret_cast<unsigned long long *>(base + Ly.created);
     p.seed = r->seed;
     p.t_max = r->t_max > 0.0 ? r->t_max : 0.0;

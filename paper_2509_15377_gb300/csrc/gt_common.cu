@@ -29,6 +29,7 @@ __global__ void k_seed(const RunParams p, const SeedArgs a)
         const double s = sqrt(kTwoAccel * fmax(a.e[i], 0.0));
         p.x0[i] = a.x[i]; p.y0[i] = a.y[i]; p.z0[i] = a.z[i]; p.t0[i] = a.t[i]; p.e0[i] = a.e[i];
         p.bvx[i] = s * a.dx[i]; p.bvy[i] = s * a.dy[i]; p.bvz[i] = s * a.dz[i];
+        p.belem[i] = -1;
         p.uid[i] = a.uid[i];
         p.aval[i] = av;
         p.status[i] = 0;

@@ -83,12 +83,12 @@ struct DevField {
     // uniform bins of the element search over the mesh's box (origin..hi)
     const float4 *tet32;
     const double *tet64;
+    const int4 *tet_nb;                  // element across the face opposite node i (-1: none)
     const int *bin_start;                // [bins + 1] offsets into bin_tets
     const int *bin_tets;                 // elements meeting each bin, ascending
     int bin_n[3];
     double bin_lo[3], bin_inv[3];        // box corner, bins per cm
     float bin_lo_f[3], bin_inv_f[3];
-    float mesh_tol_f;                    // FP32 barycentric margin of a sure inside
 };
 
 struct Header {  // at the start of the work space, 256 bytes
@@ -132,6 +132,7 @@ struct RunParams {
     Header *hdr;
     unsigned int *ready;      // [capacity] queue slot filled
     double *bvx, *bvy, *bvz;  // [capacity] velocity at birth
+    int32_t *belem;           // [capacity] MESH: element of the birth point (-1: unknown)
     unsigned long long *created;  // [n_avalanches] (size_limit only)
     const double *aval_field;     // [n_avalanches] or null
     // run options
@@ -256,7 +257,9 @@ struct Tables {
 
 // ------------------------------------------------------ tetrahedral mesh
 // An element record (built by field_setup from the element's nodes), as
-// eight rows of four values: the first node v0; the rows of M, the inverse
+// eight rows of four values: the first node v0 (and, in the FP32 record, the
+// element's margin: a bound on the FP32 error of its barycentric
+// coordinates, with a factor 2 to spare); the rows of M, the inverse
 // of the edge matrix [v1 - v0, v2 - v0, v3 - v0], so that the barycentric
 // coordinates of r are l1..l3 = M (r - v0) and l0 = 1 - l1 - l2 - l3; the
 // field and weighting potential at v0; and their gradients in the element
@@ -264,7 +267,8 @@ struct Tables {
 // interpolation of the nodal values is E(r) = E(v0) + G (r - v0).
 constexpr int kMeshRec = 32;
 
-// Smallest barycentric coordinate of r in the element record q.
+// Smallest barycentric coordinate of r in the element record q, in units of
+// the element's FP32 margin: >= 1 inside for sure, < -1 outside for sure.
 __device__ __forceinline__ float tet_min32(const float4 *q, float x, float y, float z)
 {
     const float4 v = __ldg(q), m0 = __ldg(q + 1), m1 = __ldg(q + 2), m2 = __ldg(q + 3);
@@ -272,7 +276,7 @@ __device__ __forceinline__ float tet_min32(const float4 *q, float x, float y, fl
     const float l1 = fmaf(m0.x, dx, fmaf(m0.y, dy, m0.z * dz));
     const float l2 = fmaf(m1.x, dx, fmaf(m1.y, dy, m1.z * dz));
     const float l3 = fmaf(m2.x, dx, fmaf(m2.y, dy, m2.z * dz));
-    return fminf(fminf(l1, l2), fminf(l3, 1.0f - l1 - l2 - l3));
+    return __fdividef(fminf(fminf(l1, l2), fminf(l3, 1.0f - l1 - l2 - l3)), v.w);
 }
 
 __device__ __forceinline__ double tet_min64(const double *q, double x, double y, double z)
@@ -304,8 +308,8 @@ __device__ __forceinline__ int mesh_bin(const int n[3], const R lo[3], const R i
 }
 
 // Element search: the hint when it holds r with every barycentric
-// coordinate >= tol, else the first (lowest-index) element of r's bin that
-// does; -1 if none.
+// coordinate >= tol (FP32: in units of the element's margin), else the
+// first (lowest-index) element of r's bin that does; -1 if none.
 __device__ __forceinline__ int mesh_find32(const DevField &f, float x, float y, float z, int hint,
                                            float tol)
 {
@@ -331,6 +335,63 @@ __device__ __forceinline__ int mesh_find64(const DevField &f, double x, double y
     for (int i = f.bin_start[c]; i < e; ++i) {
         const int t = f.bin_tets[i];
         if (tet_min64(f.tet64 + kMeshRec * (int64_t)t, x, y, z) >= tol) return t;
+    }
+    return -1;
+}
+
+// Walk from element t towards r (FP32): while r is not inside with every
+// coordinate >= tol (margin units), step across the face opposite the node
+// of the most negative coordinate; -1 when the walk leaves the mesh or takes
+// more than kMeshWalk steps (the bins decide then).
+constexpr int kMeshWalk = 8;
+
+__device__ __forceinline__ int mesh_walk32(const DevField &f, float x, float y, float z, int t,
+                                           float tol)
+{
+    for (int step = 0; step < kMeshWalk; ++step) {
+        const float4 *q = f.tet32 + (kMeshRec / 4) * (int64_t)t;
+        const float4 v = __ldg(q), m0 = __ldg(q + 1), m1 = __ldg(q + 2), m2 = __ldg(q + 3);
+        const float dx = x - v.x, dy = y - v.y, dz = z - v.z;
+        const float l1 = fmaf(m0.x, dx, fmaf(m0.y, dy, m0.z * dz));
+        const float l2 = fmaf(m1.x, dx, fmaf(m1.y, dy, m1.z * dz));
+        const float l3 = fmaf(m2.x, dx, fmaf(m2.y, dy, m2.z * dz));
+        float mn = 1.0f - l1 - l2 - l3;
+        int im = 0;
+        if (l1 < mn) { mn = l1; im = 1; }
+        if (l2 < mn) { mn = l2; im = 2; }
+        if (l3 < mn) { mn = l3; im = 3; }
+        if (mn >= tol * v.w) return t;
+        const int4 nb = __ldg(f.tet_nb + t);
+        t = im == 0 ? nb.x : im == 1 ? nb.y : im == 2 ? nb.z : nb.w;
+        if (t < 0) return -1;
+    }
+    return -1;
+}
+
+// The FP64 search (closed elements) of the position r = (x, y, z), which is
+// (x32, y32, z32) in FP32: an element is tested in FP64 only when its FP32
+// test does not rule it out (every coordinate above minus its margin).
+__device__ __forceinline__ int mesh_find_mixed(const DevField &f, double x, double y, double z,
+                                               float x32, float y32, float z32, int hint)
+{
+    auto holds = [&](int t) {
+        return tet_min32(f.tet32 + (kMeshRec / 4) * (int64_t)t, x32, y32, z32) >= -1.0f &&
+               tet_min64(f.tet64 + kMeshRec * (int64_t)t, x, y, z) >= 0.0;
+    };
+    if (hint >= 0) {  // the hint, then its face neighbours
+        if (holds(hint)) return hint;
+        const int4 nb = __ldg(f.tet_nb + hint);
+        if (nb.x >= 0 && holds(nb.x)) return nb.x;
+        if (nb.y >= 0 && holds(nb.y)) return nb.y;
+        if (nb.z >= 0 && holds(nb.z)) return nb.z;
+        if (nb.w >= 0 && holds(nb.w)) return nb.w;
+    }
+    const int c = mesh_bin<float>(f.bin_n, f.bin_lo_f, f.bin_inv_f, x32, y32, z32);
+    if (c < 0) return -1;
+    const int e = __ldg(f.bin_start + c + 1);
+    for (int i = __ldg(f.bin_start + c); i < e; ++i) {
+        const int t = __ldg(f.bin_tets + i);
+        if (holds(t)) return t;
     }
     return -1;
 }
@@ -416,7 +477,7 @@ __device__ __forceinline__ void field32(const DevField &f, float plate_e, float 
         const float s = __fdividef(f.coax_k_f, x * x + y * y);
         ex = s * x; ey = s * y; ez = 0.f;
     } else if (FK == GT_FIELD_MESH) {
-        const int t = mesh_find32(f, x, y, z, -1, -f.mesh_tol_f);
+        const int t = mesh_find32(f, x, y, z, -1, -1.0f);
         if (t < 0) {
             ex = ey = ez = 0.f;
         } else {
@@ -816,6 +877,7 @@ __device__ __forceinline__ void store_birth(const RunParams &p, int64_t s, const
     parent.position(p, p.x0[s], p.y0[s], p.z0[s], p.t0[s]);
     p.e0[s] = (double)c.e;
     p.bvx[s] = (double)c.vx; p.bvy[s] = (double)c.vy; p.bvz[s] = (double)c.vz;
+    p.belem[s] = parent.birth_elem();  // a new electron starts in its parent's element
     p.uid[s] = c.uid;
     p.aval[s] = parent.aval;
     p.status[s] = 0;
@@ -1225,6 +1287,7 @@ struct Fp64Electron {
 
     template <int FK>
     __device__ __forceinline__ void round_end(const RunParams &) {}
+    __device__ __forceinline__ int birth_elem() const { return -1; }
 
     __device__ void write_end(const RunParams &p) const
     {
@@ -1309,7 +1372,7 @@ struct MixedElectron {
     {
         if (FK == GT_FIELD_MESH) {
             const float x = px + ox, y = py + oy, z = pz + oz;
-            if (elem < 0) elem = mesh_find32(p.field, x, y, z, -1, -p.field.mesh_tol_f);
+            if (elem < 0) elem = mesh_find32(p.field, x, y, z, -1, -1.0f);
             if (elem < 0) {
                 ex = ey = ez = 0.f;
                 return;
@@ -1437,7 +1500,7 @@ struct MixedElectron {
         nf = nreal = nnull = 0;
         status = 0;
         timed = false;
-        elem = -1;
+        elem = FK == GT_FIELD_MESH ? p.belem[s] : -1;
         set_base<FK>(p, p.x0[s], p.y0[s], p.z0[s], p.t0[s]);
         if (GEO) signal_start(p);
     }
@@ -1465,7 +1528,8 @@ struct MixedElectron {
                               (rx > f.box_hi_f[0]) || (ry < f.box_lo_f[1]) ||
                               (ry > f.box_hi_f[1]) || (rz < f.box_lo_f[2]) || (rz > f.box_hi_f[2]);
             if (!near) {
-                const int t = mesh_find32(f, rx, ry, rz, elem, f.mesh_tol_f);
+                int t = elem >= 0 ? mesh_walk32(f, rx, ry, rz, elem, 1.0f) : -1;
+                if (t < 0) t = mesh_find32(f, rx, ry, rz, -1, 1.0f);
                 if (t >= 0) {
                     elem = t;
                     return 0;
@@ -1474,7 +1538,7 @@ struct MixedElectron {
             const unsigned S = blockDim.x;
             const double x = b[0] + (double)ox, y = b[S] + (double)oy, z = b[2 * S] + (double)oz;
             if (f.wire_r2 > 0.0 && x * x + y * y <= f.wire_r2) return GT_ST_WIRE;
-            const int t = mesh_find64(f, x, y, z, elem, 0.0);
+            const int t = mesh_find_mixed(f, x, y, z, rx, ry, rz, elem);
             if (t < 0) return GT_ST_OUT_OF_MAP;
             elem = t;
             return 0;
@@ -1764,6 +1828,7 @@ struct MixedElectron {
     {
         flush<FK>(p);
     }
+    __device__ __forceinline__ int birth_elem() const { return elem; }
 
     __device__ void write_end(const RunParams &p) const
     {

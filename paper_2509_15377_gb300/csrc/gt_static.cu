@@ -21,12 +21,13 @@ namespace {
 
 // Layout of the batched run's work space for GT_STATIC_MAX_ELECTRONS slots
 // and GT_STATIC_MAX_AVALANCHES avalanches with device-resident primaries:
-// header, ready flags (u32), birth velocity (3 x f64), created counters
-// (u64), every region rounded up to 256 bytes.
+// header, ready flags (u32), birth velocity (3 x f64), birth element (i32),
+// created counters (u64), every region rounded up to 256 bytes.
 constexpr size_t round256(size_t x) { return (x + 255) & ~(size_t)255; }
 constexpr size_t kStaticBytes =
     round256(sizeof(gt::Header)) + round256(sizeof(uint32_t) * GT_STATIC_MAX_ELECTRONS) +
     3 * round256(sizeof(double) * GT_STATIC_MAX_ELECTRONS) +
+    round256(sizeof(int32_t) * GT_STATIC_MAX_ELECTRONS) +
     round256(sizeof(unsigned long long) * GT_STATIC_MAX_AVALANCHES) + 256;
 static_assert(kStaticBytes == GT_STATIC_SCRATCH_BYTES, "header constant out of date");
 

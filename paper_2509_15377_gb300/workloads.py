@@ -335,13 +335,22 @@ def box_mesh(cells, lo, hi, jitter: float = 0.15, seed: int = 0):
 
 def coax_mesh_map(cells: int = 8, half_width: float = 0.15, length: float = 1.0,
                   jitter: float = 0.15, wire_r: float = 25e-4, tube_r: float = 0.5,
-                  voltage: float = 1500.0, seed: int = 0) -> Field:
+                  voltage: float = 1500.0, seed: int = 0, grading: float = 0.0) -> Field:
     """The coaxial field on a jittered tetrahedral mesh of [-w, w]^2 x
     [0, length] (cells^3 cubes, six tetrahedra each), sampled at the nodes
     as coax_grid_map samples its grid (r clamped at the wire radius); the
-    4th nodal value is the wire's weighting potential."""
+    4th nodal value is the wire's weighting potential.  grading = a > 0
+    refines the mesh towards the wire: x and y become w sinh(a x/w)/sinh(a)
+    (cells about cosh(a) times finer on the axis than at the box's side)."""
     nodes, tets = box_mesh((cells, cells, cells), (-half_width, -half_width, 0.0),
                            (half_width, half_width, length), jitter, seed)
+    if grading > 0.0:
+        nodes[:, :2] = half_width * np.sinh(grading * nodes[:, :2] / half_width) / math.sinh(grading)
+        v = nodes[tets]
+        det = np.einsum("ij,ij->i", v[:, 1] - v[:, 0],
+                        np.cross(v[:, 2] - v[:, 0], v[:, 3] - v[:, 0]))
+        if not np.all(det > 0.0):
+            raise ValueError("grading turned an element over")
     x, y = nodes[:, 0], nodes[:, 1]
     r2 = np.maximum(x * x + y * y, wire_r * wire_r)
     s = voltage / (math.log(tube_r / wire_r) * r2)
@@ -365,13 +374,13 @@ def uniform_mesh_map(e0: float, half_width: float, cells: int = 6, jitter: float
 
 def mesh_coax(n_avalanches: int = 64, cells: int = 8, voltage: float = 1810.0,
               r_start: float = 0.1, k_exc: float = ARGON_LIKE_K_EXC, t_max: float = 1000.0,
-              seed: int = 0) -> Workload:
+              seed: int = 0, grading: float = 0.0) -> Workload:
     """The grid workload's geometry on a tetrahedral mesh: coax field sampled
-    at the nodes of a jittered mesh of the map box; one primary per
-    avalanche at r = r_start, random phi, mid-length."""
+    at the nodes of a jittered (optionally graded) mesh of the map box; one
+    primary per avalanche at r = r_start, random phi, mid-length."""
     rng = np.random.default_rng(seed)
     phi = rng.uniform(0.0, 2.0 * math.pi, n_avalanches)
-    f = coax_mesh_map(cells=cells, voltage=voltage, seed=seed)
+    f = coax_mesh_map(cells=cells, voltage=voltage, seed=seed, grading=grading)
     prim = _primaries(rng, r_start * np.cos(phi), r_start * np.sin(phi),
                       np.full(n_avalanches, 0.5), np.arange(n_avalanches), n_avalanches)
     return Workload("mesh_coax", argon_like_gas(k_exc), f, prim, t_max, 0, seed)

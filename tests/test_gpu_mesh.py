@@ -144,6 +144,33 @@ def test_mixed_mesh_distributions(av):
         assert abs(fr - fg) < 0.05, (s, fr, fg)
 
 
+def test_mixed_mesh_follows_fp64_over_a_few_flights(av):
+    """Over a few flights the mixed step stays on the FP64 trajectories, on a
+    mesh graded towards the wire where electrons cross elements often: a
+    wrong element (a search or walk slip) would show as a field error."""
+    n = 200
+    w = _near_wire(n, seed=33)
+    w.field = W.coax_mesh_map(cells=12, half_width=0.02, length=0.05, voltage=1500.0, seed=33,
+                              grading=3.0)
+    r = np.random.default_rng(34).uniform(0.003, 0.008, n)
+    ph = np.random.default_rng(35).uniform(0, 2 * math.pi, n)
+    w.primaries.x[:] = r * np.cos(ph)
+    w.primaries.y[:] = r * np.sin(ph)
+    _setup(av, w)
+    t_max = 0.01
+    ref = oracle.run(w.gas, w.field, w.primaries, seed=33, t_max=t_max)
+    _, out = run_gpu(av, w, seed=33, t_max=t_max, precision=A.GT_MIXED,
+                     capacity=4 * len(ref["uid"]) + 64)
+    g, o = by_uid(out), by_uid(ref)
+    prim = (g["uid"] < n) & np.isin(g["uid"], o["uid"])
+    gi = np.nonzero(prim)[0]
+    oi = np.searchsorted(o["uid"], g["uid"][gi])
+    d = np.max(np.abs(np.stack([g[k][gi] - o[k][oi] for k in ("x1", "y1", "z1")])), axis=0)
+    same = (d < 1e-6) & (g["status"][gi] == o["status"][oi]) & (g["n_flight"][gi] == o["n_flight"][oi])
+    assert np.mean(o["n_flight"][oi]) > 3
+    assert same.mean() > 0.9, (same.mean(), np.sort(d)[-10:])
+
+
 def test_mesh_setup_rejects_bad_meshes(av):
     f = W.coax_mesh_map(cells=2, half_width=0.02, length=0.05, seed=1)
     bad = W.Field(W.MESH, mesh_nodes=f.mesh_nodes, mesh_tets=f.mesh_tets.copy(),

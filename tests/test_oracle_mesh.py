@@ -27,10 +27,12 @@ def _tet_volumes(f):
                      np.cross(v[:, 2] - v[:, 0], v[:, 3] - v[:, 0])) / 6.0
 
 
-def test_mesh_tiles_its_box(coax_mesh):
+@pytest.mark.parametrize("grading", [0.0, 3.0])
+def test_mesh_tiles_its_box(coax_mesh, grading):
     """Positive volumes summing to the box; every interior point lies in
-    exactly one element (counted with a separate linear solve per element)."""
-    f = coax_mesh
+    exactly one element (counted with a separate linear solve per element);
+    also for a mesh graded towards the axis."""
+    f = coax_mesh if grading == 0.0 else W.coax_mesh_map(cells=6, seed=3, grading=grading)
     vol = _tet_volumes(f)
     assert vol.min() > 0.0
     assert vol.sum() == pytest.approx(0.3 * 0.3 * 1.0, rel=1e-12)
