@@ -182,8 +182,10 @@ def field_map_lines(av, args, seed: int, cap: int, stream, flush, majorant) -> d
     """Field maps of the coax geometry (the grid workload's box, 1810 V, one
     primary at r = 1 mm per avalanche): the regular 256^3 grid and a
     tetrahedral mesh of the same box (48^3 jittered cubes graded towards the
-    wire, six elements each), batched mixed, each kernel autotuned unless a
-    launch shape is given."""
+    wire, six elements each), batched mixed.  Launch shapes are fixed per map
+    (the best of fixed-shape runs of the full workload; the autotuner's small
+    samples, a few avalanches growing from one electron each, are starved of
+    parallelism and pick poorly) unless given on the command line."""
     from paper_2509_15377_gb300 import avalanche as A
     from paper_2509_15377_gb300 import workloads as W
     maps = {}
@@ -196,14 +198,13 @@ def field_map_lines(av, args, seed: int, cap: int, stream, flush, majorant) -> d
             wl = W.mesh_coax(n_avalanches=n_map, cells=48, seed=seed, grading=4.0)
         av.set_gas(wl.gas)
         av.set_field(wl.field)
+        given = args.block or args.refill_period or args.flights_per_phase
+        shape = ((args.block, args.refill_period, args.flights_per_phase) if given
+                 else (512, 4, 1) if name == "grid" else (512, 32, 1))
         m_opt = A.RunOptions(seed=seed, t_max=wl.t_max, precision=A.GT_MIXED, mode=A.GT_BATCHED,
-                             block=args.block, refill_period=args.refill_period,
-                             flights_per_phase=args.flights_per_phase, majorant=majorant,
-                             majorant_window=args.window)
+                             block=shape[0], refill_period=shape[1], flights_per_phase=shape[2],
+                             majorant=majorant, majorant_window=args.window)
         m_dev = av.primaries_device(wl.primaries)
-        if not args.no_autotune and not (args.block or args.refill_period or args.flights_per_phase):
-            av.autotune(av.primaries_device(wl.primaries.subset(list(range(min(16, n_map))))),
-                        m_opt, cap, stream=stream)
         m_real, m_ms, m_fl = 0, 0.0, 0
         for _ in range(2):
             flush.fill_(1)
