@@ -144,10 +144,12 @@ def test_mixed_mesh_distributions(av):
         assert abs(fr - fg) < 0.05, (s, fr, fg)
 
 
-def test_mixed_mesh_follows_fp64_over_a_few_flights(av):
+@pytest.mark.parametrize("geo", [{}, {"substeps": 2, "crossing": True}])
+def test_mixed_mesh_follows_fp64_over_a_few_flights(av, geo):
     """Over a few flights the mixed step stays on the FP64 trajectories, on a
     mesh graded towards the wire where electrons cross elements often: a
-    wrong element (a search or walk slip) would show as a field error."""
+    wrong element (a search or walk slip) would show as a field error.  Also
+    with sub-steps and exact crossings (the FP32 bisection on the mesh)."""
     n = 200
     w = _near_wire(n, seed=33)
     w.field = W.coax_mesh_map(cells=12, half_width=0.02, length=0.05, voltage=1500.0, seed=33,
@@ -158,9 +160,10 @@ def test_mixed_mesh_follows_fp64_over_a_few_flights(av):
     w.primaries.y[:] = r * np.sin(ph)
     _setup(av, w)
     t_max = 0.01
-    ref = oracle.run(w.gas, w.field, w.primaries, seed=33, t_max=t_max)
+    ref = oracle.run(w.gas, w.field, w.primaries, seed=33, t_max=t_max, **geo)
     _, out = run_gpu(av, w, seed=33, t_max=t_max, precision=A.GT_MIXED,
-                     capacity=4 * len(ref["uid"]) + 64)
+                     capacity=4 * len(ref["uid"]) + 64, substeps=geo.get("substeps", 0),
+                     crossing=int(geo.get("crossing", False)))
     g, o = by_uid(out), by_uid(ref)
     prim = (g["uid"] < n) & np.isin(g["uid"], o["uid"])
     gi = np.nonzero(prim)[0]
