@@ -329,7 +329,13 @@ int gt_gas_nu_max(gt_ctx *ctx, double *nu_max);
 
 /* Set the field and geometry used by later runs (Sec. 3.1: the field data
  * is transferred once, before the first transport).  The GRID map stays in
- * caller memory and is read by pointer. */
+ * caller memory and is read by pointer.  A MESH is copied from the host
+ * arrays and turned into element records, face neighbours and search bins
+ * held by the context (replaced by the next field_setup, freed by
+ * gt_destroy).  GT_ERR_ARG for an unknown kind, a non-finite or
+ * non-positive size, a node index out of range, an element of zero volume,
+ * a face shared by more than two elements or a non-finite nodal value;
+ * GT_ERR_CUDA if a device allocation or copy fails. */
 int field_setup(gt_ctx *ctx, const gt_field *field);
 
 /* Work-space bytes that avalanche_run needs for `run` with endpoint
