@@ -144,16 +144,25 @@ def test_mixed_mesh_distributions(av):
         assert abs(fr - fg) < 0.05, (s, fr, fg)
 
 
-@pytest.mark.parametrize("geo", [{}, {"substeps": 2, "crossing": True}])
+@pytest.mark.parametrize("geo", [{}, {"substeps": 2, "crossing": True}, {"hole": True}])
 def test_mixed_mesh_follows_fp64_over_a_few_flights(av, geo):
     """Over a few flights the mixed step stays on the FP64 trajectories, on a
     mesh graded towards the wire where electrons cross elements often: a
     wrong element (a search or walk slip) would show as a field error.  Also
-    with sub-steps and exact crossings (the FP32 bisection on the mesh)."""
+    with sub-steps and exact crossings (the FP32 bisection on the mesh), and
+    with a hole on the electrons' way (the decision that a point is in no
+    element, taken in FP64 near the hole's faces)."""
     n = 200
+    geo = dict(geo)
+    hole = geo.pop("hole", False)
     w = _near_wire(n, seed=33)
     w.field = W.coax_mesh_map(cells=12, half_width=0.02, length=0.05, voltage=1500.0, seed=33,
                               grading=3.0)
+    if hole:  # the elements of one quadrant between 40 and 55 um from the axis
+        c = w.field.mesh_nodes[w.field.mesh_tets].mean(axis=1)
+        rc = np.hypot(c[:, 0], c[:, 1])
+        keep = ~((c[:, 0] > 0.0) & (c[:, 1] > 0.0) & (rc > 0.004) & (rc < 0.0055))
+        w.field.mesh_tets = np.ascontiguousarray(w.field.mesh_tets[keep])
     r = np.random.default_rng(34).uniform(0.003, 0.008, n)
     ph = np.random.default_rng(35).uniform(0, 2 * math.pi, n)
     w.primaries.x[:] = r * np.cos(ph)
@@ -172,6 +181,9 @@ def test_mixed_mesh_follows_fp64_over_a_few_flights(av, geo):
     same = (d < 1e-6) & (g["status"][gi] == o["status"][oi]) & (g["n_flight"][gi] == o["n_flight"][oi])
     assert np.mean(o["n_flight"][oi]) > 3
     assert same.mean() > 0.9, (same.mean(), np.sort(d)[-10:])
+    if hole:
+        assert (o["status"] == W.OUT_OF_MAP).sum() > 0
+        assert abs((g["status"] == W.OUT_OF_MAP).mean() - (o["status"] == W.OUT_OF_MAP).mean()) < 0.05
 
 
 def test_mesh_setup_rejects_bad_meshes(av):
