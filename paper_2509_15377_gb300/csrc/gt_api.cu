@@ -565,10 +565,15 @@ static int build_mesh(gt_ctx *ctx, const gt_field *f, DevField &d)
         inv[k] = nb[k] / ext[k];
     }
     std::vector<int64_t> count(ncell + 1, 0);
+    // an element's box is padded by more than the FP32 rounding of a
+    // coordinate, so that an FP32 position falls in a bin that lists it
+    double pad[3];
+    for (int k = 0; k < 3; ++k)
+        pad[k] = std::max(1e-4 * h[k], 4.0 * 1.1920928955078125e-7 *
+                                           std::max(std::fabs(lo[k]), std::fabs(hi[k])));
     auto range = [&](int64_t t, int k, int &i0, int &i1) {
-        const double pad = 1e-6 * h[k];
-        i0 = (int)std::floor((box[6 * t + k] - pad - lo[k]) * inv[k]);
-        i1 = (int)std::floor((box[6 * t + 3 + k] + pad - lo[k]) * inv[k]);
+        i0 = (int)std::floor((box[6 * t + k] - pad[k] - lo[k]) * inv[k]);
+        i1 = (int)std::floor((box[6 * t + 3 + k] + pad[k] - lo[k]) * inv[k]);
         i0 = std::min(std::max(i0, 0), nb[k] - 1);
         i1 = std::min(std::max(i1, 0), nb[k] - 1);
     };

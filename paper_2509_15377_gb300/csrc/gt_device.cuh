@@ -386,7 +386,7 @@ __device__ __forceinline__ int mesh_find_mixed(const DevField &f, double x, doub
         if (nb.z >= 0 && holds(nb.z)) return nb.z;
         if (nb.w >= 0 && holds(nb.w)) return nb.w;
     }
-    const int c = mesh_bin<float>(f.bin_n, f.bin_lo_f, f.bin_inv_f, x32, y32, z32);
+    const int c = mesh_bin<double>(f.bin_n, f.bin_lo, f.bin_inv, x, y, z);
     if (c < 0) return -1;
     const int e = __ldg(f.bin_start + c + 1);
     for (int i = __ldg(f.bin_start + c); i < e; ++i) {
@@ -1373,6 +1373,11 @@ struct MixedElectron {
         if (FK == GT_FIELD_MESH) {
             const float x = px + ox, y = py + oy, z = pz + oz;
             if (elem < 0) elem = mesh_find32(p.field, x, y, z, -1, -1.0f);
+            if (elem < 0) {  // the FP32 position's bin missed: search in FP64
+                const unsigned S = blockDim.x;
+                elem = mesh_find64(p.field, b[0] + (double)ox, b[S] + (double)oy,
+                                   b[2 * S] + (double)oz, -1, 0.0);
+            }
             if (elem < 0) {
                 ex = ey = ez = 0.f;
                 return;
