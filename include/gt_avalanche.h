@@ -397,6 +397,10 @@ int avalanche_run_static(gt_ctx *ctx, const gt_run *run, const gt_endpoints *out
  *   gt_graph_launch   enqueues a replay on `stream` with `seed` (a seed that
  *                     differs from the last one records the graph again and
  *                     updates it in place, tens of microseconds on the host);
+ *                     GT_ERR_STATE once gas_table_upload or field_setup has
+ *                     run on the context after the graph was created (the
+ *                     graph holds the tables of its own setup: create a new
+ *                     graph);
  *   gt_graph_stats    waits for the last replay and returns its summary and
  *                     status (as avalanche_run; GT_ERR_STATE before a launch);
  *   gt_graph_destroy  releases it (after its replays have finished).

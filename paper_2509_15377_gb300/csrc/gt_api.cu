@@ -8,6 +8,7 @@
 #include <cstdio>
 #include <cstring>
 #include <new>
+#include <utility>
 #include <vector>
 
 #include "gt_avalanche.h"
@@ -45,6 +46,9 @@ struct gt_ctx {
     double *d_tet64 = nullptr;
     int *d_tet_nb = nullptr;
     int *d_bin_start = nullptr, *d_bin_tets = nullptr;
+    // counts gas_table_upload and field_setup calls that replaced device
+    // tables: a captured graph holds the tables of its own setup
+    unsigned long long setup_gen = 0;
     char last_error[256] = {0};
 };
 
@@ -381,6 +385,7 @@ int gas_table_upload(gt_ctx *ctx, const gt_gas *g)
     for (int j = 0; j < L; ++j)
         if (d.type[j] == GT_LEVEL_ATTACHMENT) d.any_special = 1;
     ctx->has_gas = true;
+    ++ctx->setup_gen;
     return GT_OK;
 }
 
@@ -604,30 +609,41 @@ static int build_mesh(gt_ctx *ctx, const gt_field *f, DevField &d)
             for (size_t i = 0; i < rec.size(); ++i) rec32[i] = (float)rec[i];
             DeviceGuard dg(ctx->device);
             if (!dg.ok) return GT_ERR_CUDA;
-            if (ctx->d_tet32) cudaFree(ctx->d_tet32);
-            if (ctx->d_tet64) cudaFree(ctx->d_tet64);
-            if (ctx->d_tet_nb) cudaFree(ctx->d_tet_nb);
-            if (ctx->d_bin_start) cudaFree(ctx->d_bin_start);
-            if (ctx->d_bin_tets) cudaFree(ctx->d_bin_tets);
-            ctx->d_tet32 = nullptr; ctx->d_tet64 = nullptr; ctx->d_tet_nb = nullptr;
-            ctx->d_bin_start = nullptr; ctx->d_bin_tets = nullptr;
-            GT_CUDA(ctx, cudaMalloc((void **)&ctx->d_tet32, sizeof(float) * rec32.size()));
-            GT_CUDA(ctx, cudaMalloc((void **)&ctx->d_tet64, sizeof(double) * rec.size()));
-            GT_CUDA(ctx, cudaMalloc((void **)&ctx->d_tet_nb, sizeof(int) * nbr.size()));
-            GT_CUDA(ctx, cudaMemcpy(ctx->d_tet_nb, nbr.data(), sizeof(int) * nbr.size(),
-                                    cudaMemcpyHostToDevice));
-            GT_CUDA(ctx, cudaMalloc((void **)&ctx->d_bin_start, sizeof(int) * start.size()));
-            GT_CUDA(ctx, cudaMalloc((void **)&ctx->d_bin_tets,
+            // the new buffers are filled first and replace the context's only
+            // then, so that a failure leaves the previous field intact; the
+            // holder frees whichever set it ends up with
+            struct MeshBuffers {
+                float *tet32 = nullptr;
+                double *tet64 = nullptr;
+                int *nb = nullptr, *start = nullptr, *tets = nullptr;
+                ~MeshBuffers()
+                {
+                    cudaFree(tet32); cudaFree(tet64); cudaFree(nb);
+                    cudaFree(start); cudaFree(tets);
+                }
+            } nbuf;
+            GT_CUDA(ctx, cudaMalloc((void **)&nbuf.tet32, sizeof(float) * rec32.size()));
+            GT_CUDA(ctx, cudaMalloc((void **)&nbuf.tet64, sizeof(double) * rec.size()));
+            GT_CUDA(ctx, cudaMalloc((void **)&nbuf.nb, sizeof(int) * nbr.size()));
+            GT_CUDA(ctx, cudaMalloc((void **)&nbuf.start, sizeof(int) * start.size()));
+            GT_CUDA(ctx, cudaMalloc((void **)&nbuf.tets,
                                     sizeof(int) * std::max<size_t>(tets.size(), 1)));
-            GT_CUDA(ctx, cudaMemcpy(ctx->d_tet32, rec32.data(), sizeof(float) * rec32.size(),
+            GT_CUDA(ctx, cudaMemcpy(nbuf.tet32, rec32.data(), sizeof(float) * rec32.size(),
                                     cudaMemcpyHostToDevice));
-            GT_CUDA(ctx, cudaMemcpy(ctx->d_tet64, rec.data(), sizeof(double) * rec.size(),
+            GT_CUDA(ctx, cudaMemcpy(nbuf.tet64, rec.data(), sizeof(double) * rec.size(),
                                     cudaMemcpyHostToDevice));
-            GT_CUDA(ctx, cudaMemcpy(ctx->d_bin_start, start.data(), sizeof(int) * start.size(),
+            GT_CUDA(ctx, cudaMemcpy(nbuf.nb, nbr.data(), sizeof(int) * nbr.size(),
+                                    cudaMemcpyHostToDevice));
+            GT_CUDA(ctx, cudaMemcpy(nbuf.start, start.data(), sizeof(int) * start.size(),
                                     cudaMemcpyHostToDevice));
             if (!tets.empty())
-                GT_CUDA(ctx, cudaMemcpy(ctx->d_bin_tets, tets.data(), sizeof(int) * tets.size(),
+                GT_CUDA(ctx, cudaMemcpy(nbuf.tets, tets.data(), sizeof(int) * tets.size(),
                                         cudaMemcpyHostToDevice));
+            std::swap(ctx->d_tet32, nbuf.tet32);
+            std::swap(ctx->d_tet64, nbuf.tet64);
+            std::swap(ctx->d_tet_nb, nbuf.nb);
+            std::swap(ctx->d_bin_start, nbuf.start);
+            std::swap(ctx->d_bin_tets, nbuf.tets);
         }
     }
     d.tet32 = reinterpret_cast<const float4 *>(ctx->d_tet32);
@@ -737,6 +753,14 @@ int field_setup(gt_ctx *ctx, const gt_field *f)
     d.tube_r2_lo_f = (float)(d.tube_r2 * 0.99999);
     ctx->field = d;
     ctx->has_field = true;
+    ++ctx->setup_gen;
+    if (d.kind != GT_FIELD_MESH && ctx->d_tet32) {  // a previous mesh is no longer used
+        DeviceGuard dg(ctx->device);
+        cudaFree(ctx->d_tet32); cudaFree(ctx->d_tet64); cudaFree(ctx->d_tet_nb);
+        cudaFree(ctx->d_bin_start); cudaFree(ctx->d_bin_tets);
+        ctx->d_tet32 = nullptr; ctx->d_tet64 = nullptr; ctx->d_tet_nb = nullptr;
+        ctx->d_bin_start = nullptr; ctx->d_bin_tets = nullptr;
+    }
     return GT_OK;
 }
 
@@ -1154,6 +1178,7 @@ struct gt_graph {
     cudaEvent_t ev0 = nullptr, ev1 = nullptr, ev2 = nullptr;  // transport start/end, run end
     Header *h_hdr = nullptr;       // pinned, written by the graph's last copy
     uint64_t seed = 0;
+    unsigned long long setup_gen = 0;  // the context's setup the graph was recorded with
     bool launched = false;
 };
 
@@ -1210,6 +1235,7 @@ int gt_graph_create(gt_ctx *ctx, const gt_run *run, const gt_endpoints *out, voi
     g->o = *out;
     g->na = run->n_avalanches;
     g->seed = run->seed;
+    g->setup_gen = ctx->setup_gen;
     cudaGraph_t gr = nullptr;
     if (cudaStreamCreateWithFlags(&g->cap, cudaStreamNonBlocking) != cudaSuccess ||
         cudaEventCreate(&g->ev0) != cudaSuccess || cudaEventCreate(&g->ev1) != cudaSuccess ||
@@ -1237,6 +1263,9 @@ int gt_graph_launch(gt_graph *g, uint64_t seed, void *stream)
 {
     if (!g) return GT_ERR_ARG;
     gt_ctx *ctx = g->ctx;
+    // the gas table or field was set again since the graph was recorded:
+    // its kernels would read the replaced (freed) tables
+    if (g->setup_gen != ctx->setup_gen) return GT_ERR_STATE;
     DeviceGuard dg(ctx->device);
     if (!dg.ok) return GT_ERR_CUDA;
     if (seed != g->seed) {

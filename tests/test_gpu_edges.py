@@ -199,3 +199,31 @@ def test_graph_replays_equal_runs(av):
     with pytest.raises(A.GtError) as e:
         av.graph(av.primaries_pinned(w.primaries), opt, cap)
     assert e.value.code == A.GT_ERR_UNSUPPORTED
+
+
+def test_graph_refuses_a_replaced_setup(av):
+    """A graph holds the gas table and field of the setup it was recorded
+    with: after field_setup (or gas_table_upload) replaces them, a replay is
+    refused with GT_ERR_STATE instead of reading freed tables; a new graph
+    runs."""
+    w = W.plate(n_avalanches=8, e_field=40_000.0, seed=113)
+    av.set_gas(w.gas)
+    av.set_field(w.field)
+    p = av.primaries_device(w.primaries)
+    opt = A.RunOptions(seed=7, t_max=w.t_max, precision=A.GT_MIXED, mode=A.GT_BATCHED)
+    g = av.graph(p, opt, 100_000)
+    try:
+        g.launch(7)
+        g.stats()
+        av.set_field(w.field)
+        with pytest.raises(A.GtError) as e:
+            g.launch(8)
+        assert e.value.code == A.GT_ERR_STATE
+    finally:
+        g.close()
+    g = av.graph(p, opt, 100_000)
+    try:
+        g.launch(8)
+        assert g.stats()["n_endpoints"] > 0
+    finally:
+        g.close()
