@@ -58,8 +58,10 @@ LANES_PER_WARP = 32
 # DRAM bytes per electron of the batched kernel (ncu dram__bytes_read.sum +
 # dram__bytes_write.sum on the 256-avalanche case, divided by its
 # electrons; traffic grows with electrons, so it is scaled to a launch by
-# the electrons the launch stores).  None once the kernel has changed.
-DRAM_BYTES_PER_ELECTRON = 199.8
+# the electrons the launch stores).  None once the kernel has changed: the
+# last capture (199.8 B per electron) predates the 4-byte birth-element
+# field that every new electron now stores.
+DRAM_BYTES_PER_ELECTRON = None
 
 
 # ---------------------------------------------------------------- sharding
