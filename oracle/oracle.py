@@ -158,6 +158,9 @@ def _field_struct(field, keep):
         nodes = np.ascontiguousarray(field.mesh_nodes, np.float64)
         tets = np.ascontiguousarray(field.mesh_tets, np.int32)
         vals = np.ascontiguousarray(field.mesh_values, np.float32)
+        if (nodes.ndim != 2 or nodes.shape[1] != 3 or tets.ndim != 2 or tets.shape[1] != 4 or
+                vals.shape != (nodes.shape[0], 4)):
+            raise ValueError("mesh arrays must be nodes [n, 3], tets [m, 4], values [n, 4]")
         keep.extend([nodes, tets, vals])
         f.n_mesh_nodes, f.n_tets = nodes.shape[0], tets.shape[0]
         f.mesh_nodes, f.mesh_tets, f.mesh_values = _ptr(nodes).value, _ptr(tets).value, _ptr(vals).value

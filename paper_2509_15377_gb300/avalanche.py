@@ -208,6 +208,24 @@ def gas_nu_max(ctx) -> float:
     return v.value
 
 
+def mesh_arrays(field: W.Field):
+    """The mesh's node, element and value arrays as the C ABI reads them
+    (float64 [n, 3], int32 [m, 4], float32 [n, 4], contiguous); ValueError for
+    other shapes, which the library would read past."""
+    if field.mesh_nodes is None or field.mesh_tets is None or field.mesh_values is None:
+        raise ValueError("a MESH field needs mesh_nodes, mesh_tets and mesh_values")
+    nodes = np.ascontiguousarray(field.mesh_nodes, np.float64)
+    tets = np.ascontiguousarray(field.mesh_tets, np.int32)
+    vals = np.ascontiguousarray(field.mesh_values, np.float32)
+    if nodes.ndim != 2 or nodes.shape[1] != 3:
+        raise ValueError(f"mesh_nodes must be [n, 3], got {nodes.shape}")
+    if tets.ndim != 2 or tets.shape[1] != 4:
+        raise ValueError(f"mesh_tets must be [m, 4], got {tets.shape}")
+    if vals.shape != (nodes.shape[0], 4):
+        raise ValueError(f"mesh_values must be [{nodes.shape[0]}, 4], got {vals.shape}")
+    return nodes, tets, vals
+
+
 def field_setup(ctx, field: W.Field, grid_ptr: int = 0) -> None:
     f = gt_field()
     f.kind = field.kind
@@ -221,9 +239,7 @@ def field_setup(ctx, field: W.Field, grid_ptr: int = 0) -> None:
         f.grid = grid_ptr
     keep = []
     if field.kind == W.MESH:
-        nodes = np.ascontiguousarray(field.mesh_nodes, np.float64)
-        tets = np.ascontiguousarray(field.mesh_tets, np.int32)
-        vals = np.ascontiguousarray(field.mesh_values, np.float32)
+        nodes, tets, vals = mesh_arrays(field)
         keep.extend([nodes, tets, vals])  # host arrays, copied by field_setup
         f.n_mesh_nodes, f.n_tets = nodes.shape[0], tets.shape[0]
         f.mesh_nodes, f.mesh_tets, f.mesh_values = (nodes.ctypes.data, tets.ctypes.data,

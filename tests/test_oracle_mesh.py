@@ -129,3 +129,25 @@ def test_constant_field_mesh_transports_like_uniform():
     for k in ("x1", "y1", "z1", "t1", "e1"):
         np.testing.assert_allclose(b[k][ib], a[k][ia], rtol=1e-9, atol=1e-12)
     assert np.abs(np.stack([b["x1"], b["y1"], b["z1"]])).max() < 0.5
+
+
+def test_mesh_arrays_of_the_wrong_shape_are_refused():
+    """The binding and the oracle wrapper refuse mesh arrays whose shapes
+    the C code would read past."""
+    from paper_2509_15377_gb300 import avalanche as A
+    f = W.coax_mesh_map(cells=2, seed=1)
+    bad = [W.Field(W.MESH, mesh_nodes=f.mesh_nodes[:, :2], mesh_tets=f.mesh_tets,
+                   mesh_values=f.mesh_values),
+           W.Field(W.MESH, mesh_nodes=f.mesh_nodes, mesh_tets=f.mesh_tets[:, :3],
+                   mesh_values=f.mesh_values),
+           W.Field(W.MESH, mesh_nodes=f.mesh_nodes, mesh_tets=f.mesh_tets,
+                   mesh_values=f.mesh_values[:-1]),
+           W.Field(W.MESH, mesh_nodes=f.mesh_nodes, mesh_tets=f.mesh_tets,
+                   mesh_values=f.mesh_values[:, :3])]
+    for g in bad:
+        with pytest.raises(ValueError):
+            A.mesh_arrays(g)
+        with pytest.raises(ValueError):
+            oracle.field_eval(g, np.zeros(3))
+    nodes, tets, vals = A.mesh_arrays(f)
+    assert nodes.shape[1] == 3 and tets.shape[1] == 4 and vals.shape == (nodes.shape[0], 4)
