@@ -364,7 +364,11 @@ class Avalanche:
     def set_field(self, field: W.Field):
         ptr = 0
         if field.kind == W.GRID:
-            t = self.torch.from_numpy(np.ascontiguousarray(field.grid, np.float32))
+            g = np.ascontiguousarray(field.grid, np.float32)
+            if g.ndim != 4 or g.shape[3] != 4 or min(g.shape[:3]) < 2:
+                # the kernels read one float4 per node of an [nz, ny, nx] map
+                raise ValueError(f"grid must be [nz, ny, nx, 4] with every n >= 2, got {g.shape}")
+            t = self.torch.from_numpy(g)
             self._grid = t.to(f"cuda:{self.device}")
             ptr = self._grid.data_ptr()
         field_setup(self.ctx, field, ptr)

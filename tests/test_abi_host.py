@@ -6,7 +6,10 @@ import ctypes as C
 import os
 import re
 
+import numpy as np
 import pytest
+
+from paper_2509_15377_gb300 import workloads as W
 
 ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
 HEADER = os.path.join(ROOT, "include", "gt_avalanche.h")
@@ -85,3 +88,13 @@ def test_binding_fails_loudly_without_library(tmp_path):
             A.load(str(tmp_path / "missing.so"))
     finally:
         A._lib = saved
+
+
+def test_grid_maps_of_the_wrong_shape_are_refused():
+    """The binding refuses a grid map that is not [nz, ny, nx, 4] (the
+    kernels read one float4 per node) before touching the device."""
+    from paper_2509_15377_gb300 import avalanche as A
+    av = A.Avalanche.__new__(A.Avalanche)  # no device: the check comes first
+    for shape in ((4, 4, 4, 3), (4, 4, 4), (1, 4, 4, 4)):
+        with pytest.raises(ValueError):
+            av.set_field(W.Field(W.GRID, grid=np.zeros(shape, np.float32)))

@@ -151,3 +151,4 @@ def test_mesh_arrays_of_the_wrong_shape_are_refused():
             oracle.field_eval(g, np.zeros(3))
     nodes, tets, vals = A.mesh_arrays(f)
     assert nodes.shape[1] == 3 and tets.shape[1] == 4 and vals.shape == (nodes.shape[0], 4)
+
