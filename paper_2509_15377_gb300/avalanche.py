@@ -413,8 +413,24 @@ class Avalanche:
         o.signal = self.ep["signal"].data_ptr() if self.ep.get("signal") is not None else None
         return o
 
+    def check_primaries(self, prim: W.Primaries) -> None:
+        """Every per-primary array one-dimensional and of the same length, and
+        the per-avalanche fields (if any) one per avalanche: the seed kernel
+        reads them all by primary (or avalanche) index."""
+        n = prim.n
+        for k in self.PRIM_KEYS + ("aval", "uid"):
+            a = np.asarray(getattr(prim, k))
+            if a.ndim != 1 or a.shape[0] != n:
+                raise ValueError(f"primaries.{k} must have shape ({n},), got {a.shape}")
+        if prim.aval_field is not None:
+            a = np.asarray(prim.aval_field)
+            if a.ndim != 1 or a.shape[0] != prim.n_avalanches:
+                raise ValueError(f"primaries.aval_field must have shape ({prim.n_avalanches},), "
+                                 f"got {a.shape}")
+
     def primaries_device(self, prim: W.Primaries) -> dict:
         """Primaries as device tensors (resident in HBM)."""
+        self.check_primaries(prim)
         torch = self.torch
         dev = f"cuda:{self.device}"
         d = {k: torch.from_numpy(np.ascontiguousarray(getattr(prim, k), np.float64)).to(dev)
@@ -430,6 +446,7 @@ class Avalanche:
 
     def primaries_pinned(self, prim: W.Primaries) -> dict:
         """Primaries in pinned host memory (copied inside each run)."""
+        self.check_primaries(prim)
         torch = self.torch
         d = {k: torch.from_numpy(np.ascontiguousarray(getattr(prim, k), np.float64)).pin_memory()
              for k in self.PRIM_KEYS}

@@ -98,3 +98,23 @@ def test_grid_maps_of_the_wrong_shape_are_refused():
     for shape in ((4, 4, 4, 3), (4, 4, 4), (1, 4, 4, 4)):
         with pytest.raises(ValueError):
             av.set_field(W.Field(W.GRID, grid=np.zeros(shape, np.float32)))
+
+
+def test_primaries_of_unequal_lengths_are_refused():
+    """The binding refuses primaries whose arrays differ in length (or a
+    per-avalanche field of the wrong length) before anything is copied."""
+    from paper_2509_15377_gb300 import avalanche as A
+    av = A.Avalanche.__new__(A.Avalanche)  # no device: the check comes first
+    w = W.plate(n_avalanches=6, e_field=40_000.0, seed=1)
+    av.check_primaries(w.primaries)
+    for key in ("dx", "aval", "uid"):
+        p = W.plate(n_avalanches=6, e_field=40_000.0, seed=1).primaries
+        setattr(p, key, getattr(p, key)[:-1])
+        with pytest.raises(ValueError):
+            av.primaries_device(p)
+        with pytest.raises(ValueError):
+            av.primaries_pinned(p)
+    p = W.plate(n_avalanches=6, e_field=40_000.0, seed=1).primaries
+    p.aval_field = np.full(p.n_avalanches - 1, 40_000.0)
+    with pytest.raises(ValueError):
+        av.primaries_device(p)
