@@ -192,9 +192,12 @@ def gas_table_upload(ctx, gas: W.Gas) -> None:
     rt = np.ascontiguousarray(gas.rate, np.float64)
     xi = None if gas.xi0 is None else np.ascontiguousarray(gas.xi0, np.float64)
     sc = None if gas.screen is None else np.ascontiguousarray(gas.screen, np.float64)
-    for a in (xi, sc):
+    if rt.ndim != 2:
+        raise ValueError(f"rate must be [n_nodes, n_levels], got {rt.shape}")
+    for name, a in (("level_type", lt), ("threshold", th), ("xi0", xi), ("screen", sc)):
+        # the library reads one value per level from each
         if a is not None and a.shape != (rt.shape[1],):
-            raise ValueError("xi0 / screen need one value per level")
+            raise ValueError(f"{name} needs one value per level ({rt.shape[1]}), got {a.shape}")
     g = gt_gas(rt.shape[1], rt.shape[0], gas.d_eps, lt.ctypes.data, th.ctypes.data,
                rt.ctypes.data, gas.recoil, gas.nu_max, gas.band_width,
                xi.ctypes.data if xi is not None else None,

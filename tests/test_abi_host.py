@@ -118,3 +118,17 @@ def test_primaries_of_unequal_lengths_are_refused():
     p.aval_field = np.full(p.n_avalanches - 1, 40_000.0)
     with pytest.raises(ValueError):
         av.primaries_device(p)
+
+
+def test_gas_arrays_of_the_wrong_length_are_refused():
+    """The binding refuses a gas whose per-level arrays do not match the
+    rate table's levels, before the library reads them."""
+    import dataclasses
+    from paper_2509_15377_gb300 import avalanche as A
+    g = W.argon_like_gas()
+    for name in ("level_type", "threshold"):
+        bad = dataclasses.replace(g, **{name: np.asarray(getattr(g, name))[:-1]})
+        with pytest.raises(ValueError):
+            A.gas_table_upload(None, bad)
+    with pytest.raises(ValueError):
+        A.gas_table_upload(None, dataclasses.replace(g, rate=np.asarray(g.rate).ravel()))
