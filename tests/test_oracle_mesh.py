@@ -152,3 +152,25 @@ def test_mesh_arrays_of_the_wrong_shape_are_refused():
     nodes, tets, vals = A.mesh_arrays(f)
     assert nodes.shape[1] == 3 and tets.shape[1] == 4 and vals.shape == (nodes.shape[0], 4)
 
+
+
+def test_mesh_signal_telescopes():
+    """Shockley-Ramo on a mesh: an avalanche's signal summed over its bins is
+    the sum over its electrons of the weighting potential at the end minus
+    at the start (every electron's life inside the binned window)."""
+    f = W.coax_mesh_map(cells=6, half_width=0.02, length=0.05, voltage=1500.0, seed=9)
+    w = W.mesh_coax(n_avalanches=12, cells=2, seed=9)
+    w.field = f
+    ph = np.random.default_rng(9).uniform(0, 2 * np.pi, 12)
+    w.primaries.x[:] = 0.008 * np.cos(ph)
+    w.primaries.y[:] = 0.008 * np.sin(ph)
+    w.primaries.z[:] = 0.025
+    t_max = 0.3
+    out = oracle.run(w.gas, f, w.primaries, seed=9, t_max=t_max, signal=(W.W_MAP, 100, 0.0, 0.003))
+    phi = lambda x, y, z: np.array([oracle.weighting_potential(f, W.W_MAP, np.array(p))
+                                    for p in zip(x, y, z)])
+    d = phi(out["x1"], out["y1"], out["z1"]) - phi(out["x0"], out["y0"], out["z0"])
+    expect = np.bincount(out["aval"], weights=d, minlength=12)
+    assert np.abs(expect).max() > 0.0
+    np.testing.assert_allclose(out["signal"].sum(axis=1), expect, rtol=1e-9,
+                               atol=1e-12 * np.abs(expect).max())
