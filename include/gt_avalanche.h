@@ -57,6 +57,7 @@ extern "C" {
 #define GT_ERR_CUDA (-6)           /* a CUDA runtime call failed */
 #define GT_ERR_NO_DEVICE (-7)      /* no usable CUDA device */
 #define GT_ERR_UNSUPPORTED (-8)    /* combination not implemented */
+#define GT_ERR_HOST_MEMORY (-9)    /* a host allocation failed (e.g. a very large mesh) */
 
 /* ---- electron status codes (endpoint.status; non-zero = finished) ---- */
 #define GT_ST_ACTIVE 0        /* not finished (only in a partial result) */

@@ -25,6 +25,7 @@ LIB_PATH = os.path.join(_PKG, "_build", "libgt_avalanche.so")
 GT_OK, GT_ERR_ARG, GT_ERR_STATE, GT_ERR_WORKSPACE = 0, -1, -2, -3
 GT_ERR_QUEUE_OVERFLOW, GT_ERR_TIMEOUT, GT_ERR_CUDA, GT_ERR_NO_DEVICE = -4, -5, -6, -7
 GT_ERR_UNSUPPORTED = -8
+GT_ERR_HOST_MEMORY = -9
 GT_FP64, GT_MIXED = 0, 1
 GT_BATCHED, GT_PLAIN = 0, 1
 GT_DEBUG_UNFILLED_SLOT = 1

@@ -182,6 +182,7 @@ const char *gt_strerror(int code)
     case GT_ERR_CUDA: return "CUDA runtime error";
     case GT_ERR_NO_DEVICE: return "no usable sm_103 CUDA device";
     case GT_ERR_UNSUPPORTED: return "unsupported combination";
+    case GT_ERR_HOST_MEMORY: return "host allocation failed";
     default: return "unknown error";
     }
 }
@@ -253,7 +254,42 @@ int gt_destroy(gt_ctx *ctx)
     return GT_OK;
 }
 
+static int gas_table_upload_impl(gt_ctx *ctx, const gt_gas *g);
+static int field_setup_impl(gt_ctx *ctx, const gt_field *f);
+static int avalanche_run_impl(gt_ctx *ctx, const gt_run *r, const gt_endpoints *o, void *ws,
+                              size_t ws_bytes, void *stream, gt_stats *stats);
+
+// The entry points that build host-side tables catch a failed host
+// allocation: nothing throws across the C ABI.
 int gas_table_upload(gt_ctx *ctx, const gt_gas *g)
+{
+    try {
+        return gas_table_upload_impl(ctx, g);
+    } catch (const std::bad_alloc &) {
+        return GT_ERR_HOST_MEMORY;
+    }
+}
+
+int field_setup(gt_ctx *ctx, const gt_field *f)
+{
+    try {
+        return field_setup_impl(ctx, f);
+    } catch (const std::bad_alloc &) {
+        return GT_ERR_HOST_MEMORY;
+    }
+}
+
+int avalanche_run(gt_ctx *ctx, const gt_run *r, const gt_endpoints *o, void *ws, size_t ws_bytes,
+                  void *stream, gt_stats *stats)
+{
+    try {
+        return avalanche_run_impl(ctx, r, o, ws, ws_bytes, stream, stats);
+    } catch (const std::bad_alloc &) {
+        return GT_ERR_HOST_MEMORY;
+    }
+}
+
+static int gas_table_upload_impl(gt_ctx *ctx, const gt_gas *g)
 {
     if (!ctx || !g) return GT_ERR_ARG;
     const int L = g->n_levels, N = g->n_nodes;
@@ -669,7 +705,7 @@ static int build_mesh(gt_ctx *ctx, const gt_field *f, DevField &d)
     return GT_OK;
 }
 
-int field_setup(gt_ctx *ctx, const gt_field *f)
+static int field_setup_impl(gt_ctx *ctx, const gt_field *f)
 {
     if (!ctx || !f) return GT_ERR_ARG;
     DevField d{};
@@ -1039,8 +1075,8 @@ static void fill_stats(const Header &h, const RunPlan &pl, int64_t capacity, dou
     stats->flights_per_phase = pl.p.flights_per_phase;
 }
 
-int avalanche_run(gt_ctx *ctx, const gt_run *r, const gt_endpoints *o, void *ws, size_t ws_bytes,
-                  void *stream, gt_stats *stats)
+static int avalanche_run_impl(gt_ctx *ctx, const gt_run *r, const gt_endpoints *o, void *ws,
+                              size_t ws_bytes, void *stream, gt_stats *stats)
 {
     if (!ctx) return GT_ERR_ARG;
     int rc = validate_run(ctx, r, o, ws, ws_bytes);

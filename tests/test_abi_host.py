@@ -53,7 +53,7 @@ def test_error_strings(lib):
     from paper_2509_15377_gb300 import avalanche as A
     for code in (A.GT_OK, A.GT_ERR_ARG, A.GT_ERR_STATE, A.GT_ERR_WORKSPACE,
                  A.GT_ERR_QUEUE_OVERFLOW, A.GT_ERR_TIMEOUT, A.GT_ERR_CUDA, A.GT_ERR_NO_DEVICE,
-                 A.GT_ERR_UNSUPPORTED):
+                 A.GT_ERR_UNSUPPORTED, A.GT_ERR_HOST_MEMORY):
         assert A.strerror(code) and A.strerror(code) != "unknown error"
     assert A.strerror(12345) == "unknown error"
 
