@@ -174,3 +174,26 @@ def test_mesh_signal_telescopes():
     assert np.abs(expect).max() > 0.0
     np.testing.assert_allclose(out["signal"].sum(axis=1), expect, rtol=1e-9,
                                atol=1e-12 * np.abs(expect).max())
+
+
+def test_crossing_out_of_a_mesh_closed_form():
+    """Collisionless electrons pushed out of the top face of a constant-field
+    mesh: with exact crossings each ends on that face, at the closed-form
+    time of uniform acceleration t* = (sqrt(vz^2 + 2 a h) - vz) / a, h the
+    distance to the face; without them, far beyond it."""
+    from tests import physics as P
+    w = W.plate(n_avalanches=40, e_field=30_000.0, seed=71)
+    w.gas = W.model_gas(1e-9)
+    half = 0.02
+    mesh = W.uniform_mesh_map(30_000.0, half_width=half, cells=4, seed=5)
+    w.primaries.z[:] = 0.0  # the centre of the cube; the field pushes them to +z
+    a = P.ACCEL_PER_VCM * 30_000.0
+    vz = w.primaries.dz * np.sqrt(P.speed_sq(w.primaries.e))
+    ts = (np.sqrt(vz * vz + 2 * a * half) - vz) / a
+    o = oracle.run(w.gas, mesh, w.primaries, seed=71, t_max=100.0, crossing=True)
+    idx = np.argsort(o["uid"])
+    assert np.all(o["status"] == W.OUT_OF_MAP)
+    np.testing.assert_allclose((o["t1"] - o["t0"])[idx], ts, rtol=1e-9)
+    assert np.all(np.abs(o["z1"] - half) < 1e-12)
+    p = oracle.run(w.gas, mesh, w.primaries, seed=71, t_max=100.0)
+    assert np.all(p["z1"] > 1.0)
