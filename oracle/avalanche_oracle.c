@@ -715,6 +715,35 @@ double or_majorant(const or_gas *g, double band_width, const double v[3], const 
     return nu;
 }
 
+/* Test hook: the largest field magnitude of a field (V/cm), the bound a run
+ * with sub-steps gives the banded majorant (0 for fields that are the same
+ * everywhere). */
+double or_field_emax(const or_field *f) { return field_emax(f); }
+
+/* Test hook: the banded majorant of a flight along which the field is
+ * re-evaluated, with the field magnitude bounded by `emax` (> 0; as a run
+ * with sub-steps sets it from or_field_emax).  Returns the rate (1/ns), or a
+ * negative value for a bad table or emax <= 0. */
+double or_majorant_reach(const or_gas *g, double band_width, const double v[3], double emax,
+                         double window, double *tau_out)
+{
+    if (!(emax > 0.0)) return -1.0;
+    or_table t;
+    if (table_build(g, &t)) return -1.0;
+    if (bands_build(&t, band_width)) {
+        free(t.cum);
+        return -1.0;
+    }
+    const double E0[3] = {0.0, 0.0, 0.0};
+    double tau = 0.0;
+    t.field_emax = emax;
+    double nu = banded_majorant(&t, v, E0, 0, window, &tau);
+    if (tau_out) *tau_out = tau;
+    free(t.cum);
+    free(t.bmax);
+    return nu;
+}
+
 /* Cumulative rates at energy eps by linear interpolation between nodes;
  * energies at or beyond the last node use the last node. */
 static void table_interp(const or_table *t, double eps, double *c)

@@ -24,9 +24,8 @@ _lock = threading.Lock()
 _lib = None
 
 __all__ = ["build", "philox4x32_10", "splitmix64_mix", "child_uid", "flight", "elastic", "field_eval",
-           "boundary", "mesh_locate", "select", "majorant", "scatter", "ionisation_share",
-           "weighting_potential", "run",
-           "default_threads"]
+           "boundary", "mesh_locate", "select", "majorant", "field_emax", "majorant_reach", "scatter",
+           "ionisation_share", "weighting_potential", "run", "default_threads"]
 
 
 def build(force: bool = False) -> str:
@@ -103,6 +102,11 @@ def _load():
                                         C.POINTER(C.c_double), C.c_int, C.c_double,
                                         C.POINTER(C.c_double)]
             lib.or_majorant.restype = C.c_double
+            lib.or_field_emax.argtypes = [C.POINTER(_Field)]
+            lib.or_field_emax.restype = C.c_double
+            lib.or_majorant_reach.argtypes = [C.POINTER(_Gas), C.c_double, C.POINTER(C.c_double),
+                                              C.c_double, C.c_double, C.POINTER(C.c_double)]
+            lib.or_majorant_reach.restype = C.c_double
             lib.or_run.argtypes = [C.POINTER(_Gas), C.POINTER(_Field), C.POINTER(_Run),
                                    C.POINTER(C.c_void_p)]
             lib.or_run.restype = C.c_int
@@ -287,6 +291,29 @@ def majorant(gas, band_width: float, v, e_field, has_b: bool, window: float):
                              float(window), C.byref(tau))
     if nu < 0.0:
         raise ValueError("bad gas table")
+    return nu, tau.value
+
+
+def field_emax(field) -> float:
+    """Largest field magnitude (V/cm) the oracle assumes for `field` when the
+    field is re-evaluated along a flight (sub-steps); 0 for uniform fields."""
+    keep = []
+    f = _field_struct(field, keep)
+    return float(_load().or_field_emax(C.byref(f)))
+
+
+def majorant_reach(gas, band_width: float, v, emax: float, window: float):
+    """Banded majorant (1/ns) and window tau (ns) of a flight with velocity v
+    (cm/ns) along which the field may change, its magnitude bounded by emax
+    (V/cm): the bound runs with sub-steps use."""
+    keep = []
+    g = _gas_struct(gas, keep)
+    vv = (C.c_double * 3)(*[float(x) for x in v])
+    tau = C.c_double(0.0)
+    nu = _load().or_majorant_reach(C.byref(g), float(band_width), vv, float(emax), float(window),
+                                   C.byref(tau))
+    if nu < 0.0:
+        raise ValueError("bad gas table or emax")
     return nu, tau.value
 
 
