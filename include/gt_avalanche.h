@@ -42,7 +42,7 @@
 extern "C" {
 #endif
 
-#define GT_ABI_VERSION 3
+#define GT_ABI_VERSION 4
 #define GT_MAX_LEVELS 32 /* collision levels per gas table */
 
 /* ---- return codes ---------------------------------------------------- */
@@ -199,7 +199,18 @@ typedef struct {
                                          0 = default (1 with the banded majorant,
                                          6 with the global one) */
     int32_t majorant;                 /* GT_MAJORANT_GLOBAL / GT_MAJORANT_BANDED */
-    int32_t pad;
+    int32_t aval_base;                /* >= 0: number of this run's avalanche 0 in a
+                                         larger workload.  Avalanches are independent
+                                         (Sec. 2), and the random streams are keyed
+                                         by the workload's avalanche number
+                                         aval[i] + aval_base, so a run of avalanches
+                                         [a0, a1) of a workload with aval_base = a0
+                                         (and the workload's electron ids) transports
+                                         exactly those avalanches of the whole run:
+                                         a workload can be split over GPUs and the
+                                         parts gathered.  Every per-avalanche array
+                                         (aval_field, electrons, tallies, signal,
+                                         endpoint aval) stays indexed by aval[i]. */
     double majorant_window;           /* banded: window factor c, 0 = 2 */
     int32_t substeps;                 /* field evaluations per flight: <= 1 holds
                                          the field of the flight's start (Sec. 2

@@ -145,6 +145,11 @@ typedef struct {
     int32_t signal_kind;             /* readout electrode (OR_W_*), 0: no signal */
     int32_t signal_bins;             /* time bins of the induced signal */
     double signal_t0, signal_dt;     /* bin j covers [t0 + j dt, t0 + (j+1) dt) */
+    int32_t aval_base;               /* number of avalanche 0 in a larger workload: the
+                                        random streams are keyed by aval + aval_base, so
+                                        avalanches [a0, a1) of a workload run alone with
+                                        aval_base = a0 are those of the whole run (they
+                                        are independent, Sec. 2) */
 } or_run_args;
 
 /* ------------------------------------------------ Philox4x32-10
@@ -963,7 +968,7 @@ static void transport_electron(const or_table *tb, const or_field *f, const or_r
         }
         const uint32_t flight = n_flight;
         double u[4];
-        draw4(a->seed, aval, start->uid, flight, 0u, u);
+        draw4(a->seed, aval + a->aval_base, start->uid, flight, 0u, u);
         /* field at the start of the flight, held for the flight */
         double E[3];
         or_field_eval(f, plate_e, r, E);
@@ -1062,7 +1067,7 @@ static void transport_electron(const or_table *tb, const or_field *f, const or_r
                  * electron starts here, now, in an independent isotropic
                  * direction */
                 double u2[4];
-                draw4(a->seed, aval, start->uid, flight, 1u, u2);
+                draw4(a->seed, aval + a->aval_base, start->uid, flight, 1u, u2);
                 double eps_sec = ionisation_share(tb->split_w, eps_new, u2[0]);
                 eps_new = eps_new - eps_sec;
                 share += eps_sec;

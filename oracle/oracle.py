@@ -65,7 +65,7 @@ class _Run(C.Structure):
                 ("n_threads", C.c_int32), ("majorant", C.c_int32), ("window", C.c_double),
                 ("band_width", C.c_double), ("substeps", C.c_int32), ("crossing", C.c_int32),
                 ("signal_kind", C.c_int32), ("signal_bins", C.c_int32),
-                ("signal_t0", C.c_double), ("signal_dt", C.c_double)]
+                ("signal_t0", C.c_double), ("signal_dt", C.c_double), ("aval_base", C.c_int32)]
 
 
 def _load():
@@ -321,14 +321,15 @@ def majorant_reach(gas, band_width: float, v, emax: float, window: float):
 def run(gas, field, prim, seed: int = 0, t_max: float = 0.0, coll_limit: int = 0,
         n_threads: int | None = None, majorant: int = 0, window: float = 2.0,
         band_width: float = 1.0, substeps: int = 1, crossing: bool = False,
-        signal: tuple | None = None) -> dict:
+        signal: tuple | None = None, aval_base: int = 0) -> dict:
     """Transport every avalanche of `prim` and return a dict of arrays
     (majorant 0: one global nu_max; 1: the banded majorant with flight
     window `window` / band rate and bands of `band_width` eV; `substeps`
     field evaluations per flight; `crossing`: an electron that leaves ends
     at its first boundary crossing; `signal` = (electrode kind, bins, t0, dt)
     for the induced signal per avalanche, out["signal"] [n_avalanches, bins]
-    in units of e):
+    in units of e; `aval_base`: the workload number of avalanche 0, which keys
+    the random streams, for a part of a larger workload):
     x0..e0 (start), x1..e1 (end), status, aval, uid, n_flight, ledger [n, 4]
     (field work, inelastic loss, recoil loss, secondary share; eV),
     electrons [n_avalanches], tallies [n_avalanches, L+1] (real collisions
@@ -363,6 +364,7 @@ def run(gas, field, prim, seed: int = 0, t_max: float = 0.0, coll_limit: int = 0
     ra.band_width = band_width
     ra.substeps = int(substeps)
     ra.crossing = int(bool(crossing))
+    ra.aval_base = int(aval_base)
     if signal is not None:
         ra.signal_kind, ra.signal_bins = int(signal[0]), int(signal[1])
         ra.signal_t0, ra.signal_dt = float(signal[2]), float(signal[3])

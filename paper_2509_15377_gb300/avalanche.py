@@ -31,7 +31,7 @@ GT_BATCHED, GT_PLAIN = 0, 1
 GT_DEBUG_UNFILLED_SLOT = 1
 GT_MAJORANT_GLOBAL, GT_MAJORANT_BANDED = 0, 1
 GT_OBS_COUNT = 8
-GT_ABI_VERSION = 3
+GT_ABI_VERSION = 4
 PARTIAL_OK = (GT_OK, GT_ERR_QUEUE_OVERFLOW, GT_ERR_TIMEOUT)
 
 
@@ -69,7 +69,7 @@ class gt_run(C.Structure):
                 ("refill_period", C.c_int32), ("grid", C.c_int32),
                 ("size_limit", C.c_uint64), ("spin_limit_ms", C.c_double),
                 ("time_limit_ms", C.c_double), ("debug_flags", C.c_int32),
-                ("flights_per_phase", C.c_int32), ("majorant", C.c_int32), ("pad", C.c_int32),
+                ("flights_per_phase", C.c_int32), ("majorant", C.c_int32), ("aval_base", C.c_int32),
                 ("majorant_window", C.c_double), ("substeps", C.c_int32),
                 ("crossing", C.c_int32), ("signal_kind", C.c_int32), ("signal_bins", C.c_int32),
                 ("signal_t0", C.c_double), ("signal_dt", C.c_double)]
@@ -317,6 +317,7 @@ class RunOptions:
     grid: int = 0
     majorant: int = 0          # GT_MAJORANT_GLOBAL / GT_MAJORANT_BANDED
     majorant_window: float = 0.0
+    aval_base: int = 0         # workload number of avalanche 0 (a part of a larger workload)
     size_limit: int = 0
     spin_limit_ms: float = 0.0
     time_limit_ms: float = 0.0
@@ -481,6 +482,7 @@ class Avalanche:
         r.flights_per_phase = opt.flights_per_phase
         r.majorant = opt.majorant
         r.majorant_window = opt.majorant_window
+        r.aval_base = opt.aval_base
         r.grid = opt.grid
         r.size_limit = opt.size_limit
         r.spin_limit_ms = opt.spin_limit_ms

@@ -816,6 +816,7 @@ static int validate_run(gt_ctx *ctx, const gt_run *r, const gt_endpoints *o, voi
     if (!ctx->has_gas || !ctx->has_field) return GT_ERR_STATE;
     if (r->n_primaries < 0 || r->n_avalanches < 0) return GT_ERR_ARG;
     if (r->n_primaries > 0 && r->n_avalanches < 1) return GT_ERR_ARG;
+    if (r->aval_base < 0 || (int64_t)r->aval_base + r->n_avalanches > INT32_MAX) return GT_ERR_ARG;
     if (r->precision != GT_FP64 && r->precision != GT_MIXED) return GT_ERR_ARG;
     if (r->mode != GT_BATCHED && r->mode != GT_PLAIN) return GT_ERR_ARG;
     if (!std::isfinite(r->t_max)) return GT_ERR_ARG;
@@ -942,6 +943,7 @@ static int plan_run(gt_ctx *ctx, const gt_run *r, const gt_endpoints *o, void *w
     p.spin_limit_ns = (long long)((r->spin_limit_ms > 0 ? r->spin_limit_ms : 60000.0) * 1e6);
     p.time_limit_ns = (long long)((r->time_limit_ms > 0 ? r->time_limit_ms : 600000.0) * 1e6);
     p.n_avalanches = na;
+    p.aval_base = r->aval_base;
 
     // primaries: stage host arrays in the work space (inside the run)
     sa.n = np;

@@ -155,6 +155,7 @@ struct RunParams {
     uint64_t size_limit;
     long long spin_limit_ns, time_limit_ns;
     int n_avalanches;
+    int aval_base;          // workload number of avalanche 0 (random-stream key only)
 };
 
 // --------------------------------------------------------- small helpers
@@ -1186,7 +1187,7 @@ struct Fp64Electron {
             return EV_RETIRE;
         }
         const uint32_t flight = nf;
-        const uint4 w = draw(p.seed, aval, uid, flight, 0u);
+        const uint4 w = draw(p.seed, aval + p.aval_base, uid, flight, 0u);
         double ex, ey, ez;
         field64<FK>(p.field, plate_e, x, y, z, ex, ey, ez);
         const double ax = -kAccel * ex, ay = -kAccel * ey, az = -kAccel * ez;
@@ -1263,7 +1264,7 @@ struct Fp64Electron {
         } else {
             eps_new = eps - tb.thr[lvl];
             if (type == GT_LEVEL_IONISATION) {
-                const uint4 w2 = draw(p.seed, aval, uid, flight, 1u);
+                const uint4 w2 = draw(p.seed, aval + p.aval_base, uid, flight, 1u);
                 const double es = ionisation_share64(p.gas.split_w, eps_new, u01d(w2.x));
                 eps_new = eps_new - es;
                 double sx, sy, sz;
@@ -1668,7 +1669,7 @@ struct MixedElectron {
             status = GT_ST_FLIGHT_LIMIT;
             return EV_RETIRE;
         }
-        const uint4 w = draw(p.seed, aval, uid, nf, 0u);
+        const uint4 w = draw(p.seed, aval + p.aval_base, uid, nf, 0u);
         float ex, ey, ez;
         efield<FK>(p, ex, ey, ez);
         const float ax = -kAccelF * ex, ay = -kAccelF * ey, az = -kAccelF * ez;
@@ -1799,7 +1800,7 @@ struct MixedElectron {
             float eps_new = fmaxf(eps - tb.thr_f[lvl], 0.0f);
             if (type == GT_LEVEL_IONISATION) {
                 const uint32_t flight = nf - 1u;
-                const float4 c = new_electron32(p.seed, aval, uid, flight, eps_new,
+                const float4 c = new_electron32(p.seed, aval + p.aval_base, uid, flight, eps_new,
                                                 PHYS ? p.gas.split_w_f : 0.0f);
                 eps_new = eps_new - c.w;
                 ch.e = c.w;

@@ -46,7 +46,7 @@ def test_struct_layouts_match(lib):
     assert list(sizes) == [C.sizeof(s) for s in (A.gt_gas, A.gt_field, A.gt_run,
                                                     A.gt_endpoints, A.gt_stats)]
     assert lib.gt_abi_sizes(sizes, 4) == A.GT_ERR_ARG
-    assert lib.gt_abi_version() == 3
+    assert lib.gt_abi_version() == A.GT_ABI_VERSION == 4
 
 
 def test_error_strings(lib):
