@@ -7,8 +7,12 @@ comparators.
 
     python bench.py [--gpus N --steps K --warmup W] [--impl reference]
 
-Prints one JSON line on rank 0.  Under torchrun every rank runs its own
-4096 avalanches (seed = rank): weak scaling, no collective on the data path.
+Prints one JSON line on rank 0.  Under torchrun with N ranks the workload
+is one batched workload of N x 4096 avalanches (one seed); rank r transports
+the contiguous avalanche range r x 4096 .. (r+1) x 4096 - 1 with its random
+streams keyed by the workload's avalanche numbers, and rank 0 gathers the
+per-avalanche electron counts and collision tallies over the host at the
+end: weak scaling, no collective during the runs.
 """
 from __future__ import annotations
 
@@ -34,14 +38,21 @@ UNIT = "electron-collisions/s"
 WORKLOAD = "plate_batched_4096"
 
 # Roofline of the batched transport kernel (bound: instruction issue of the
-# SM's ALU/FMA pipes).  Algorithmic work per flight = lane instructions of
-# the straight-line step: ncu smsp__thread_inst_executed.sum / flights on
-# `bench.py --calibrate --steps 1 --block B --refill-period 32
-# --flights-per-phase 1` with the default banded majorant, per launch bound
-# B (the spill code differs; profiles/k_batched_mixed_plate_batched_4096.md).
-# Lanes switched off by divergence are not counted, so divergence, stalls
-# and queue work all show as lost efficiency.
+# SM's ALU/FMA pipes).  Work per flight, two ways:
+# - calibrated: lane instructions of the kernel's own straight-line step,
+#   ncu smsp__thread_inst_executed.sum / flights on `bench.py --calibrate
+#   --steps 1 --block B --refill-period 32 --flights-per-phase 1` with the
+#   banded majorant, per launch bound B (the spill code differs).  Lanes
+#   switched off by divergence are not counted, so divergence, stalls and
+#   queue work all show as lost efficiency;
+# - algorithmic: the operations the method needs per flight of the mixed
+#   step on this workload (Philox-10 block, majorant window and reach, log,
+#   exact flight, energy, table interpolation, and per real collision the
+#   level choice, tally, isotropic direction and speed), counted from its
+#   arithmetic, one lane instruction per operation; what the kernel issues
+#   beyond it (spill code, addressing, control, FP64 folds) is overhead.
 LANE_INST_PER_FLIGHT_BY_BLOCK = {768: 413.3, 896: 402.1, 1024: 423.8}
+ALGORITHMIC_LANE_INST_PER_FLIGHT = 190.0
 
 
 def lane_inst_per_flight(block: int) -> float:
@@ -62,14 +73,16 @@ LANES_PER_WARP = 32
 # last capture (199.8 B per electron) predates the 4-byte birth-element
 # field that every new electron now stores.
 DRAM_BYTES_PER_ELECTRON = None
+# Bytes per electron that the batched transport kernel must move by its
+# data layout: at birth the start record (x0 y0 z0 t0 e0, 40 B), id (8),
+# avalanche (4), birth velocity (24), birth element (4) and ready flag (4)
+# are written (84 B); the lane that takes the electron reads them back
+# without e0 (76 B); at the end x1 y1 z1 t1 e1 (40), status (4) and flight
+# count (4) are written (48 B).
+ALGORITHMIC_BYTES_PER_ELECTRON = 84 + 76 + 48
 
 
 # ---------------------------------------------------------------- sharding
-def shard_seed(rank: int) -> int:
-    """Each rank transports its own statistically identical workload."""
-    return rank
-
-
 def dist_env():
     ws = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
@@ -159,10 +172,10 @@ class ClockSampler:
 
 
 # ------------------------------------------------------------ CPU baseline
-def oracle_baseline(w, seed: int, n_aval: int, args) -> dict:
+def oracle_baseline(w, seed: int, n_aval: int, args, keep: bool = False) -> dict:
     """The FP64 oracle as it stands on the host cores, on the first n_aval
     avalanches of the workload (a bounded sample), with the same majorant
-    as the GPU run."""
+    as the GPU run.  keep: also return the oracle's endpoints ("_out")."""
     import oracle
     sub = w.primaries.subset(list(range(n_aval)))
     threads = oracle.default_threads()
@@ -173,10 +186,50 @@ def oracle_baseline(w, seed: int, n_aval: int, args) -> dict:
     dt = time.perf_counter() - t0
     L = w.gas.n_levels
     real = int(o["tallies"][:, :L].sum())
-    return {"value": real / dt, "unit": UNIT, "cores": threads, "kind": "oracle",
-            "sample": f"avalanches 0..{n_aval - 1} of {w.primaries.n_avalanches} "
-                      f"({real:.3g} real collisions in {dt:.1f} s, {args.majorant} majorant)",
-            "seconds": dt, "real_collisions": real}
+    res = {"value": real / dt, "unit": UNIT, "cores": threads, "kind": "oracle",
+           "sample": f"avalanches 0..{n_aval - 1} of {w.primaries.n_avalanches} "
+                     f"({real:.3g} real collisions in {dt:.1f} s, {args.majorant} majorant)",
+           "seconds": dt, "real_collisions": real}
+    if keep:
+        res["_out"] = o
+        res["_prim"] = sub
+    return res
+
+
+# ---------------------------------------------------- matched observables
+def matched_check(av, w, ref_out, ref_prim, n_aval: int, opt, seeds, cap, stream, collect,
+                  geometry: str = "plate") -> dict:
+    """The batched mixed-precision GPU path against the FP64 oracle on the
+    same avalanche numbers 0..n_aval-1 with independent seeds (the oracle
+    run `ref_out` with its seed; the GPU once per seed in `seeds`): gain,
+    Townsend coefficient, drift velocity and diffusion, each with its
+    bootstrap standard error over avalanches, the difference in units of
+    the combined error and a pass at 3 sigma."""
+    from paper_2509_15377_gb300 import avalanche as A
+    from paper_2509_15377_gb300 import observables as O
+    gap = w.field.gap
+    n_prim = np.bincount(ref_prim.aval, minlength=ref_prim.n_avalanches)[:n_aval]
+    ref = O.with_errors(O.per_avalanche(ref_out, n_aval, collect, n_prim, geometry), gap,
+                        geometry, seed=1)
+    dev_prim = av.primaries_device(ref_prim)
+    parts = []
+    for sd in seeds:
+        st = av.run(dev_prim, dataclasses.replace(opt, seed=sd), cap, stream=stream,
+                    allow=(A.GT_OK,))
+        out = av.fetch(st["n_endpoints"])
+        parts.append(O.per_avalanche(out, n_aval, collect, n_prim, geometry))
+    # (avalanche, seed) pairs are the independent units of the GPU sample
+    gpu = O.with_errors({k: np.concatenate([p_[k] for p_ in parts]) for k in parts[0]}, gap,
+                        geometry, seed=2)
+    rows = O.compare(ref, gpu)
+    return {"avalanches": n_aval, "oracle_runs": 1, "gpu_seeds": len(seeds),
+            "observables": {k: {"oracle": r["a"], "oracle_se": r["se_a"], "mixed": r["b"],
+                                "mixed_se": r["se_b"], "rel_diff": r["rel_diff"],
+                                "sigma": r["sigma"], "pass_3sigma": r["within_3sigma"]}
+                            for k, r in rows.items()},
+            "gain_window_3sigma_rel": 3.0 * math.hypot(rows["gain"]["se_a"], rows["gain"]["se_b"])
+            / rows["gain"]["a"],
+            "matched": all(r["within_3sigma"] for r in rows.values())}
 
 
 # ---------------------------------------------------------------- our arm
@@ -184,10 +237,10 @@ def field_map_lines(av, args, seed: int, cap: int, stream, flush, majorant) -> d
     """Field maps of the coax geometry (the grid workload's box, 1810 V, one
     primary at r = 1 mm per avalanche): the regular 256^3 grid and a
     tetrahedral mesh of the same box (48^3 jittered cubes graded towards the
-    wire, six elements each), batched mixed.  Launch shapes are fixed per map
-    (the best of fixed-shape runs of the full workload; the autotuner's small
-    samples, a few avalanches growing from one electron each, are starved of
-    parallelism and pick poorly) unless given on the command line."""
+    wire, six elements each), batched mixed.  Each map's launch shape comes
+    from the autotuner on its first --map-tune-avalanches avalanches (about
+    1e5 electrons each: enough to keep every SM busy for most of a run),
+    unless given on the command line."""
     from paper_2509_15377_gb300 import avalanche as A
     from paper_2509_15377_gb300 import workloads as W
     maps = {}
@@ -200,12 +253,16 @@ def field_map_lines(av, args, seed: int, cap: int, stream, flush, majorant) -> d
             wl = W.mesh_coax(n_avalanches=n_map, cells=48, seed=seed, grading=4.0)
         av.set_gas(wl.gas)
         av.set_field(wl.field)
-        given = args.block or args.refill_period or args.flights_per_phase
-        shape = ((args.block, args.refill_period, args.flights_per_phase) if given
-                 else (512, 4, 1) if name == "grid" else (512, 32, 1))
         m_opt = A.RunOptions(seed=seed, t_max=wl.t_max, precision=A.GT_MIXED, mode=A.GT_BATCHED,
-                             block=shape[0], refill_period=shape[1], flights_per_phase=shape[2],
+                             block=args.block, refill_period=args.refill_period,
+                             flights_per_phase=args.flights_per_phase,
                              majorant=majorant, majorant_window=args.window)
+        tuned = None
+        if not args.no_autotune:
+            tsub = wl.primaries.subset(list(range(min(args.map_tune_avalanches, n_map))))
+            tb, tp = av.autotune(av.primaries_device(tsub), m_opt, cap, stream=stream)
+            tuned = {"best": [tb["block"], tb["refill_period"], tb["flights_per_phase"]],
+                     "runs": len(tp), "sample_avalanches": len(set(tsub.aval.tolist()))}
         m_dev = av.primaries_device(wl.primaries)
         m_real, m_ms, m_fl = 0, 0.0, 0
         for _ in range(2):
@@ -217,7 +274,8 @@ def field_map_lines(av, args, seed: int, cap: int, stream, flush, majorant) -> d
         maps[name] = {"value_kernel_time": m_real / (m_ms / 1e3), "unit": UNIT,
                       "flights_per_real": m_fl / max(m_real, 1), "avalanches": n_map,
                       "electrons_per_avalanche": m_st["n_endpoints"] / n_map,
-                      "shape": [m_st["block"], m_st["refill_period"], m_st["flights_per_phase"]]}
+                      "shape": [m_st["block"], m_st["refill_period"], m_st["flights_per_phase"]],
+                      "autotune": tuned}
         if name == "grid":
             maps[name]["map"] = "256^3 float4 nodes, trilinear"
         else:
@@ -252,20 +310,29 @@ def run_ours(args) -> None:
         dist.init_process_group("nccl", device_id=torch.device(f"cuda:{local}"))
     torch.cuda.set_device(local)
     dev = torch.device(f"cuda:{local}")
+    # the gather at the end goes over the host (gloo), not the GPUs
+    host_group = dist.new_group(backend="gloo") if ws > 1 else None
 
     import __graft_entry__
     if rank == 0:
         __graft_entry__.build()
     barrier()
     from paper_2509_15377_gb300 import avalanche as A
+    from paper_2509_15377_gb300 import shard
     from paper_2509_15377_gb300 import workloads as W
 
-    seed = shard_seed(rank)
-    w = W.plate_batched(n_avalanches=args.avalanches, seed=seed)
+    # one workload of ws x 4096 avalanches, one seed; this rank's contiguous
+    # range of avalanche numbers (rank 0's part of the 1-GPU run is the
+    # whole 4096-avalanche workload)
+    seed = 0
+    n_total = args.avalanches * ws
+    whole = W.plate_batched(n_avalanches=n_total, seed=seed)
+    a0, a1 = shard.partition(n_total, ws, rank)
+    w = dataclasses.replace(whole, primaries=shard.part_primaries(whole.primaries, a0, a1))
 
     cpu = None
     if rank == 0 and ws == 1 and not args.no_cpu_baseline:
-        cpu = oracle_baseline(w, seed, args.cpu_avalanches, args)
+        cpu = oracle_baseline(w, seed, args.cpu_avalanches, args, keep=True)
 
     av = A.Avalanche(local)
     av.set_gas(w.gas)
@@ -275,7 +342,7 @@ def run_ours(args) -> None:
     opt = A.RunOptions(seed=seed, t_max=w.t_max, precision=A.GT_MIXED, mode=A.GT_BATCHED,
                        block=args.block, refill_period=args.refill_period,
                        flights_per_phase=args.flights_per_phase, majorant=majorant,
-                       majorant_window=args.window)
+                       majorant_window=args.window, aval_base=a0)
     cap = args.capacity
     stream = torch.cuda.current_stream(dev)
     flush = torch.empty(256 * 1024 * 1024, dtype=torch.uint8, device=dev)  # > 129 MB L2
@@ -300,7 +367,8 @@ def run_ours(args) -> None:
         flush.fill_(1)
         step_no[0] += 1
         if graph is None:
-            return av.run(prim, opt, cap, stream=stream, allow=(A.GT_OK,))
+            return av.run(prim, dataclasses.replace(opt, seed=seed + 7919 * step_no[0]), cap,
+                          stream=stream, allow=(A.GT_OK,))
         graph.launch(seed + 7919 * step_no[0], stream=stream)
         return graph.stats(allow=(A.GT_OK,))
 
@@ -331,13 +399,27 @@ def run_ours(args) -> None:
     total_real = sum_over_ranks(float(real), dev)
     value = total_real / t_max_rank
 
-    # observables of the last step (gain, drift velocity) for the matched check
+    # the gather: every rank's per-avalanche electron counts and tallies of
+    # the last step, placed at its avalanche range on rank 0 (over the host)
     last = stats[-1]
+    part = {"electrons": av.ep["electrons"][:a1 - a0].cpu().numpy().view(np.uint64),
+            "tallies": av.ep["tallies"][:a1 - a0].cpu().numpy().view(np.uint64)}
+    merged = shard.gather(part, a0, n_total, group=host_group) if ws > 1 else part
+    gathered = None
+    if rank == 0:
+        L = w.gas.n_levels
+        gathered = {"avalanches": int(merged["electrons"].shape[0]),
+                    "electrons": int(merged["electrons"].sum()),
+                    "real_collisions_last_step": int(merged["tallies"][:, :L].sum()),
+                    "ranges": [list(shard.partition(n_total, ws, r)) for r in range(ws)]}
+
+    # observables of the last step (gain, drift velocity)
     obs = av.observables(last["n_endpoints"], w.primaries, collect_status=W.ANODE,
                          drift_status=W.ANODE, gap=w.field.gap)
 
     # end to end through the public API: pinned host inputs copied inside
-    # every step, the per-avalanche results read back
+    # every step, the per-avalanche results read back (the endpoints stay on
+    # the device, as the C ABI's output arrays are the caller's)
     prim_host = av.primaries_pinned(w.primaries)
     h_elec = torch.empty(w.primaries.n_avalanches, dtype=torch.int64).pin_memory()
     h_tal = torch.empty((w.primaries.n_avalanches, w.gas.n_levels + 1), dtype=torch.int64).pin_memory()
@@ -359,83 +441,101 @@ def run_ours(args) -> None:
               for k in list(A.Avalanche.PRIM_KEYS) + ["aval", "uid", "aval_field"])
     d2h = h_elec.numel() * 8 + h_tal.numel() * 8 + 256
 
-    # plain FP64 GPU path (one avalanche per launch sequence) on a sample
-    # the same batched mixed run with the global majorant (one nu_max), for
-    # the gain of the banded majorant alone
+    if rank != 0:
+        av.close()
+        return
+    extra = not args.no_plain
+
+    def timed_runs(o, prim, n=2):
+        """Real collisions per second of transport-kernel time over n runs."""
+        r_, ms_, fl_ = 0, 0.0, 0
+        for _ in range(n):
+            flush.fill_(1)
+            s_ = av.run(prim, o, cap, stream=stream, allow=(A.GT_OK,))
+            r_ += s_["real_collisions"]
+            ms_ += s_["transport_ms"]
+            fl_ += s_["flights"]
+        return {"value_kernel_time": r_ / (ms_ / 1e3), "unit": UNIT,
+                "flights_per_real": fl_ / max(r_, 1),
+                "shape": [s_["block"], s_["refill_period"], s_["flights_per_phase"]]}, s_
+
+    # the same batched mixed run with the other majorant (one global nu_max):
+    # what the banded majorant alone buys
     other = None
-    if rank == 0 and not args.no_plain:
+    if extra:
         o_opt = dataclasses.replace(
             opt, majorant=A.GT_MAJORANT_GLOBAL if majorant == A.GT_MAJORANT_BANDED
             else A.GT_MAJORANT_BANDED)
-        o_real, o_ms = 0, 0.0
-        for _ in range(2):
-            flush.fill_(1)
-            o_st = av.run(prim_dev, o_opt, cap, stream=stream, allow=(A.GT_OK,))
-            o_real += o_st["real_collisions"]
-            o_ms += o_st["transport_ms"]
-        other = {"majorant": "global" if o_opt.majorant == A.GT_MAJORANT_GLOBAL else "banded",
-                 "value_kernel_time": o_real / (o_ms / 1e3), "unit": UNIT,
-                 "flights_per_real": o_st["flights"] / max(o_st["real_collisions"], 1)}
+        other, _ = timed_runs(o_opt, prim_dev)
+        other["majorant"] = "global" if o_opt.majorant == A.GT_MAJORANT_GLOBAL else "banded"
+
+    # the same batched run in FP64 (the FP64 kernel, autotuned): what mixed
+    # precision alone buys, at the same batching
+    fp64_batched = None
+    tune_sample = av.primaries_device(w.primaries.subset(list(range(args.tune_avalanches))))
+    if extra:
+        f_opt = dataclasses.replace(opt, precision=A.GT_FP64, block=0, refill_period=0,
+                                    flights_per_phase=0)
+        if not args.no_autotune:
+            av.autotune(tune_sample, f_opt, cap, stream=stream)
+        fp64_batched, _ = timed_runs(f_opt, prim_dev, n=1)
+        fp64_batched["note"] = "same 4096-avalanche workload, FP64 batched kernel"
 
     # the same batched mixed step with the physical gas (screened-Coulomb
     # anisotropy, Opal-Peterson-Beaty sharing, attachment)
     physical = None
-    if rank == 0 and not args.no_plain:
+    if extra:
         av.set_gas(W.argon_like_physical_gas())
-        tune_sample = av.primaries_device(w.primaries.subset(list(range(args.tune_avalanches))))
         if not args.no_autotune:  # each kernel build has its own best shape
             av.autotune(tune_sample, opt, cap, stream=stream)
-        p_real, p_ms, p_fl = 0, 0.0, 0
-        for _ in range(2):
-            flush.fill_(1)
-            p_st = av.run(prim_dev, opt, cap, stream=stream, allow=(A.GT_OK,))
-            p_real += p_st["real_collisions"]
-            p_ms += p_st["transport_ms"]
-            p_fl += p_st["flights"]
+        physical, p_st = timed_runs(opt, prim_dev)
         p_obs = av.observables(p_st["n_endpoints"], w.primaries, collect_status=W.ANODE,
                                drift_status=W.ANODE, gap=w.field.gap)
-        physical = {"gas": "argon-like + screened-Coulomb anisotropy, OPB sharing, attachment",
-                    "value_kernel_time": p_real / (p_ms / 1e3), "unit": UNIT,
-                    "flights_per_real": p_fl / max(p_real, 1), "gain": p_obs[0],
-                    "shape": [p_st["block"], p_st["refill_period"], p_st["flights_per_phase"]]}
+        physical.update(gas="argon-like + screened-Coulomb anisotropy, OPB sharing, attachment",
+                        gain=p_obs[0])
         av.set_gas(w.gas)
         # the basic gas with exact boundary crossings (the general kernel)
         c_opt = dataclasses.replace(opt, crossing=1)
         if not args.no_autotune:
             av.autotune(tune_sample, c_opt, cap, stream=stream)
-        c_real, c_ms = 0, 0.0
-        for _ in range(2):
-            flush.fill_(1)
-            c_st = av.run(prim_dev, c_opt, cap, stream=stream, allow=(A.GT_OK,))
-            c_real += c_st["real_collisions"]
-            c_ms += c_st["transport_ms"]
-        physical["crossing"] = {"value_kernel_time": c_real / (c_ms / 1e3), "unit": UNIT,
-                                "note": "basic gas, endpoints at the first boundary crossing",
-                                "shape": [c_st["block"], c_st["refill_period"],
-                                          c_st["flights_per_phase"]]}
+        physical["crossing"], _ = timed_runs(c_opt, prim_dev)
+        physical["crossing"]["note"] = "basic gas, endpoints at the first boundary crossing"
         # the basic gas with the anode's induced signal, 2000 bins of 50 ps
         s_opt = dataclasses.replace(opt, signal_kind=W.W_PLATE, signal_bins=2000,
                                     signal_t0=0.0, signal_dt=0.05)
-        s_real, s_ms = 0, 0.0
-        for _ in range(2):
-            flush.fill_(1)
-            s_st = av.run(prim_dev, s_opt, cap, stream=stream, allow=(A.GT_OK,))
-            s_real += s_st["real_collisions"]
-            s_ms += s_st["transport_ms"]
-        physical["signal"] = {"value_kernel_time": s_real / (s_ms / 1e3), "unit": UNIT,
-                              "note": "basic gas, Shockley-Ramo anode signal per avalanche, "
-                                      "2000 bins x 0.05 ns"}
+        physical["signal"], _ = timed_runs(s_opt, prim_dev)
+        physical["signal"]["note"] = ("basic gas, Shockley-Ramo anode signal per avalanche, "
+                                      "2000 bins x 0.05 ns")
+
+    # the coaxial tube with a 1 T axial field: 2048 avalanches, one primary
+    # each at r in 1-4.5 mm, batched mixed (E x B flights)
+    coax = None
+    if extra:
+        cw = W.coax(n_avalanches=2048, seed=seed)
+        av.set_gas(cw.gas)
+        av.set_field(cw.field)
+        c_prim = av.primaries_device(cw.primaries)
+        c_opt = dataclasses.replace(opt, t_max=cw.t_max, block=0, refill_period=0,
+                                    flights_per_phase=0, aval_base=0)
+        if not args.no_autotune:
+            av.autotune(av.primaries_device(cw.primaries.subset(list(range(512)))), c_opt, cap,
+                        stream=stream)
+        coax, c_st = timed_runs(c_opt, c_prim)
+        c_obs = av.observables(c_st["n_endpoints"], cw.primaries, collect_status=W.WIRE)
+        coax.update(avalanches=2048, gain=c_obs[0], gain_se=c_obs[1],
+                    electrons_per_avalanche=c_st["n_endpoints"] / 2048,
+                    field="coax a = 25 um, b = 5 mm, 1500 V, B = 1 T axial")
 
     maps = None
-    if rank == 0 and not args.no_plain:
+    if extra:
         maps = field_map_lines(av, args, seed, cap, stream, flush, majorant)
-        av.set_gas(w.gas)
-        av.set_field(w.field)
+    av.set_gas(w.gas)
+    av.set_field(w.field)
 
     # plain FP64 GPU path (the paper's structure: one avalanche at a time, one
     # launch per generation) on a sample, with both majorants
     plain = None
-    if rank == 0 and not args.no_plain:
+    if extra:
         sub = w.primaries.subset(list(range(args.plain_avalanches)))
         psub = av.primaries_device(sub)
         plain = {"sample": f"avalanches 0..{args.plain_avalanches - 1}", "unit": UNIT}
@@ -450,22 +550,35 @@ def run_ours(args) -> None:
             plain["value_" + name] = pst["real_collisions"] / pdt
             if mj == majorant:
                 # like for like: the speedup compares runs with the same majorant
-                pobs = av.observables(pst["n_endpoints"], sub, collect_status=W.ANODE,
-                                      drift_status=W.ANODE, gap=w.field.gap)
                 plain.update(value=plain["value_" + name], majorant=name,
                              launches=pst["launches"], generations=pst["iterations"])
-        # the mixed batched run restricted to the same avalanches, for the gain match
-        st_m = av.run(psub, opt, cap, stream=stream, allow=(A.GT_OK,))
-        mobs = av.observables(st_m["n_endpoints"], sub, collect_status=W.ANODE,
-                              drift_status=W.ANODE, gap=w.field.gap)
-        se = math.hypot(pobs[1], mobs[1])
-        plain.update(gain_fp64_plain=pobs[0], gain_mixed_batched=mobs[0], gain_sigma=se,
-                     matched_gain_3sigma=bool(abs(pobs[0] - mobs[0]) <= 3 * se),
-                     vd_fp64_plain=pobs[3], vd_mixed_batched=mobs[3])
 
-    if rank != 0:
-        av.close()
-        return
+    # matched observables: the batched mixed path against the FP64 oracle on
+    # the same avalanche numbers with independent seeds
+    matched = None
+    if extra and cpu is not None:
+        matched = {"plate_batched_sample": matched_check(
+            av, w, cpu.pop("_out"), cpu.pop("_prim"), args.cpu_avalanches, opt,
+            [seed + 1001, seed + 1002], cap, stream, W.ANODE)}
+        import oracle
+        pw = W.plate(n_avalanches=1000, e_field=40_000.0, seed=seed)
+        t0 = time.perf_counter()
+        p_ref = oracle.run(pw.gas, pw.field, pw.primaries, seed=seed, t_max=pw.t_max,
+                           majorant=int(majorant == A.GT_MAJORANT_BANDED), window=args.window,
+                           band_width=pw.gas.band_width)
+        p_secs = time.perf_counter() - t0
+        av.set_field(pw.field)
+        matched["plate_40kV_1000"] = matched_check(
+            av, pw, p_ref, pw.primaries, 1000, dataclasses.replace(opt, t_max=pw.t_max,
+                                                                  aval_base=0),
+            [seed + 2001, seed + 2002, seed + 2003, seed + 2004], cap, stream, W.ANODE)
+        matched["plate_40kV_1000"]["oracle_seconds"] = p_secs
+        matched["matched"] = all(v["matched"] for v in matched.values() if isinstance(v, dict))
+        av.set_field(w.field)
+    elif cpu is not None:
+        cpu.pop("_out")
+        cpu.pop("_prim")
+
     kms = statistics.mean(kernel_ms)
     fl_per_launch = flights / len(kernel_ms)
     peak_clk = clk.get("sm_max_mhz") or 2070.0
@@ -473,15 +586,19 @@ def run_ours(args) -> None:
     peak = SM_COUNT * ISSUE_PER_SM_PER_CLK * LANES_PER_WARP * peak_clk * 1e6 / 1e9
     lipf = lane_inst_per_flight(stats[-1]["block"])
     achieved = lipf * fl_per_launch / (kms / 1e3) / 1e9
+    achieved_alg = ALGORITHMIC_LANE_INST_PER_FLIGHT * fl_per_launch / (kms / 1e3) / 1e9
     electrons_per_launch = statistics.mean(s["n_endpoints"] for s in stats)
     roof = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "Glane-inst/s",
             "frac": achieved / peak,
             "traffic": (DRAM_BYTES_PER_ELECTRON * electrons_per_launch
                         if DRAM_BYTES_PER_ELECTRON else None),
-            "traffic_unit": "bytes per launch (ncu, scaled from the 256-avalanche capture)",
+            "traffic_unit": "bytes per launch (ncu DRAM bytes per electron x electrons)",
+            "algorithmic_bytes": ALGORITHMIC_BYTES_PER_ELECTRON * electrons_per_launch,
             "kernel": "k_batched<MixedElectron, PLATE, smem table>", "kernel_ms": kms,
             "flights_per_launch": fl_per_launch,
             "lane_inst_per_flight": lipf,
+            "algorithmic": {"lane_inst_per_flight": ALGORITHMIC_LANE_INST_PER_FLIGHT,
+                            "achieved": achieved_alg, "frac": achieved_alg / peak},
             "peak_note": "152 SMs x 4 schedulers x 32 lanes x max SM clock (measured max)",
             "clock_frac": (clk.get("sm_mhz") or peak_clk) / peak_clk}
     line = {
@@ -490,6 +607,7 @@ def run_ours(args) -> None:
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32+f64",
         "data": "synthetic",
         "config": {"workload": WORKLOAD, "avalanches_per_gpu": args.avalanches,
+                   "avalanches_total": n_total,
                    "field_kv_cm": [30, 50], "primaries_mean": 3, "gap_um": 128,
                    "gas": "argon-like 12-level", "precision": "mixed", "mode": "batched",
                    "block": stats[-1]["block"], "grid": stats[-1]["grid"],
@@ -498,23 +616,31 @@ def run_ours(args) -> None:
                    "autotune": tune,
                    "launch": "avalanche_run per step" if args.no_graph else
                              "captured CUDA graph replay per step (new seed each)",
-                   "l2": "flushed (256 MB write) before every step"},
+                   "l2": "flushed (256 MB write) before every step",
+                   "parallelism": f"{ws} GPU(s), contiguous avalanche ranges, host gather"},
         "flights_per_s": sum_over_ranks(float(flights), dev) / t_max_rank,
         "null_fraction": 1.0 - real / max(flights, 1),
         "electrons_per_step": stats[-1]["n_endpoints"],
+        "gathered": gathered,
         "observables": {"gain": obs[0], "gain_se": obs[1], "vd_cm_per_ns": obs[3],
-                        "dt_cm2_per_ns": obs[4], "dl_cm2_per_ns": obs[5]},
+                        "dt_cm2_per_ns": obs[4], "dl_cm2_per_ns": obs[5], "alpha_per_cm": obs[7]},
+        "matched": matched,
         "majorant": args.majorant,
         "flights_per_real": flights / max(real, 1),
         "other_majorant": other,
+        "fp64_batched": fp64_batched,
         "plain_fp64": plain,
         "speedup_vs_plain_fp64": (value / plain["value"]) if plain else None,
+        "speedup_vs_fp64_batched": (value / fp64_batched["value_kernel_time"])
+        if fp64_batched else None,
         "physical_gas": physical,
+        "coax_b": coax,
         "field_maps": maps,
         "roofline": roof,
         "cpu_baseline": cpu,
         "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": h2d,
-                "d2h_bytes_per_step": d2h, "steps": e2e_steps},
+                "d2h_bytes_per_step": d2h, "steps": e2e_steps,
+                "readback": "per-avalanche electron counts and tallies; endpoints stay on the device"},
         "gpu_launches": int(sum(s["launches"] for s in stats)),
         "clocks": clk,
     }
@@ -578,7 +704,7 @@ def run_reference(args) -> None:
     import oracle
     oracle.build()
     w = W.plate_batched(n_avalanches=args.avalanches, seed=0)
-    per_step = max(1, args.cpu_avalanches // 2)
+    per_step = max(1, args.ref_avalanches)
     for _ in range(args.warmup):
         oracle_baseline(w, 0, max(1, per_step // 8), args)
     real = 0
@@ -612,9 +738,12 @@ def parse(argv=None):
     ap.add_argument("--block", type=int, default=0)
     ap.add_argument("--refill-period", type=int, default=0)
     ap.add_argument("--flights-per-phase", type=int, default=0)
-    # the oracle's sample: ~10-15 s of CPU work on 16 Arm cores (banded majorant);
-    # the reference arm takes half of it per step
-    ap.add_argument("--cpu-avalanches", type=int, default=512)
+    # the oracle's sample: ~17 s of CPU work on 16 Arm cores (banded majorant),
+    # also the oracle side of the matched check; the reference arm takes
+    # --ref-avalanches per step
+    ap.add_argument("--cpu-avalanches", type=int, default=1024)
+    ap.add_argument("--ref-avalanches", type=int, default=256,
+                    help="oracle avalanches per step of the reference arm")
     ap.add_argument("--plain-avalanches", type=int, default=32)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-plain", action="store_true")
@@ -628,6 +757,7 @@ def parse(argv=None):
                     help="only the grid / mesh field-map lines (profiling aid)")
     ap.add_argument("--maps", default="grid,mesh")
     ap.add_argument("--map-avalanches", type=int, default=256)
+    ap.add_argument("--map-tune-avalanches", type=int, default=96)
     ap.add_argument("--calibrate", action="store_true",
                     help="run the straight-line calibration workload (for ncu)")
     return ap.parse_args(argv)

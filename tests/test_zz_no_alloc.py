@@ -2,7 +2,8 @@
 scratch instead of a caller work space, for callers that cannot allocate
 device memory where they run avalanches.  Its results must equal
 avalanche_run's (the same kernels, the same random numbers), on two calls in
-a row through the same array.
+a row through the same array, and the second call must leave the device's
+free memory and torch's allocations unchanged.
 
 This file is collected last on purpose (test_zz_*), and it also passes on
 its own in a fresh process: it builds and creates everything it uses."""
@@ -51,9 +52,16 @@ def test_static_scratch_matches_workspace_run(av, precision):
     # reuses the array the first one left behind)
     r = av.make_run(prim, opt)
     out = av.endpoints_struct(cap)
-    for _ in range(2):
+    for call in range(2):
+        if call == 1:
+            # after the first call (which may load the device code): the
+            # device's free memory and torch's allocations stay as they are
+            free0, alloc0 = torch.cuda.mem_get_info(0)[0], torch.cuda.memory_allocated(0)
         st = A.avalanche_run_static(av.ctx, r, out, stream.cuda_stream, allow=(A.GT_OK,))
         torch.cuda.synchronize()
+        if call == 1:
+            assert torch.cuda.mem_get_info(0)[0] == free0
+            assert torch.cuda.memory_allocated(0) == alloc0
         got = _fetch(av, st.n_endpoints)
         assert st.n_endpoints == st_ref["n_endpoints"]
         assert st.real_collisions == st_ref["real_collisions"]
