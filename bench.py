@@ -472,7 +472,8 @@ def run_ours(args) -> None:
     # the same batched run in FP64 (the FP64 kernel, autotuned): what mixed
     # precision alone buys, at the same batching
     fp64_batched = None
-    tune_sample = av.primaries_device(w.primaries.subset(list(range(args.tune_avalanches))))
+    tune_sample = av.primaries_device(
+        w.primaries.subset(list(range(min(args.tune_avalanches, args.avalanches)))))
     if extra:
         f_opt = dataclasses.replace(opt, precision=A.GT_FP64, block=0, refill_period=0,
                                     flights_per_phase=0)

@@ -430,12 +430,17 @@ int gt_graph_destroy(gt_graph *graph);
  * The batched kernel's throughput depends on the threads per CTA (more
  * resident warps against fewer registers each) and on the flights per
  * round (fewer queue refills and FP64 flushes against lanes idling after
- * their electron finishes).  gt_autotune runs `run` in GT_BATCHED mode once
- * per candidate shape (after one warm-up run) and measures real collisions
- * per millisecond of transport kernel time (CUDA events).  Candidates:
- * MIXED 512/768/896/1024 threads x refill period 4/8/16/32 x flights per
- * phase 1/2/4/6 (64); FP64 128/256/512 threads x refill period 8/16/32/64
- * (12).  The fastest shape is remembered by the context for the run's
+ * their electron finishes).  gt_autotune runs `run` in GT_BATCHED mode (after
+ * one warm-up run) and measures real collisions per millisecond of transport
+ * kernel time (CUDA events) for the shapes of a coordinate descent: from a
+ * middle shape, each dimension in turn takes its best value with the others
+ * held, until a whole sweep changes nothing (at most four sweeps; a shape
+ * runs at most once; typically 10-14 runs, so a sample large enough to keep
+ * the GPU saturated is affordable).  Values: MIXED 512/768/896/1024 threads,
+ * refill period 4/8/16/32, flights per phase 1/2/4/6; FP64 128/256/512
+ * threads, refill period 8/16/32/64.  A block, refill_period or
+ * flights_per_phase set (non-zero) in `run` fixes that dimension.  The
+ * fastest shape is remembered by the context for the run's
  * precision, field kind, majorant and kernel build (the basic gas; a gas
  * with anisotropy, attachment or a sharing law; a run with sub-steps,
  * crossings or signals), and used by later runs that leave block /

@@ -286,7 +286,7 @@ def avalanche_run_static(ctx, run: gt_run, out: gt_endpoints, stream_ptr: int,
 
 def gt_autotune(ctx, run: gt_run, out: gt_endpoints, workspace_ptr: int, workspace_nbytes: int,
                 stream_ptr: int):
-    """Measure every candidate launch shape; returns (best, [points])."""
+    """Coordinate-descent search over launch shapes; returns (best, [points])."""
     pts = (gt_tune_point * 128)()
     n = C.c_int32()
     best = gt_tune_point()

@@ -1363,53 +1363,89 @@ int gt_autotune(gt_ctx *ctx, const gt_run *run, const gt_endpoints *out, void *w
     gt_run r = *run;
     r.mode = GT_BATCHED;
     const bool fp64 = r.precision == GT_FP64;
-    // candidate shapes: threads per CTA x refill period (x flights per phase)
+    // candidate values per dimension: threads per CTA, refill period,
+    // flights per phase (mixed only); a dimension the caller set is fixed
     static const int blocks_mixed[] = {512, 768, 896, 1024};
     static const int blocks_fp64[] = {128, 256, 512};
     static const int ks_mixed[] = {4, 8, 16, 32};
     static const int ks_fp64[] = {8, 16, 32, 64};
     static const int ms_mixed[] = {1, 2, 4, 6};
     static const int ms_fp64[] = {1};
-    const int *blocks = fp64 ? blocks_fp64 : blocks_mixed;
-    const int *ks = fp64 ? ks_fp64 : ks_mixed;
-    const int *ms = fp64 ? ms_fp64 : ms_mixed;
-    const int nb = fp64 ? 3 : 4, nk = 4, nm = fp64 ? 1 : 4;
+    std::vector<int> cand[3];
+    if (run->block > 0) cand[0] = {run->block};
+    else if (fp64) cand[0].assign(blocks_fp64, blocks_fp64 + 3);
+    else cand[0].assign(blocks_mixed, blocks_mixed + 4);
+    if (run->refill_period > 0) cand[1] = {run->refill_period};
+    else if (fp64) cand[1].assign(ks_fp64, ks_fp64 + 4);
+    else cand[1].assign(ks_mixed, ks_mixed + 4);
+    if (run->flights_per_phase > 0) cand[2] = {run->flights_per_phase};
+    else if (fp64) cand[2].assign(ms_fp64, ms_fp64 + 1);
+    else cand[2].assign(ms_mixed, ms_mixed + 4);
+    // start: a middle shape (one flight per phase with the banded majorant,
+    // whose flights are mostly real; four with the global one)
+    auto pick = [](const std::vector<int> &c, int want) {
+        for (int v : c)
+            if (v == want) return v;
+        return c[c.size() / 2];
+    };
+    int cur[3] = {pick(cand[0], fp64 ? 256 : 896), pick(cand[1], 16),
+                  pick(cand[2], r.majorant == GT_MAJORANT_BANDED ? 1 : 4)};
     gt_stats st{};
-    r.block = blocks[0];
-    r.refill_period = ks[1];
-    r.flights_per_phase = ms[0];
+    r.block = cur[0];
+    r.refill_period = cur[1];
+    r.flights_per_phase = cur[2];
     int rc = avalanche_run(ctx, &r, out, ws, ws_bytes, stream, &st);  // warm-up
     if (rc != GT_OK) return rc;
+    // measured shapes, so that no shape runs twice
+    std::vector<gt_tune_point> seen;
     int n = 0;
-    gt_tune_point top{0, 0, 0, 0, 0.0, 0.0};
-    for (int bi = 0; bi < nb; ++bi) {
-        for (int ki = 0; ki < nk; ++ki) {
-            for (int mi = 0; mi < nm; ++mi) {
-                r.block = blocks[bi];
-                r.refill_period = ks[ki];
-                r.flights_per_phase = ms[mi];
-                if (avalanche_run(ctx, &r, out, ws, ws_bytes, stream, &st) != GT_OK) continue;
-                gt_tune_point pt;
-                pt.block = r.block;
-                pt.refill_period = r.refill_period;
-                pt.flights_per_phase = r.flights_per_phase;
-                pt.transport_ms = st.transport_ms;
-                pt.real_per_ms =
-                    st.transport_ms > 0 ? (double)st.real_collisions / st.transport_ms : 0.0;
-                if (points && n < max_points) points[n] = pt;
-                ++n;
-                if (pt.real_per_ms > top.real_per_ms) top = pt;
+    auto measure = [&](int b, int k, int m) -> double {
+        for (const gt_tune_point &q : seen)
+            if (q.block == b && q.refill_period == k && q.flights_per_phase == m)
+                return q.real_per_ms;
+        r.block = b;
+        r.refill_period = k;
+        r.flights_per_phase = m;
+        gt_tune_point pt{b, k, m, 0, 0.0, 0.0};
+        if (avalanche_run(ctx, &r, out, ws, ws_bytes, stream, &st) == GT_OK) {
+            pt.transport_ms = st.transport_ms;
+            pt.real_per_ms =
+                st.transport_ms > 0 ? (double)st.real_collisions / st.transport_ms : 0.0;
+        }
+        seen.push_back(pt);
+        if (points && n < max_points) points[n] = pt;
+        ++n;
+        return pt.real_per_ms;
+    };
+    // coordinate descent: each dimension in turn takes its best value with
+    // the others held, until a whole sweep changes nothing (at most 4)
+    double top = measure(cur[0], cur[1], cur[2]);
+    for (int sweep = 0; sweep < 4; ++sweep) {
+        bool changed = false;
+        for (int d = 0; d < 3; ++d) {
+            for (int v : cand[d]) {
+                int s3[3] = {cur[0], cur[1], cur[2]};
+                s3[d] = v;
+                const double x = measure(s3[0], s3[1], s3[2]);
+                if (x > top) {
+                    top = x;
+                    changed = changed || v != cur[d];
+                    cur[d] = v;
+                }
             }
         }
+        if (!changed) break;
     }
     if (n_points) *n_points = n;
-    if (top.block == 0) return GT_ERR_UNSUPPORTED;
+    if (!(top > 0.0)) return GT_ERR_UNSUPPORTED;
     const int pi = fp64 ? 0 : 1, mi = r.majorant == GT_MAJORANT_BANDED ? 1 : 0;
     const int vi = run_variant(ctx, &r);
-    ctx->tuned_block[pi][ctx->field.kind][mi][vi] = top.block;
-    ctx->tuned_k[pi][ctx->field.kind][mi][vi] = top.refill_period;
-    ctx->tuned_m[pi][ctx->field.kind][mi][vi] = top.flights_per_phase;
-    *best = top;
+    ctx->tuned_block[pi][ctx->field.kind][mi][vi] = cur[0];
+    ctx->tuned_k[pi][ctx->field.kind][mi][vi] = cur[1];
+    ctx->tuned_m[pi][ctx->field.kind][mi][vi] = cur[2];
+    for (const gt_tune_point &q : seen)
+        if (q.block == cur[0] && q.refill_period == cur[1] && q.flights_per_phase == cur[2])
+            *best = q;
     return GT_OK;
 }
 

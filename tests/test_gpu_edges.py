@@ -115,9 +115,18 @@ def test_autotune_picks_and_remembers_a_shape(av):
     p = av.primaries_device(w.primaries)
     opt = A.RunOptions(seed=11, t_max=w.t_max, precision=A.GT_MIXED)
     best, pts = av.autotune(p, opt, capacity=2_000_000)
-    assert len(pts) == 64 and best["real_per_ms"] == max(q["real_per_ms"] for q in pts)
+    # coordinate descent: no shape measured twice, far fewer than the 64 of
+    # the full grid, and the best is the fastest shape measured
+    shapes = [(q["block"], q["refill_period"], q["flights_per_phase"]) for q in pts]
+    assert len(set(shapes)) == len(shapes) and 8 <= len(pts) <= 40
+    assert best["real_per_ms"] == max(q["real_per_ms"] for q in pts)
     assert best["block"] in (512, 768, 896, 1024) and best["refill_period"] in (4, 8, 16, 32)
     assert best["flights_per_phase"] in (1, 2, 4, 6)
+    # a dimension set in the run stays fixed
+    fixed, fpts = av.autotune(p, A.RunOptions(seed=11, t_max=w.t_max, precision=A.GT_MIXED,
+                                              block=768), capacity=2_000_000)
+    assert fixed["block"] == 768 and all(q["block"] == 768 for q in fpts)
+    best, pts = av.autotune(p, opt, capacity=2_000_000)
     st = av.run(p, opt, capacity=2_000_000)
     assert st["block"] == best["block"] and st["refill_period"] == best["refill_period"]
     assert st["flights_per_phase"] == best["flights_per_phase"]
