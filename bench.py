@@ -67,12 +67,11 @@ SM_COUNT = 152
 ISSUE_PER_SM_PER_CLK = 4       # warp schedulers per SM, one instruction each per clock
 LANES_PER_WARP = 32
 # DRAM bytes per electron of the batched kernel (ncu dram__bytes_read.sum +
-# dram__bytes_write.sum on the 256-avalanche case, divided by its
-# electrons; traffic grows with electrons, so it is scaled to a launch by
-# the electrons the launch stores).  None once the kernel has changed: the
-# last capture (199.8 B per electron) predates the 4-byte birth-element
-# field that every new electron now stores.
-DRAM_BYTES_PER_ELECTRON = None
+# dram__bytes_write.sum on the 256-avalanche case: 104.9 MB + 286.5 MB for
+# 2,014,813 electrons; traffic grows with electrons, so it is scaled to a
+# launch by the electrons the launch stores).  Set back to None when the
+# kernel changes, until the next capture.
+DRAM_BYTES_PER_ELECTRON = 194.3
 # Bytes per electron that the batched transport kernel must move by its
 # data layout: at birth the start record (x0 y0 z0 t0 e0, 40 B), id (8),
 # avalanche (4), birth velocity (24), birth element (4) and ready flag (4)
@@ -650,18 +649,25 @@ def run_ours(args) -> None:
 
 
 # ------------------------------------------------------------- calibration
-def calibration_workload(n_electrons: int, coll_limit: int = 1000):
+def calibration_workload(n_electrons: int, coll_limit: int = 1000, field: str = "plate"):
     """Straight-line flights for the instruction count per flight, run by the
-    same kernel instantiation as the benchmark (plate field): the argon-like
-    table with its ionisation rate set to zero (same 12-level selection, no
-    secondaries), 40 kV/cm, an anode too far away to reach, one electron per
-    thread from mid-gap, each stopped after `coll_limit` real collisions."""
+    same kernel instantiation as the benchmark line: the argon-like table
+    with its ionisation rate set to zero (same 12-level selection, no
+    secondaries), one electron per thread, each stopped after `coll_limit`
+    real collisions.  plate: 40 kV/cm, an anode too far away to reach, from
+    mid-gap; grid: the field-map line's 256^3 coax map (1810 V), from
+    r = 1 mm at mid-length (1000 collisions move an electron a few um)."""
     from paper_2509_15377_gb300 import workloads as W
     g = W.argon_like_gas()
     g.rate = g.rate.copy()
     g.rate[:, -1] = 0.0
     w = W.drift_model(n_electrons=n_electrons, n_coll=coll_limit, e_field=40_000.0, seed=0)
     w.gas = g
+    if field == "grid":
+        gs = W.grid_stress(n_avalanches=n_electrons, n=256, seed=0)
+        w.field = gs.field
+        w.primaries = gs.primaries
+        return w
     w.field = W.Field(W.PLATE, e0=40_000.0, gap=1.0e3)
     w.primaries.z[:] = 500.0
     return w
@@ -674,7 +680,7 @@ def run_calibration(args) -> None:
     from paper_2509_15377_gb300 import avalanche as A
     av = A.Avalanche(0)
     threads = SM_COUNT * (args.block or 1024)
-    w = calibration_workload(threads)
+    w = calibration_workload(threads, field=args.calibrate_field)
     av.set_gas(w.gas)
     av.set_field(w.field)
     prim = av.primaries_device(w.primaries)
@@ -687,7 +693,8 @@ def run_calibration(args) -> None:
     for _ in range(max(1, args.steps)):
         st = av.run(prim, opt, threads, allow=(A.GT_OK,))
     torch.cuda.synchronize()
-    print(json.dumps({"calibration": True, "electrons": threads, "flights": st["flights"],
+    print(json.dumps({"calibration": args.calibrate_field, "electrons": threads,
+                      "flights": st["flights"],
                       "warp_flights": st["flights"] / 32.0, "real": st["real_collisions"],
                       "transport_ms": st["transport_ms"], "block": st["block"],
                       "grid": st["grid"]}), flush=True)
@@ -761,6 +768,7 @@ def parse(argv=None):
     ap.add_argument("--map-tune-avalanches", type=int, default=96)
     ap.add_argument("--calibrate", action="store_true",
                     help="run the straight-line calibration workload (for ncu)")
+    ap.add_argument("--calibrate-field", default="plate", choices=["plate", "grid"])
     return ap.parse_args(argv)
 
 
