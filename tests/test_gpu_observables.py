@@ -20,7 +20,8 @@ kV/cm, Poisson(3) primaries, avalanches 0..511) and the coaxial tube with a
 1 T axial field (256 avalanches from r in 1-4.5 mm); in the tube the drift
 quantities are radial (v_r = sum (r0 - r1) / sum dt), azimuthal (the mean
 turn of the collected electrons about the wire, from the Lorentz force) and
-along the wire (var(dz) / (2 <dt>)).
+along the wire (var(dz) / (2 <dt>)); the same quantities on the 256^3
+grid-map configuration (48 avalanches at gain ~1e5).
 
 The measured differences are printed (pytest -s) for the error table.
 """
@@ -125,3 +126,24 @@ def test_mixed_coax_b_observables_vs_oracle(av):
         parts.append(O.per_avalanche(out, n, W.WIRE, np_, "coax"))
     gpu = {k: np.concatenate([q[k] for q in parts]) for k in parts[0]}
     _compare("coax_1T", O.per_avalanche(ref, n, W.WIRE, np_, "coax"), gpu, 0.0, "coax")
+
+
+def test_mixed_grid_map_observables_vs_oracle(av):
+    """The 256^3 coax-sampled grid map at gain ~1e5 (the high-gain stress
+    configuration): the oracle transports 48 avalanches through the same
+    map, the GPU the same avalanches with 8 seeds; gain, radial drift
+    velocity, turn about the wire (no B: zero within errors) and D_L along
+    the wire, as for the tube."""
+    n = 48
+    w = W.grid_stress(n_avalanches=n, n=256, seed=0)
+    av.set_gas(w.gas)
+    av.set_field(w.field)
+    ref = oracle.run(w.gas, w.field, w.primaries, seed=0, t_max=w.t_max, majorant=1)
+    np_ = _n_prim(w.primaries)
+    parts = []
+    for sd in range(404, 412):
+        _, out = run_gpu(av, w, seed=sd, precision=A.GT_MIXED, capacity=12_000_000,
+                         majorant=A.GT_MAJORANT_BANDED)
+        parts.append(O.per_avalanche(out, n, W.WIRE, np_, "coax"))
+    gpu = {k: np.concatenate([q[k] for q in parts]) for k in parts[0]}
+    _compare("grid_256^3", O.per_avalanche(ref, n, W.WIRE, np_, "coax"), gpu, 0.0, "coax")
