@@ -51,7 +51,7 @@ WORKLOAD = "plate_batched_4096"
 #   level choice, tally, isotropic direction and speed), counted from its
 #   arithmetic, one lane instruction per operation; what the kernel issues
 #   beyond it (spill code, addressing, control, FP64 folds) is overhead.
-LANE_INST_PER_FLIGHT_BY_BLOCK = {768: 413.3, 896: 402.1, 1024: 423.8}
+LANE_INST_PER_FLIGHT_BY_BLOCK = {768: 413.2, 896: 401.8, 1024: 423.6}
 ALGORITHMIC_LANE_INST_PER_FLIGHT = 190.0
 
 
@@ -67,11 +67,11 @@ SM_COUNT = 152
 ISSUE_PER_SM_PER_CLK = 4       # warp schedulers per SM, one instruction each per clock
 LANES_PER_WARP = 32
 # DRAM bytes per electron of the batched kernel (ncu dram__bytes_read.sum +
-# dram__bytes_write.sum on the 256-avalanche case: 104.9 MB + 286.5 MB for
-# 2,014,813 electrons; traffic grows with electrons, so it is scaled to a
+# dram__bytes_write.sum on the 256-avalanche case: 102.3 MB + 285.5 MB for
+# 2,017,258 electrons; traffic grows with electrons, so it is scaled to a
 # launch by the electrons the launch stores).  Set back to None when the
 # kernel changes, until the next capture.
-DRAM_BYTES_PER_ELECTRON = 194.3
+DRAM_BYTES_PER_ELECTRON = 192.3
 # Bytes per electron that the batched transport kernel must move by its
 # data layout: at birth the start record (x0 y0 z0 t0 e0, 40 B), id (8),
 # avalanche (4), birth velocity (24), birth element (4) and ready flag (4)
