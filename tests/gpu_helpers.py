@@ -52,3 +52,44 @@ def two_sample_ks(a, b):
     """Two-sample Kolmogorov-Smirnov statistic and asymptotic p-value."""
     from scipy import stats
     return stats.ks_2samp(a, b)
+
+
+def ks_statistic(a, b):
+    """Two-sample Kolmogorov-Smirnov statistic sup |F_a - F_b|."""
+    a, b = np.sort(a), np.sort(b)
+    x = np.concatenate([a, b])
+    fa = np.searchsorted(a, x, side="right") / len(a)
+    fb = np.searchsorted(b, x, side="right") / len(b)
+    return float(np.abs(fa - fb).max())
+
+
+def paired_avalanche_ks(va, ga, vb, gb, n_avalanches, n_perm=2000, seed=0):
+    """p-value of the KS statistic between two electron-level samples of the
+    same avalanches (values va with avalanche numbers ga, and vb, gb), from
+    a permutation of whole avalanches: under the hypothesis that both runs
+    draw each avalanche from one law, swapping avalanche i's electrons
+    between the runs leaves the joint law unchanged.  The electrons of an
+    avalanche are correlated, so the asymptotic p-value of a plain KS test
+    on electrons is too small; swapping avalanches keeps that correlation."""
+    rng = np.random.default_rng(seed)
+    A = [va[ga == i] for i in range(n_avalanches)]
+    B = [vb[gb == i] for i in range(n_avalanches)]
+    d0 = ks_statistic(va, vb)
+    hits = 0
+    for _ in range(n_perm):
+        sw = rng.random(n_avalanches) < 0.5
+        pa = np.concatenate([B[i] if sw[i] else A[i] for i in range(n_avalanches)])
+        pb = np.concatenate([A[i] if sw[i] else B[i] for i in range(n_avalanches)])
+        hits += ks_statistic(pa, pb) >= d0
+    return (1 + hits) / (1 + n_perm)
+
+
+def ratio_se(num, den, n_boot=2000, seed=0):
+    """Bootstrap standard error over avalanches of sum(num) / sum(den), with
+    num, den per avalanche (a fraction of the electrons of a run, whose
+    electrons are correlated within an avalanche)."""
+    rng = np.random.default_rng(seed)
+    num, den = np.asarray(num, dtype=float), np.asarray(den, dtype=float)
+    idx = rng.integers(0, len(num), size=(n_boot, len(num)))
+    r = num[idx].sum(axis=1) / np.maximum(den[idx].sum(axis=1), 1e-300)
+    return float(r.std(ddof=1))
