@@ -18,8 +18,8 @@
  *   null-collision technique of Skullerud (Sec. 1, ref. HRSkullerud_1968) and
  *   tabulated per-level collision rates (Sec. 1, ref. Biagi).  The concrete
  *   step used here, in the order the loop below takes it:
- *     1. four uniforms from Philox4x32-10 keyed by (seed, avalanche) with the
- *        counter (flight index, 0, electron id);
+ *     1. four uniforms from Philox4x32-10 keyed by the seed with the
+ *        counter (flight index, 2 x avalanche, electron id);
  *     2. the field E (and uniform B) at the start of the flight, held
  *        constant for the flight;
  *     3. free flight dt = -ln(u0)/nu_max, truncated at the time limit, with
@@ -146,7 +146,7 @@ typedef struct {
     int32_t signal_bins;             /* time bins of the induced signal */
     double signal_t0, signal_dt;     /* bin j covers [t0 + j dt, t0 + (j+1) dt) */
     int32_t aval_base;               /* number of avalanche 0 in a larger workload: the
-                                        random streams are keyed by aval + aval_base, so
+                                        random counters hold aval + aval_base, so
                                         avalanches [a0, a1) of a workload run alone with
                                         aval_base = a0 are those of the whole run (they
                                         are independent, Sec. 2) */
@@ -181,12 +181,16 @@ void or_philox4x32_10(const uint32_t ctr[4], const uint32_t key[2], uint32_t out
 /* Open-interval uniform from one 32-bit word: (w + 1/2) / 2^32, exact. */
 static double uniform01(uint32_t w) { return ((double)w + 0.5) * (1.0 / 4294967296.0); }
 
-/* The four uniforms of draw `sub` of flight `flight` of electron `uid`. */
+/* The four uniforms of draw `sub` (0 or 1) of flight `flight` of electron
+ * `uid` in avalanche `aval`: the key is the seed alone, and the counter
+ * (flight, 2 aval + sub, uid_lo, uid_hi) is distinct for every draw of the
+ * run, so every draw is its own block of one Philox stream. */
 static void draw4(uint64_t seed, int32_t aval, uint64_t uid, uint32_t flight,
                   uint32_t sub, double u[4])
 {
-    uint32_t key[2] = {(uint32_t)seed ^ (uint32_t)aval, (uint32_t)(seed >> 32)};
-    uint32_t ctr[4] = {flight, sub, (uint32_t)uid, (uint32_t)(uid >> 32)};
+    uint32_t key[2] = {(uint32_t)seed, (uint32_t)(seed >> 32)};
+    uint32_t ctr[4] = {flight, ((uint32_t)aval << 1) | sub, (uint32_t)uid,
+                       (uint32_t)(uid >> 32)};
     uint32_t w[4];
     or_philox4x32_10(ctr, key, w);
     for (int i = 0; i < 4; ++i) u[i] = uniform01(w[i]);

@@ -53,6 +53,19 @@ struct gt_ctx {
 };
 
 namespace {
+// The seed and its Philox round keys: (k0, k1) = (seed_lo, seed_hi) advanced
+// by the Weyl constants 0x9E3779B9, 0xBB67AE85 after each of the ten rounds.
+static void set_seed(RunParams &p, uint64_t seed)
+{
+    p.seed = seed;
+    uint32_t k0 = (uint32_t)seed, k1 = (uint32_t)(seed >> 32);
+    for (int r = 0; r < 10; ++r) {
+        p.rk[2 * r] = k0;
+        p.rk[2 * r + 1] = k1;
+        k0 += 0x9E3779B9u;
+        k1 += 0xBB67AE85u;
+    }
+}
 
 // Makes the context's device current for the duration of a call.
 struct DeviceGuard {
@@ -910,7 +923,7 @@ static int plan_run(gt_ctx *ctx, const gt_run *r, const gt_endpoints *o, void *w
     p.bvz = reinterpret_cast<double *>(base + Ly.bvz);
     p.belem = reinterpret_cast<int32_t *>(base + Ly.belem);
     p.created = reinterpret_cast<unsigned long long *>(base + Ly.created);
-    p.seed = r->seed;
+    set_seed(p, r->seed);
     p.t_max = r->t_max > 0.0 ? r->t_max : 0.0;
     p.coll_limit = r->coll_limit;
     const int prec_i = r->precision == GT_FP64 ? 0 : 1;
@@ -1308,7 +1321,7 @@ int gt_graph_launch(gt_graph *g, uint64_t seed, void *stream)
     if (!dg.ok) return GT_ERR_CUDA;
     if (seed != g->seed) {
         // a new seed: record the run again and update the instantiated graph
-        g->pl.p.seed = seed;
+        set_seed(g->pl.p, seed);
         cudaGraph_t gr = nullptr;
         int rc = graph_capture(g, &gr);
         if (rc != GT_OK) return rc;

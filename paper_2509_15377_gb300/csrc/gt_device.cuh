@@ -155,7 +155,8 @@ struct RunParams {
     uint64_t size_limit;
     long long spin_limit_ns, time_limit_ns;
     int n_avalanches;
-    int aval_base;          // workload number of avalanche 0 (random-stream key only)
+    int aval_base;          // workload number of avalanche 0 (random-stream counter only)
+    uint32_t rk[20];        // Philox round keys of the seed: (k0, k1) of rounds 0..9
 };
 
 // --------------------------------------------------------- small helpers
@@ -210,13 +211,31 @@ __device__ __forceinline__ uint4 philox10(uint4 c, uint32_t k0, uint32_t k1)
     return c;
 }
 
-// Stream of electron `uid` in avalanche `aval`: key (seed_lo ^ aval,
-// seed_hi), counter (flight, sub, uid_lo, uid_hi).
+// Stream of electron `uid` in avalanche `aval`: key (seed_lo, seed_hi),
+// counter (flight, 2 aval + sub, uid_lo, uid_hi).
 __device__ __forceinline__ uint4 draw(uint64_t seed, int aval, uint64_t uid, uint32_t flight,
                                       uint32_t sub)
 {
-    return philox10(make_uint4(flight, sub, (uint32_t)uid, (uint32_t)(uid >> 32)),
-                    (uint32_t)seed ^ (uint32_t)aval, (uint32_t)(seed >> 32));
+    return philox10(make_uint4(flight, ((uint32_t)aval << 1) | sub, (uint32_t)uid,
+                               (uint32_t)(uid >> 32)),
+                    (uint32_t)seed, (uint32_t)(seed >> 32));
+}
+
+// The same with the round keys of the seed taken from the run parameters
+// (rk[2r], rk[2r + 1] = key + r * Weyl constants): the key schedule costs no
+// instruction per block.
+__device__ __forceinline__ uint4 draw_rk(const uint32_t (&rk)[20], int aval, uint64_t uid,
+                                         uint32_t flight, uint32_t sub)
+{
+    uint4 c = make_uint4(flight, ((uint32_t)aval << 1) | sub, (uint32_t)uid,
+                         (uint32_t)(uid >> 32));
+#pragma unroll
+    for (int r = 0; r < 10; ++r) {
+        const uint32_t lo_a = 0xD2511F53u * c.x, hi_a = __umulhi(0xD2511F53u, c.x);
+        const uint32_t lo_b = 0xCD9E8D57u * c.z, hi_b = __umulhi(0xCD9E8D57u, c.z);
+        c = make_uint4(hi_b ^ c.y ^ rk[2 * r], lo_b, hi_a ^ c.w ^ rk[2 * r + 1], lo_a);
+    }
+    return c;
 }
 
 // (w + 1/2) 2^-32 in (0, 1), exact in FP64.
@@ -1681,7 +1700,7 @@ struct MixedElectron {
             status = GT_ST_FLIGHT_LIMIT;
             return EV_RETIRE;
         }
-        const uint4 w = draw(p.seed, aval + p.aval_base, uid, nf, 0u);
+        const uint4 w = draw_rk(p.rk, aval + p.aval_base, uid, nf, 0u);
         float ex, ey, ez;
         efield<FK>(p, ex, ey, ez);
         const float ax = -kAccelF * ex, ay = -kAccelF * ey, az = -kAccelF * ez;
