@@ -42,7 +42,9 @@ WORKLOAD = "plate_batched_4096"
 # - calibrated: lane instructions of the kernel's own straight-line step,
 #   ncu smsp__thread_inst_executed.sum / flights on `bench.py --calibrate
 #   --steps 1 --block B --refill-period 32 --flights-per-phase 1` with the
-#   banded majorant, per launch bound B (the spill code differs).  Lanes
+#   banded majorant (the step's build for one flight per round, band bounds
+#   rising with energy and no magnetic field), per launch bound B (the
+#   register allocation differs).  Lanes
 #   switched off by divergence are not counted, so divergence, stalls and
 #   queue work all show as lost efficiency;
 # - algorithmic: the operations the method needs per flight of the mixed
@@ -51,7 +53,7 @@ WORKLOAD = "plate_batched_4096"
 #   level choice, tally, isotropic direction and speed), counted from its
 #   arithmetic, one lane instruction per operation; what the kernel issues
 #   beyond it (spill code, addressing, control, FP64 folds) is overhead.
-LANE_INST_PER_FLIGHT_BY_BLOCK = {768: 413.2, 896: 401.8, 1024: 423.6}
+LANE_INST_PER_FLIGHT_BY_BLOCK = {768: 330.6, 896: 328.7, 1024: 332.9}
 ALGORITHMIC_LANE_INST_PER_FLIGHT = 190.0
 
 
@@ -71,7 +73,7 @@ LANES_PER_WARP = 32
 # 2,017,258 electrons; traffic grows with electrons, so it is scaled to a
 # launch by the electrons the launch stores).  Set back to None when the
 # kernel changes, until the next capture.
-DRAM_BYTES_PER_ELECTRON = 192.3
+DRAM_BYTES_PER_ELECTRON = None
 # Bytes per electron that the batched transport kernel must move by its
 # data layout: at birth the start record (x0 y0 z0 t0 e0, 40 B), id (8),
 # avalanche (4), birth velocity (24), birth element (4) and ready flag (4)

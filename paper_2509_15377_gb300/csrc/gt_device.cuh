@@ -1360,6 +1360,31 @@ struct Fp64Electron {
 // one collision round) until collide() selects the level and scatters.
 // Each electron still takes exactly the sequence flight, collision,
 // flight, ... with the same random numbers.
+// Speed after an elastic collision that turns the direction from v to the
+// unit vector n (cos chi = mu when `given`, else from v and n), with the
+// recoil factor r: |v'| = |v| sqrt(1 - x), x = r (1 - cos chi), scaled on
+// the speed itself; a round trip through the energy would multiply by
+// (2a)_f32 * (1/2a)_f32 != 1 at every collision and drift.
+// |v| = v2 / sqrt(v2) from the hardware rsqrt with one Newton step in
+// residual form, r + r h with h = 1/2 - v2 r^2 / 2 from an FMA: within ~2 ulp
+// and unbiased (a refinement factor rounded near 1.0 biases the speed by
+// ~1e-8 per collision).  Then |v'| = |v| - |v| d with
+// d = x/2 + x^2/8 = 1 - sqrt(1 - x) to O(x^3) (x <= 2 recoil ~ 5e-5), one
+// FMA: multiplying by a factor rounded just below 1.0 would bias it by
+// ~3e-10 per collision (a float32 emulation of both forms; this one is
+// unbiased).
+__device__ __forceinline__ float elastic_speed32(float vx, float vy, float vz, float nx, float ny,
+                                                 float nz, bool given, float mu, float recoil)
+{
+    const float v2 = vx * vx + vy * vy + vz * vz;
+    float r = rsqrtf(v2);
+    r = fmaf(r, fmaf(-0.5f * v2 * r, r, 0.5f), r);
+    const float cchi = given ? mu : (vx * nx + vy * ny + vz * nz) * r;
+    const float x = recoil * (1.0f - cchi);
+    const float vm = v2 * r, d = fmaf(0.125f * x, x, 0.5f * x);
+    return v2 > 0.f ? fmaf(-vm, d, vm) : 0.f;
+}
+
 struct MixedElectron {
     static constexpr bool kTwoPhase = true;
     struct ChildT {
@@ -1602,11 +1627,13 @@ struct MixedElectron {
                                       f.hi[1], f.hi[2]);
     }
 
-    // Exact motion of the FP32 offsets over dt with the acceleration a.
-    __device__ __forceinline__ void move(const RunParams &p, float ax, float ay, float az, float dt)
+    // Exact motion of the FP32 offsets over dt with the acceleration a
+    // (no_b: the run has no magnetic field, known at compile time).
+    __device__ __forceinline__ void move(const RunParams &p, float ax, float ay, float az, float dt,
+                                         bool no_b = false)
     {
         float dx, dy, dz;
-        if (!p.field.has_b) {
+        if (no_b || !p.field.has_b) {
             const float h = 0.5f * dt;
             dx = dt * fmaf(h, ax, vx);
             dy = dt * fmaf(h, ay, vy);
@@ -1692,7 +1719,10 @@ struct MixedElectron {
     // add random time step", "Collision?").  Returns EV_RETIRE or EV_NONE;
     // fills `pd` (pd.real) for a real collision.  GEO = true also builds
     // the sub-steps and exact crossings of fly_steps().
-    template <int FK, bool GEO>
+    // MAJ = 1 builds the step for runs with the banded majorant, band bounds
+    // that rise with energy, no magnetic field and the field held over the
+    // flight (the common case), without the run-time tests of the others.
+    template <int FK, bool GEO, int MAJ = 0>
     __device__ __forceinline__ int advance(const RunParams &p, const Tables &tb, Pending &pd)
     {
         pd.real = false;
@@ -1706,14 +1736,15 @@ struct MixedElectron {
         const float ax = -kAccelF * ex, ay = -kAccelF * ey, az = -kAccelF * ez;
         float nu = p.gas.nu_max_f, dt;
         bool pseudo = false;
-        if (p.majorant == GT_MAJORANT_BANDED) {
+        if (MAJ == 1 || p.majorant == GT_MAJORANT_BANDED) {
             // the rate bound over the energies reachable within the window
+            const bool mono = MAJ == 1 || p.gas.bands_monotone;
             const float eps0 = (vx * vx + vy * vy + vz * vz) * kInvTwoAccelF;
             const float tau = __fdividef(p.window_f, tb.band32[band_index32(p.gas, eps0)]);
             float lo, hi;
-            reach32<FK>(p.field.has_b, p.field_emax_f, eps0, vx, vy, vz, ex, ey, ez, plate_e, tau,
-                        lo, hi, !p.gas.bands_monotone);
-            nu = p.gas.bands_monotone
+            reach32<FK>(MAJ == 1 ? 0 : p.field.has_b, MAJ == 1 ? 0.0f : p.field_emax_f, eps0, vx,
+                        vy, vz, ex, ey, ez, plate_e, tau, lo, hi, !mono);
+            nu = mono
                      ? tb.band32[band_index32(p.gas, hi)]
                      : band_range_max(tb.band32, p.gas.n_bands, band_index32(p.gas, lo),
                                       band_index32(p.gas, hi));
@@ -1734,21 +1765,18 @@ struct MixedElectron {
         if (GEO && (p.substeps > 1 || p.crossing || p.signal_bins)) {
             st = fly_steps<FK>(p, dt, ex, ey, ez);
         } else {
-            move(p, ax, ay, az, dt);
+            move(p, ax, ay, az, dt, MAJ == 1);
             ot += dt;
             st = boundary<FK>(p);
         }
         ++nf;
-        if (st) {
-            status = st;
+        if (st | (int)timed) {
+            status = st ? st : GT_ST_TIME;
             return EV_RETIRE;
         }
-        if (timed) {
-            status = GT_ST_TIME;
-            return EV_RETIRE;
-        }
-        if (pseudo) return EV_NONE;  // the window ended before a collision
-        // null test against the interpolated total rate
+        // null test against the interpolated total rate, as straight-line
+        // code; a pseudo-flight (the window ended before a collision) takes
+        // no test
         const float eps = (vx * vx + vy * vy + vz * vz) * kInvTwoAccelF;
         const float R = u01f(w.y) * nu;
         const float xk = eps * p.gas.inv_d_eps_f;
@@ -1758,17 +1786,15 @@ struct MixedElectron {
         const int L = p.gas.n_levels;
         const float *c0 = tb.cum32 + k * tb.stride32 + (L - 1);
         const float top = fmaf(f, c0[tb.stride32] - c0[0], c0[0]);
-        if (R < top) {
-            pd.real = true;
-            pd.R = R;
-            pd.eps = eps;
-            pd.k = k;
-            pd.f = f;
-            pd.w2 = w.z;
-            pd.w3 = w.w;
-        } else {
-            ++nnull;
-        }
+        const bool real = !pseudo && R < top;
+        pd.real = real;
+        pd.R = R;
+        pd.eps = eps;
+        pd.k = k;
+        pd.f = f;
+        pd.w2 = w.z;
+        pd.w3 = w.w;
+        nnull += (!pseudo && !real) ? 1u : 0u;
         return EV_NONE;
     }
 
@@ -1789,6 +1815,22 @@ struct MixedElectron {
         // the warp skips the search
         const bool lvl0 = p.gas.level0_elastic &&
                           __all_sync(__activemask(), pd.R < fmaf(pd.f, c0[tb.stride32] - c0[0], c0[0]));
+        if (lvl0 && !(PHYS && p.gas.any_aniso)) {
+            // the common case as straight-line code: every colliding lane of
+            // the warp scatters elastically and isotropically on level 0
+            tb.tally[threadIdx.x] += 1u;
+            float nx, ny, nz;
+            isotropic32(u01f(pd.w2), u01f(pd.w3), nx, ny, nz);
+            const float sp = elastic_speed32(vx, vy, vz, nx, ny, nz, false, 0.0f,
+                                             p.gas.recoil_f);
+            vx = sp * nx; vy = sp * ny; vz = sp * nz;
+            ++nreal;
+            if (p.coll_limit && nreal >= p.coll_limit) {
+                status = GT_ST_COLL_LIMIT;
+                return EV_RETIRE;
+            }
+            return EV_NONE;
+        }
         const int lvl = lvl0 ? 0 : select_below_total32(c0, tb.stride32, p.gas.n_levels, pd.f, pd.R);
         const int type = tb.type[lvl];
         if (type != GT_LEVEL_ELASTIC) {
@@ -1818,24 +1860,7 @@ struct MixedElectron {
         else
             isotropic32(u01f(pd.w2), u01f(pd.w3), nx, ny, nz);
         if (type == GT_LEVEL_ELASTIC) {
-            // scale the speed itself: |v'| = |v| sqrt(1 - x), x = recoil (1 -
-            // cos chi); a round trip through the energy would multiply by
-            // (2a)_f32 * (1/2a)_f32 != 1 at every collision and drift.
-            // |v| = v2 / sqrt(v2) from the hardware rsqrt with one Newton step
-            // in residual form, r + r h with h = 1/2 - v2 r^2 / 2 from an FMA:
-            // within ~2 ulp and unbiased (a refinement factor rounded near
-            // 1.0 biases the speed by ~1e-8 per collision).  Then
-            // |v'| = |v| - |v| d with d = x/2 + x^2/8 = 1 - sqrt(1 - x) to
-            // O(x^3) (x <= 2 recoil ~ 5e-5), one FMA: multiplying by a factor
-            // rounded just below 1.0 would bias it by ~3e-10 per collision
-            // (a float32 emulation of both forms; this one is unbiased).
-            const float v2 = vx * vx + vy * vy + vz * vz;
-            float r = rsqrtf(v2);
-            r = fmaf(r, fmaf(-0.5f * v2 * r, r, 0.5f), r);
-            const float cchi = xi != 0.0f ? mu : (vx * nx + vy * ny + vz * nz) * r;
-            const float x = p.gas.recoil_f * (1.0f - cchi);
-            const float vm = v2 * r, d = fmaf(0.125f * x, x, 0.5f * x);
-            sp = v2 > 0.f ? fmaf(-vm, d, vm) : 0.f;
+            sp = elastic_speed32(vx, vy, vz, nx, ny, nz, xi != 0.0f, mu, p.gas.recoil_f);
         } else {
             float eps_new = fmaxf(eps - tb.thr_f[lvl], 0.0f);
             if (type == GT_LEVEL_IONISATION) {

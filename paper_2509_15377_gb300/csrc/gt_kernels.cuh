@@ -237,7 +237,6 @@ __global__ void __launch_bounds__(MAXT) k_batched(const RunParams p)
             // the whole warp waits: finished when every queued electron is done
             const int r = __reduce_add_sync(FULL, retired);
             if (r) {
-                __threadfence();
                 if (lane == 0) atomicAdd(&p.hdr->done, (unsigned long long)r);
                 continue;
             }
@@ -275,17 +274,25 @@ __global__ void __launch_bounds__(MAXT) k_batched(const RunParams p)
             // pending collision fly (at most M flights) until they meet a
             // real one; then the warp applies its lanes' collisions together.
             // MP = 1 builds the one-flight round (M = 1) at compile time.
-            const int M = MP ? MP : p.flights_per_phase;
+            // MP = 2: one flight per round and the step built for the common
+            // run (MixedElectron::advance with MAJ = 1)
+            constexpr int MPF = MP == 2 ? 1 : MP;
+            constexpr int MAJ = MP == 2 ? 1 : 0;
+            const int M = MPF ? MPF : p.flights_per_phase;
+            // an electron that finishes during the rounds keeps its lane (a
+            // lane takes a new electron only at the next refill) and is
+            // written out after the last round, together with the warp's
+            // other finished electrons, instead of one divergent pass each
+            bool fin = false;
             for (int k = 0; k < K; ++k) {
                 typename E::Pending pd;
                 pd.real = false;
                 for (int mm = 0; mm < M; ++mm) {
                     const bool go = has && !pd.real;
-                    if (MP != 1 && !__any_sync(FULL, go)) break;
-                    if (go && (e.template advance<FK, GEO>(p, tb, pd) & EV_RETIRE)) {
-                        finish<GEO>(p, tb, e, bs);
+                    if (MPF != 1 && !__any_sync(FULL, go)) break;
+                    if (go && (e.template advance<FK, GEO, MAJ>(p, tb, pd) & EV_RETIRE)) {
                         has = false;
-                        ++retired;
+                        fin = true;
                     }
                 }
                 typename E::ChildT ch;
@@ -294,10 +301,13 @@ __global__ void __launch_bounds__(MAXT) k_batched(const RunParams p)
                 if (__any_sync(FULL, ev & EV_CHILD))
                     retired += push_children(p, (ev & EV_CHILD) != 0, e, ch, lane);
                 if (ev & EV_RETIRE) {
-                    finish<GEO>(p, tb, e, bs);
                     has = false;
-                    ++retired;
+                    fin = true;
                 }
+            }
+            if (fin) {
+                finish<GEO>(p, tb, e, bs);
+                ++retired;
             }
         } else {
             // K flights per electron between refills
@@ -316,12 +326,12 @@ __global__ void __launch_bounds__(MAXT) k_batched(const RunParams p)
         }
         if (has) e.template round_end<FK>(p);
 
-        // finished electrons are published after their endpoint writes
+        // finished electrons are counted; the count only decides when the
+        // launch may end (done == tail), and no kernel reads an endpoint, so
+        // no fence orders the endpoint writes before it (the launch's end
+        // makes them visible to the host)
         const int r = __reduce_add_sync(FULL, retired);
-        if (r) {
-            __threadfence();
-            if (lane == 0) atomicAdd(&p.hdr->done, (unsigned long long)r);
-        }
+        if (r && lane == 0) atomicAdd(&p.hdr->done, (unsigned long long)r);
         // the run-wide checks: the time budget, and an abort from any warp
         unsigned stop = 0;
         if (lane == 0) {

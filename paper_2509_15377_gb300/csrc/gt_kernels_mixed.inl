@@ -20,9 +20,24 @@ namespace gt {
 constexpr int kMaxThreadsMixed = 1024;
 constexpr int kPlainThreadsMixed = 512;
 
+// The run the step has a build of its own for (MP = 2): one flight per
+// round, the banded majorant with band bounds rising with energy, no
+// magnetic field, the field held over each flight.
+static bool common_run(const RunParams &p)
+{
+    return p.flights_per_phase == 1 && p.majorant == GT_MAJORANT_BANDED &&
+           p.gas.bands_monotone && !p.field.has_b && p.field_emax_f == 0.0f;
+}
+
 template <int FK, bool TAB, int MAXT, bool PHYS, bool GEO>
 static cudaError_t batched_t(const RunParams &p, int grid, int block, size_t smem, cudaStream_t s)
 {
+    if constexpr (!PHYS && !GEO) {
+        if (common_run(p)) {
+            k_batched<MixedElectron, FK, TAB, MAXT, 2, PHYS, GEO><<<grid, block, smem, s>>>(p);
+            return cudaGetLastError();
+        }
+    }
     if (p.flights_per_phase == 1)
         k_batched<MixedElectron, FK, TAB, MAXT, 1, PHYS, GEO><<<grid, block, smem, s>>>(p);
     else
@@ -114,6 +129,9 @@ static cudaError_t configure_one(size_t max_smem)
     cudaError_t e;
     if ((e = configure_mp<FK, TAB, 0, PHYS, GEO>(max_smem)) != cudaSuccess) return e;
     if ((e = configure_mp<FK, TAB, 1, PHYS, GEO>(max_smem)) != cudaSuccess) return e;
+    if constexpr (!PHYS && !GEO) {
+        if ((e = configure_mp<FK, TAB, 2, PHYS, GEO>(max_smem)) != cudaSuccess) return e;
+    }
     return allow_dynamic_smem(k_plain_transport<MixedElectron, FK, TAB, kPlainThreadsMixed, PHYS, GEO>,
                               max_smem);
 }
