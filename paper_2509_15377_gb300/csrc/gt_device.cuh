@@ -1628,17 +1628,24 @@ struct MixedElectron {
     }
 
     // Exact motion of the FP32 offsets over dt with the acceleration a
-    // (no_b: the run has no magnetic field, known at compile time).
+    // (no_b: the run has no magnetic field; z_only: the field is along z, so
+    // ax = ay = 0 and x, y move uniformly; both known at compile time).
     __device__ __forceinline__ void move(const RunParams &p, float ax, float ay, float az, float dt,
-                                         bool no_b = false)
+                                         bool no_b = false, bool z_only = false)
     {
         float dx, dy, dz;
         if (no_b || !p.field.has_b) {
             const float h = 0.5f * dt;
-            dx = dt * fmaf(h, ax, vx);
-            dy = dt * fmaf(h, ay, vy);
+            if (z_only) {
+                dx = dt * vx;
+                dy = dt * vy;
+            } else {
+                dx = dt * fmaf(h, ax, vx);
+                dy = dt * fmaf(h, ay, vy);
+                vx = fmaf(ax, dt, vx); vy = fmaf(ay, dt, vy);
+            }
             dz = dt * fmaf(h, az, vz);
-            vx = fmaf(ax, dt, vx); vy = fmaf(ay, dt, vy); vz = fmaf(az, dt, vz);
+            vz = fmaf(az, dt, vz);
         } else {
             lorentz_step<float>(p.field.w_f, ax, ay, az, dt, vx, vy, vz, dx, dy, dz);
         }
@@ -1720,8 +1727,9 @@ struct MixedElectron {
     // fills `pd` (pd.real) for a real collision.  GEO = true also builds
     // the sub-steps and exact crossings of fly_steps().
     // MAJ = 1 builds the step for runs with the banded majorant, band bounds
-    // that rise with energy, no magnetic field and the field held over the
-    // flight (the common case), without the run-time tests of the others.
+    // that rise with energy, an elastic level 0, no magnetic field and the
+    // field held over the flight (the common case), without the run-time
+    // tests of the others.
     template <int FK, bool GEO, int MAJ = 0>
     __device__ __forceinline__ int advance(const RunParams &p, const Tables &tb, Pending &pd)
     {
@@ -1765,7 +1773,7 @@ struct MixedElectron {
         if (GEO && (p.substeps > 1 || p.crossing || p.signal_bins)) {
             st = fly_steps<FK>(p, dt, ex, ey, ez);
         } else {
-            move(p, ax, ay, az, dt, MAJ == 1);
+            move(p, ax, ay, az, dt, MAJ == 1, FK == GT_FIELD_PLATE || FK == GT_FIELD_UNIFORM);
             ot += dt;
             st = boundary<FK>(p);
         }
@@ -1803,7 +1811,7 @@ struct MixedElectron {
     // PHYS = false builds the collision of a gas with isotropic levels, no
     // attachment and a uniform ionisation split (the basic gas) without the
     // code of the general case; PHYS = true handles every gas.
-    template <int FK, bool PHYS>
+    template <int FK, bool PHYS, int MAJ = 0>
     __device__ __forceinline__ int collide(const RunParams &p, const Tables &tb, Pending &pd,
                                            ChildT &ch)
     {
@@ -1813,7 +1821,7 @@ struct MixedElectron {
         // most real collisions are elastic (level 0 when it is the elastic
         // level): when every colliding lane's R lies below the level-0 sum,
         // the warp skips the search
-        const bool lvl0 = p.gas.level0_elastic &&
+        const bool lvl0 = (MAJ == 1 || p.gas.level0_elastic) &&
                           __all_sync(__activemask(), pd.R < fmaf(pd.f, c0[tb.stride32] - c0[0], c0[0]));
         if (lvl0 && !(PHYS && p.gas.any_aniso)) {
             // the common case as straight-line code: every colliding lane of

@@ -297,7 +297,7 @@ __global__ void __launch_bounds__(MAXT) k_batched(const RunParams p)
                 }
                 typename E::ChildT ch;
                 int ev = EV_NONE;
-                if (pd.real) ev = e.template collide<FK, PHYS>(p, tb, pd, ch);
+                if (pd.real) ev = e.template collide<FK, PHYS, MAJ>(p, tb, pd, ch);
                 if (__any_sync(FULL, ev & EV_CHILD))
                     retired += push_children(p, (ev & EV_CHILD) != 0, e, ch, lane);
                 if (ev & EV_RETIRE) {

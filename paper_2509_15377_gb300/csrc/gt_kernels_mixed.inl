@@ -21,12 +21,13 @@ constexpr int kMaxThreadsMixed = 1024;
 constexpr int kPlainThreadsMixed = 512;
 
 // The run the step has a build of its own for (MP = 2): one flight per
-// round, the banded majorant with band bounds rising with energy, no
-// magnetic field, the field held over each flight.
+// round, the banded majorant with band bounds rising with energy, an
+// elastic level 0, no magnetic field, the field held over each flight.
 static bool common_run(const RunParams &p)
 {
     return p.flights_per_phase == 1 && p.majorant == GT_MAJORANT_BANDED &&
-           p.gas.bands_monotone && !p.field.has_b && p.field_emax_f == 0.0f;
+           p.gas.bands_monotone && p.gas.level0_elastic && !p.field.has_b &&
+           p.field_emax_f == 0.0f;
 }
 
 template <int FK, bool TAB, int MAXT, bool PHYS, bool GEO>
