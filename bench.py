@@ -55,14 +55,29 @@ WORKLOAD = "plate_batched_4096"
 #   beyond it (spill code, addressing, control, FP64 folds) is overhead.
 LANE_INST_PER_FLIGHT_BY_BLOCK = {768: 323.3, 896: 317.8, 1024: 322.5}
 ALGORITHMIC_LANE_INST_PER_FLIGHT = 190.0
+# The same calibration for the field-map line on the 256^3 grid (`bench.py
+# --calibrate --calibrate-field grid --block B --refill-period 16
+# --flights-per-phase 1`: straight-line flights at r = 1 mm in the map, the
+# step plus eight float4 gathers and the trilinear interpolation per flight).
+GRID_LANE_INST_PER_FLIGHT_BY_BLOCK = {512: 439.4, 768: 457.1, 1024: 455.7}
 
 
-def lane_inst_per_flight(block: int) -> float:
-    """The calibration of the launch bound a block size runs under."""
-    for bound in sorted(LANE_INST_PER_FLIGHT_BY_BLOCK):
+def lane_inst_per_flight(block: int, table=None) -> float:
+    """The calibration of the launch bound a block size runs under (None
+    when the table has none)."""
+    table = LANE_INST_PER_FLIGHT_BY_BLOCK if table is None else table
+    if not table:
+        return None
+    for bound in sorted(table):
         if block <= bound:
-            return LANE_INST_PER_FLIGHT_BY_BLOCK[bound]
-    return LANE_INST_PER_FLIGHT_BY_BLOCK[max(LANE_INST_PER_FLIGHT_BY_BLOCK)]
+            return table[bound]
+    return table[max(table)]
+
+
+def issue_peak(sm_max_mhz) -> float:
+    """Lane instructions per second of the whole GPU, in G: 152 SMs x 4
+    schedulers x 32 lanes x the SM clock."""
+    return SM_COUNT * ISSUE_PER_SM_PER_CLK * LANES_PER_WARP * (sm_max_mhz or 2070.0) * 1e6 / 1e9
 
 
 SM_COUNT = 152
@@ -279,6 +294,19 @@ def field_map_lines(av, args, seed: int, cap: int, stream, flush, majorant) -> d
                       "autotune": tuned}
         if name == "grid":
             maps[name]["map"] = "256^3 float4 nodes, trilinear"
+            lipf = lane_inst_per_flight(m_st["block"], GRID_LANE_INST_PER_FLIGHT_BY_BLOCK)
+            if lipf:
+                # issue roofline of the line: the calibrated work per flight
+                # times the line's flights per second of transport time; the
+                # line's first ~15 ns run only its 256 primaries (latency)
+                ach = lipf * m_fl / (m_ms / 1e3) / 1e9
+                peak = issue_peak(None)
+                maps[name]["roofline"] = {
+                    "bound": "alu", "achieved": ach, "peak": peak, "unit": "Glane-inst/s",
+                    "frac": ach / peak, "lane_inst_per_flight": lipf,
+                    "flights_per_s": m_fl / (m_ms / 1e3),
+                    "kernel": "k_batched<MixedElectron, GRID, smem table>",
+                    "peak_note": "152 SMs x 4 schedulers x 32 lanes x 2070 MHz"}
         else:
             maps[name]["map"] = (f"{wl.field.mesh_tets.shape[0]} tetrahedra, "
                                  f"{wl.field.mesh_nodes.shape[0]} nodes, linear, "
@@ -584,8 +612,7 @@ def run_ours(args) -> None:
     kms = statistics.mean(kernel_ms)
     fl_per_launch = flights / len(kernel_ms)
     peak_clk = clk.get("sm_max_mhz") or 2070.0
-    # G lane-instructions/s: SMs x schedulers x lanes x max SM clock
-    peak = SM_COUNT * ISSUE_PER_SM_PER_CLK * LANES_PER_WARP * peak_clk * 1e6 / 1e9
+    peak = issue_peak(peak_clk)
     lipf = lane_inst_per_flight(stats[-1]["block"])
     achieved = lipf * fl_per_launch / (kms / 1e3) / 1e9
     achieved_alg = ALGORITHMIC_LANE_INST_PER_FLIGHT * fl_per_launch / (kms / 1e3) / 1e9
