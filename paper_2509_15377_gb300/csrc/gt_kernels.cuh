@@ -208,7 +208,19 @@ __global__ void __launch_bounds__(MAXT) k_batched(const RunParams p)
     if (lane == 0) err0 = *reinterpret_cast<volatile unsigned *>(&p.hdr->error);
     const bool stop0 = (__shfl_sync(FULL, err0, 0) & (ERR_TIMEOUT | ERR_BADARG)) != 0;
 
+    // tickets requested at the end of the previous iteration (the atomic's
+    // round trip overlaps that iteration's endpoint writes and flushes); in
+    // the common-run build only, whose registers have room for it
+    constexpr bool kPrefetch = MP == 2;
+    unsigned pre_m = 0u;
+    unsigned long long pre_base = 0ull;
     for (; !stop0;) {
+        if (kPrefetch && pre_m) {
+            const int leader = __ffs(pre_m) - 1;
+            const unsigned long long base = __shfl_sync(FULL, pre_base, leader);
+            if ((pre_m >> lane) & 1u) ticket = (long long)(base + __popc(pre_m & lanemask_lt()));
+            pre_m = 0u;
+        }
         // lanes without an electron take queue tickets: one atomic per warp
         const bool need = !has && ticket < 0;
         const unsigned m = __ballot_sync(FULL, need);
@@ -304,6 +316,12 @@ __global__ void __launch_bounds__(MAXT) k_batched(const RunParams p)
                     has = false;
                     fin = true;
                 }
+            }
+            // the lanes that will need an electron ask for tickets now
+            if constexpr (kPrefetch) {
+                pre_m = __ballot_sync(FULL, !has && ticket < 0);
+                if (pre_m && lane == __ffs(pre_m) - 1)
+                    pre_base = atomicAdd(&p.hdr->head, (unsigned long long)__popc(pre_m));
             }
             if (fin) {
                 finish<GEO>(p, tb, e, bs);
