@@ -210,8 +210,9 @@ __global__ void __launch_bounds__(MAXT) k_batched(const RunParams p)
 
     // tickets requested at the end of the previous iteration (the atomic's
     // round trip overlaps that iteration's endpoint writes and flushes); in
-    // the common-run build only, whose registers have room for it
-    constexpr bool kPrefetch = MP == 2;
+    // the common-run builds without sub-steps, crossings or signals, whose
+    // registers have room for it
+    constexpr bool kPrefetch = MP == 2 && !GEO;
     unsigned pre_m = 0u;
     unsigned long long pre_base = 0ull;
     for (; !stop0;) {

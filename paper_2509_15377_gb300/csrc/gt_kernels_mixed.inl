@@ -33,7 +33,8 @@ static bool common_run(const RunParams &p)
 template <int FK, bool TAB, int MAXT, bool PHYS, bool GEO>
 static cudaError_t batched_t(const RunParams &p, int grid, int block, size_t smem, cudaStream_t s)
 {
-    if constexpr (!PHYS && !GEO) {
+    // built for every field in the basic variant, for the plate field in the others
+    if constexpr ((!PHYS && !GEO) || FK == GT_FIELD_PLATE) {
         if (common_run(p)) {
             k_batched<MixedElectron, FK, TAB, MAXT, 2, PHYS, GEO><<<grid, block, smem, s>>>(p);
             return cudaGetLastError();
@@ -130,7 +131,7 @@ static cudaError_t configure_one(size_t max_smem)
     cudaError_t e;
     if ((e = configure_mp<FK, TAB, 0, PHYS, GEO>(max_smem)) != cudaSuccess) return e;
     if ((e = configure_mp<FK, TAB, 1, PHYS, GEO>(max_smem)) != cudaSuccess) return e;
-    if constexpr (!PHYS && !GEO) {
+    if constexpr ((!PHYS && !GEO) || FK == GT_FIELD_PLATE) {
         if ((e = configure_mp<FK, TAB, 2, PHYS, GEO>(max_smem)) != cudaSuccess) return e;
     }
     return allow_dynamic_smem(k_plain_transport<MixedElectron, FK, TAB, kPlainThreadsMixed, PHYS, GEO>,
