@@ -53,7 +53,7 @@ WORKLOAD = "plate_batched_4096"
 #   level choice, tally, isotropic direction and speed), counted from its
 #   arithmetic, one lane instruction per operation; what the kernel issues
 #   beyond it (spill code, addressing, control, FP64 folds) is overhead.
-LANE_INST_PER_FLIGHT_BY_BLOCK = {768: 323.3, 896: 317.8, 1024: 322.5}
+LANE_INST_PER_FLIGHT_BY_BLOCK = {768: 321.2, 896: 323.2, 1024: 313.5}
 ALGORITHMIC_LANE_INST_PER_FLIGHT = 190.0
 # The same calibration for the field-map line on the 256^3 grid (`bench.py
 # --calibrate --calibrate-field grid --block B --refill-period 16
@@ -84,11 +84,11 @@ SM_COUNT = 152
 ISSUE_PER_SM_PER_CLK = 4       # warp schedulers per SM, one instruction each per clock
 LANES_PER_WARP = 32
 # DRAM bytes per electron of the batched kernel (ncu dram__bytes_read.sum +
-# dram__bytes_write.sum on the 256-avalanche case at 1024 threads: 131.8 MB +
-# 320.5 MB for 2,005,010 electrons; traffic grows with electrons, so it is
+# dram__bytes_write.sum on the 256-avalanche case at 1024 threads: 139.5 MB +
+# 321.1 MB for 2,005,010 electrons; traffic grows with electrons, so it is
 # scaled to a launch by the electrons the launch stores).  Set back to None
 # when the kernel changes, until the next capture.
-DRAM_BYTES_PER_ELECTRON = 225.6
+DRAM_BYTES_PER_ELECTRON = 229.7
 # Bytes per electron that the batched transport kernel must move by its
 # data layout: at birth the start record (x0 y0 z0 t0 e0, 40 B), id (8),
 # avalanche (4), birth velocity (24), birth element (4) and ready flag (4)

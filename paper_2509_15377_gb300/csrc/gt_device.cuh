@@ -1319,6 +1319,7 @@ struct Fp64Electron {
 
     template <int FK>
     __device__ __forceinline__ void round_end(const RunParams &) {}
+    __device__ __forceinline__ uint32_t level0_count() const { return 0u; }
     __device__ __forceinline__ int birth_elem() const { return -1; }
 
     __device__ void write_end(const RunParams &p) const
@@ -1393,7 +1394,7 @@ struct MixedElectron {
     };
     struct Pending {
         float R;          // u1 * majorant
-        float eps, f;     // energy at the collision, fraction within table interval k
+        float f;          // fraction within table interval k
         int k;
         uint32_t w2, w3;  // direction words
         bool real;
@@ -1410,6 +1411,7 @@ struct MixedElectron {
     float zhi, zlo, tlim;    // pre-test limits for the offsets (see flush)
     float plate_e;
     uint32_t nf, nreal, nnull;
+    uint32_t n0;             // real collisions of the straight-line elastic path (level 0)
     int status;
     int aval;
     bool timed;
@@ -1559,7 +1561,7 @@ struct MixedElectron {
         uid = p.uid[s];
         aval = p.aval[s];
         plate_e = (float)(p.aval_field ? p.aval_field[aval] : p.field.e0);
-        nf = nreal = nnull = 0;
+        nf = nreal = nnull = n0 = 0;
         status = 0;
         timed = false;
         elem = FK == GT_FIELD_MESH ? p.belem[s] : -1;
@@ -1797,7 +1799,6 @@ struct MixedElectron {
         const bool real = !pseudo && R < top;
         pd.real = real;
         pd.R = R;
-        pd.eps = eps;
         pd.k = k;
         pd.f = f;
         pd.w2 = w.z;
@@ -1816,7 +1817,6 @@ struct MixedElectron {
                                            ChildT &ch)
     {
         pd.real = false;
-        const float eps = pd.eps;
         const float *c0 = tb.cum32 + pd.k * tb.stride32;
         // most real collisions are elastic (level 0 when it is the elastic
         // level): when every colliding lane's R lies below the level-0 sum,
@@ -1826,7 +1826,7 @@ struct MixedElectron {
         if (lvl0 && !(PHYS && p.gas.any_aniso)) {
             // the common case as straight-line code: every colliding lane of
             // the warp scatters elastically and isotropically on level 0
-            tb.tally[threadIdx.x] += 1u;
+            ++n0;
             float nx, ny, nz;
             isotropic32(u01f(pd.w2), u01f(pd.w3), nx, ny, nz);
             const float sp = elastic_speed32(vx, vy, vz, nx, ny, nz, false, 0.0f,
@@ -1839,6 +1839,8 @@ struct MixedElectron {
             }
             return EV_NONE;
         }
+        // the energy at the collision (the velocity has not changed since the flight)
+        const float eps = (vx * vx + vy * vy + vz * vz) * kInvTwoAccelF;
         const int lvl = lvl0 ? 0 : select_below_total32(c0, tb.stride32, p.gas.n_levels, pd.f, pd.R);
         const int type = tb.type[lvl];
         if (type != GT_LEVEL_ELASTIC) {
@@ -1908,6 +1910,7 @@ struct MixedElectron {
         flush<FK>(p);
     }
     __device__ __forceinline__ int birth_elem() const { return elem; }
+    __device__ __forceinline__ uint32_t level0_count() const { return n0; }
 
     __device__ void write_end(const RunParams &p) const
     {
@@ -1936,7 +1939,7 @@ struct MixedElectron {
         nf = s.nf[i]; nreal = s.nreal[i]; uid = s.uid[i]; slot = s.slot[i];
         aval = av;
         plate_e = (float)(p.aval_field ? p.aval_field[aval] : p.field.e0);
-        nnull = 0;
+        nnull = n0 = 0;
         status = 0;
         timed = false;
         elem = -1;

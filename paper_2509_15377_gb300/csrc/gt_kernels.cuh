@@ -123,11 +123,14 @@ __device__ __forceinline__ void flush_block_stats(const RunParams &p, BlockState
 // Move an electron's per-level collision counts from shared memory to the
 // avalanche's tallies; returns the number of real collisions moved.
 __device__ __forceinline__ unsigned long long flush_tally(const RunParams &p, const Tables &tb,
-                                                          int aval, uint32_t nnull)
+                                                          int aval, uint32_t nnull,
+                                                          uint32_t n0 = 0u)
 {
     const int L = p.gas.n_levels;
     uint64_t *tal = p.tallies + (int64_t)aval * (L + 1);
     unsigned long long real = 0;
+    // level 0's collisions counted in a register (the straight-line path)
+    tb.tally[threadIdx.x] += n0;
     for (int j = 0; j < L; ++j) {
         uint32_t &c = tb.tally[j * blockDim.x + threadIdx.x];
         if (c) {
@@ -147,7 +150,7 @@ __device__ __forceinline__ void finish(const RunParams &p, const Tables &tb, con
 {
     if (GEO) e.signal_end(p);  // induced signals are built only into GEO kernels
     e.write_end(p);
-    const unsigned long long real = flush_tally(p, tb, e.aval, e.nnull);
+    const unsigned long long real = flush_tally(p, tb, e.aval, e.nnull, e.level0_count());
     atomicAdd(&bs.flights, (unsigned long long)e.nf);
     atomicAdd(&bs.real, real);
     atomicAdd(&bs.nul, (unsigned long long)e.nnull);
@@ -415,7 +418,7 @@ __global__ void __launch_bounds__(MAXT)
         }
     }
     // per-level counts of this stretch go to the avalanche's tallies
-    flush_tally(p, tb, aval, e.nnull);
+    flush_tally(p, tb, aval, e.nnull, e.level0_count());
     atomicAdd(&p.hdr->flights, (unsigned long long)(e.nf - nf0));
     atomicAdd(&p.hdr->real, (unsigned long long)(e.nreal - nr0));
     atomicAdd(&p.hdr->nul, (unsigned long long)e.nnull);
