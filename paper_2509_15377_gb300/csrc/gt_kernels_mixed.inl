@@ -93,20 +93,37 @@ static cudaError_t plain_fk(const RunParams &p, const PlainArgs &a, int block, s
     }
 }
 
+// Entry points per table placement (TAB: the FP32 table in shared memory),
+// so that a variant's kernels can be split over two translation units by
+// TAB and compiled in parallel (the GEO variant is).
+template <bool TAB, bool PHYS, bool GEO>
+cudaError_t launch_batched_mixed_tab(const RunParams &p, int grid, int block, size_t smem,
+                                     cudaStream_t s)
+{
+    return batched_fk<TAB, PHYS, GEO>(p, grid, block, smem, s);
+}
+
+template <bool TAB, bool PHYS, bool GEO>
+cudaError_t launch_plain_mixed_tab(const RunParams &p, const PlainArgs &a, int block, size_t smem,
+                                   cudaStream_t s)
+{
+    return plain_fk<TAB, PHYS, GEO>(p, a, block, smem, s);
+}
+
 template <bool PHYS, bool GEO>
 cudaError_t launch_batched_mixed_t(const RunParams &p, bool smem_table, int grid, int block,
                                    size_t smem, cudaStream_t s)
 {
-    return smem_table ? batched_fk<true, PHYS, GEO>(p, grid, block, smem, s)
-                      : batched_fk<false, PHYS, GEO>(p, grid, block, smem, s);
+    return smem_table ? launch_batched_mixed_tab<true, PHYS, GEO>(p, grid, block, smem, s)
+                      : launch_batched_mixed_tab<false, PHYS, GEO>(p, grid, block, smem, s);
 }
 
 template <bool PHYS, bool GEO>
 cudaError_t launch_plain_mixed_t(const RunParams &p, const PlainArgs &a, bool smem_table,
                                  int block, size_t smem, cudaStream_t s)
 {
-    return smem_table ? plain_fk<true, PHYS, GEO>(p, a, block, smem, s)
-                      : plain_fk<false, PHYS, GEO>(p, a, block, smem, s);
+    return smem_table ? launch_plain_mixed_tab<true, PHYS, GEO>(p, a, block, smem, s)
+                      : launch_plain_mixed_tab<false, PHYS, GEO>(p, a, block, smem, s);
 }
 
 template <int FK, bool TAB, int MP, bool PHYS, bool GEO>
@@ -149,12 +166,18 @@ static cudaError_t configure_tab(size_t max_smem)
     return configure_one<GT_FIELD_GRID, TAB, PHYS, GEO>(max_smem);
 }
 
+template <bool TAB, bool PHYS, bool GEO>
+cudaError_t configure_mixed_tab(size_t max_smem)
+{
+    return configure_tab<TAB, PHYS, GEO>(max_smem);
+}
+
 template <bool PHYS, bool GEO>
 cudaError_t configure_mixed_t(size_t max_smem)
 {
-    cudaError_t e = configure_tab<true, PHYS, GEO>(max_smem);
+    cudaError_t e = configure_mixed_tab<true, PHYS, GEO>(max_smem);
     if (e != cudaSuccess) return e;
-    return configure_tab<false, PHYS, GEO>(max_smem);
+    return configure_mixed_tab<false, PHYS, GEO>(max_smem);
 }
 
 template <int FK, bool TAB, bool PHYS, bool GEO>
@@ -189,11 +212,17 @@ static int occ_fk(int field_kind, int block, size_t smem)
     }
 }
 
+template <bool TAB, bool PHYS, bool GEO>
+int occupancy_batched_mixed_tab(int field_kind, int block, size_t smem)
+{
+    return occ_fk<TAB, PHYS, GEO>(field_kind, block, smem);
+}
+
 template <bool PHYS, bool GEO>
 int occupancy_batched_mixed_t(int field_kind, bool smem_table, int block, size_t smem)
 {
-    return smem_table ? occ_fk<true, PHYS, GEO>(field_kind, block, smem)
-                      : occ_fk<false, PHYS, GEO>(field_kind, block, smem);
+    return smem_table ? occupancy_batched_mixed_tab<true, PHYS, GEO>(field_kind, block, smem)
+                      : occupancy_batched_mixed_tab<false, PHYS, GEO>(field_kind, block, smem);
 }
 
 }  // namespace gt
