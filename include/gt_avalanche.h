@@ -201,9 +201,10 @@ typedef struct {
     int32_t majorant;                 /* GT_MAJORANT_GLOBAL / GT_MAJORANT_BANDED */
     int32_t aval_base;                /* >= 0: number of this run's avalanche 0 in a
                                          larger workload.  Avalanches are independent
-                                         (Sec. 2), and the random streams are keyed
+                                         (Sec. 2), and the random streams are chosen
                                          by the workload's avalanche number
-                                         aval[i] + aval_base, so a run of avalanches
+                                         aval[i] + aval_base (it enters the Philox
+                                         counter), so a run of avalanches
                                          [a0, a1) of a workload with aval_base = a0
                                          (and the workload's electron ids) transports
                                          exactly those avalanches of the whole run:
