@@ -533,6 +533,8 @@ def run_ours(args) -> None:
         # the basic gas with the anode's induced signal, 2000 bins of 50 ps
         s_opt = dataclasses.replace(opt, signal_kind=W.W_PLATE, signal_bins=2000,
                                     signal_t0=0.0, signal_dt=0.05)
+        if not args.no_autotune:  # a kernel build of its own (crossings alone have another)
+            av.autotune(tune_sample, s_opt, cap, stream=stream)
         physical["signal"], _ = timed_runs(s_opt, prim_dev)
         physical["signal"]["note"] = ("basic gas, Shockley-Ramo anode signal per avalanche, "
                                       "2000 bins x 0.05 ns")

@@ -1658,22 +1658,25 @@ struct MixedElectron {
     // start of each), with the first boundary crossing located in FP64
     // (crossing64) when p.crossing is set.  Returns the boundary status; on
     // a crossing the FP64 base moves to the crossing point and time.
-    template <int FK>
+    template <int FK, bool XONLY = false>
     __device__ int fly_steps(const RunParams &p, float dt, float ex, float ey, float ez)
     {
-        const bool sig = p.signal_bins != 0;
-        const int ns = p.substeps > 1 ? p.substeps : 1;
+        // XONLY: exact crossings in a run without B, sub-steps or signals,
+        // known at compile time
+        const bool sig = !XONLY && p.signal_bins != 0;
+        const int ns = XONLY ? 1 : (p.substeps > 1 ? p.substeps : 1);
+        const bool zonly = XONLY && (FK == GT_FIELD_PLATE || FK == GT_FIELD_UNIFORM);
         const float h = ns > 1 ? dt / (float)ns : dt;
         const unsigned S = blockDim.x;
         for (int sub = 0; sub < ns; ++sub) {
             if (sub > 0) efield<FK>(p, ex, ey, ez);
             const float ax = -kAccelF * ex, ay = -kAccelF * ey, az = -kAccelF * ez;
             const float sox = ox, soy = oy, soz = oz, sot = ot, svx = vx, svy = vy, svz = vz;
-            move(p, ax, ay, az, h);
+            move(p, ax, ay, az, h, XONLY, zonly);
             ot += h;
             int st = boundary<FK>(p);
             float tc = h;
-            if (FK == GT_FIELD_PLATE && p.crossing && !p.field.has_b && az != 0.0f) {
+            if (FK == GT_FIELD_PLATE && (XONLY || (p.crossing && !p.field.has_b)) && az != 0.0f) {
                 // a sub-step that leaves the gap and returns: the vertex of z(t)
                 const float tv = -svz / az;
                 if (tv > 0.0f && tv < h) {
@@ -1689,7 +1692,7 @@ struct MixedElectron {
                     }
                 }
             }
-            if (p.crossing && st) {
+            if ((XONLY || p.crossing) && st) {
                 // first crossing within (0, tc], by bisection on the FP32
                 // motion of the offsets (2^-32 of tc: below FP32 resolution);
                 // the point found is on the surface to FP32 rounding
@@ -1699,7 +1702,7 @@ struct MixedElectron {
                 for (int it = 0; it < 32; ++it) {
                     const float mid = 0.5f * (lo + hi);
                     ox = sox; oy = soy; oz = soz; vx = svx; vy = svy; vz = svz;
-                    move(p, ax, ay, az, mid);
+                    move(p, ax, ay, az, mid, XONLY, zonly);
                     if (outside32<FK>(p.field, zg, zc, px + ox, py + oy,
                                       FK == GT_FIELD_PLATE ? oz : pz + oz))
                         hi = mid;
@@ -1707,7 +1710,7 @@ struct MixedElectron {
                         lo = mid;
                 }
                 ox = sox; oy = soy; oz = soz; vx = svx; vy = svy; vz = svz;
-                move(p, ax, ay, az, hi);
+                move(p, ax, ay, az, hi, XONLY, zonly);
                 ot = sot + hi;
                 timed = false;  // the electron left before the time limit
                 if (sig && ot >= sg_toff)
@@ -1731,7 +1734,8 @@ struct MixedElectron {
     // MAJ = 1 builds the step for runs with the banded majorant, band bounds
     // that rise with energy, an elastic level 0, no magnetic field and the
     // field held over the flight (the common case), without the run-time
-    // tests of the others.
+    // tests of the others; MAJ = 2 the same with exact crossings and neither
+    // sub-steps nor signals.
     template <int FK, bool GEO, int MAJ = 0>
     __device__ __forceinline__ int advance(const RunParams &p, const Tables &tb, Pending &pd)
     {
@@ -1746,13 +1750,13 @@ struct MixedElectron {
         const float ax = -kAccelF * ex, ay = -kAccelF * ey, az = -kAccelF * ez;
         float nu = p.gas.nu_max_f, dt;
         bool pseudo = false;
-        if (MAJ == 1 || p.majorant == GT_MAJORANT_BANDED) {
+        if (MAJ >= 1 || p.majorant == GT_MAJORANT_BANDED) {
             // the rate bound over the energies reachable within the window
-            const bool mono = MAJ == 1 || p.gas.bands_monotone;
+            const bool mono = MAJ >= 1 || p.gas.bands_monotone;
             const float eps0 = (vx * vx + vy * vy + vz * vz) * kInvTwoAccelF;
             const float tau = __fdividef(p.window_f, tb.band32[band_index32(p.gas, eps0)]);
             float lo, hi;
-            reach32<FK>(MAJ == 1 ? 0 : p.field.has_b, MAJ == 1 ? 0.0f : p.field_emax_f, eps0, vx,
+            reach32<FK>(MAJ >= 1 ? 0 : p.field.has_b, MAJ >= 1 ? 0.0f : p.field_emax_f, eps0, vx,
                         vy, vz, ex, ey, ez, plate_e, tau, lo, hi, !mono);
             nu = mono
                      ? tb.band32[band_index32(p.gas, hi)]
@@ -1772,10 +1776,10 @@ struct MixedElectron {
             timed = c.y != 0.0f;
         }
         int st;
-        if (GEO && (p.substeps > 1 || p.crossing || p.signal_bins)) {
-            st = fly_steps<FK>(p, dt, ex, ey, ez);
+        if (GEO && (MAJ == 2 || p.substeps > 1 || p.crossing || p.signal_bins)) {
+            st = fly_steps<FK, MAJ == 2>(p, dt, ex, ey, ez);
         } else {
-            move(p, ax, ay, az, dt, MAJ == 1, FK == GT_FIELD_PLATE || FK == GT_FIELD_UNIFORM);
+            move(p, ax, ay, az, dt, MAJ >= 1, FK == GT_FIELD_PLATE || FK == GT_FIELD_UNIFORM);
             ot += dt;
             st = boundary<FK>(p);
         }
@@ -1821,7 +1825,7 @@ struct MixedElectron {
         // most real collisions are elastic (level 0 when it is the elastic
         // level): when every colliding lane's R lies below the level-0 sum,
         // the warp skips the search
-        const bool lvl0 = (MAJ == 1 || p.gas.level0_elastic) &&
+        const bool lvl0 = (MAJ >= 1 || p.gas.level0_elastic) &&
                           __all_sync(__activemask(), pd.R < fmaf(pd.f, c0[tb.stride32] - c0[0], c0[0]));
         if (lvl0 && !(PHYS && p.gas.any_aniso)) {
             // the common case as straight-line code: every colliding lane of

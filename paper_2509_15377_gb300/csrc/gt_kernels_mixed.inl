@@ -30,9 +30,22 @@ static bool common_run(const RunParams &p)
            p.field_emax_f == 0.0f;
 }
 
+// The common run with exact crossings and neither sub-steps nor signals
+// (MP = 3, the plate field in the GEO variant).
+static bool crossing_only_run(const RunParams &p)
+{
+    return common_run(p) && p.crossing && p.substeps <= 1 && !p.signal_bins;
+}
+
 template <int FK, bool TAB, int MAXT, bool PHYS, bool GEO>
 static cudaError_t batched_t(const RunParams &p, int grid, int block, size_t smem, cudaStream_t s)
 {
+    if constexpr (GEO && FK == GT_FIELD_PLATE) {
+        if (crossing_only_run(p)) {
+            k_batched<MixedElectron, FK, TAB, MAXT, 3, PHYS, GEO><<<grid, block, smem, s>>>(p);
+            return cudaGetLastError();
+        }
+    }
     // built for every field in the basic variant, for the plate field in the others
     if constexpr ((!PHYS && !GEO) || FK == GT_FIELD_PLATE) {
         if (common_run(p)) {
@@ -150,6 +163,9 @@ static cudaError_t configure_one(size_t max_smem)
     if ((e = configure_mp<FK, TAB, 1, PHYS, GEO>(max_smem)) != cudaSuccess) return e;
     if constexpr ((!PHYS && !GEO) || FK == GT_FIELD_PLATE) {
         if ((e = configure_mp<FK, TAB, 2, PHYS, GEO>(max_smem)) != cudaSuccess) return e;
+    }
+    if constexpr (GEO && FK == GT_FIELD_PLATE) {
+        if ((e = configure_mp<FK, TAB, 3, PHYS, GEO>(max_smem)) != cudaSuccess) return e;
     }
     return allow_dynamic_smem(k_plain_transport<MixedElectron, FK, TAB, kPlainThreadsMixed, PHYS, GEO>,
                               max_smem);
