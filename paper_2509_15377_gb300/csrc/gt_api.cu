@@ -37,10 +37,10 @@ struct gt_ctx {
     // autotuned batched launch shape per [precision][field kind] (0 = none)
     // autotuned launch shapes per [precision][field kind][majorant]
     // [precision][field kind][majorant][kernel build: basic, general gas,
-    // sub-steps/crossings/signals, crossings alone]
-    int tuned_block[2][5][2][4] = {};
-    int tuned_k[2][5][2][4] = {};
-    int tuned_m[2][5][2][4] = {};
+    // sub-steps/crossings/signals, crossings alone, signals alone]
+    int tuned_block[2][5][2][5] = {};
+    int tuned_k[2][5][2][5] = {};
+    int tuned_m[2][5][2][5] = {};
     // MESH field: element records and search bins (device, owned)
     float *d_tet32 = nullptr;
     double *d_tet64 = nullptr;
@@ -169,7 +169,9 @@ int default_block(int precision) { return precision == GT_FP64 ? 256 : 512; }
 int run_variant(const gt_ctx *ctx, const gt_run *r)
 {
     const bool signal = r->signal_kind != GT_W_NONE && r->signal_bins > 0;
-    if (r->crossing && r->substeps <= 1 && !signal) return 3;  // a build of its own (mixed)
+    // crossings alone and signals alone have builds of their own (mixed)
+    if (r->crossing && r->substeps <= 1 && !signal) return 3;
+    if (signal && r->substeps <= 1 && !r->crossing) return 4;
     if (r->substeps > 1 || r->crossing || signal) return 2;
     return ctx->gas.any_special ? 1 : 0;
 }

@@ -1658,25 +1658,27 @@ struct MixedElectron {
     // start of each), with the first boundary crossing located in FP64
     // (crossing64) when p.crossing is set.  Returns the boundary status; on
     // a crossing the FP64 base moves to the crossing point and time.
-    template <int FK, bool XONLY = false>
+    template <int FK, int MODE = 0>
     __device__ int fly_steps(const RunParams &p, float dt, float ex, float ey, float ez)
     {
-        // XONLY: exact crossings in a run without B, sub-steps or signals,
-        // known at compile time
-        const bool sig = !XONLY && p.signal_bins != 0;
-        const int ns = XONLY ? 1 : (p.substeps > 1 ? p.substeps : 1);
-        const bool zonly = XONLY && (FK == GT_FIELD_PLATE || FK == GT_FIELD_UNIFORM);
+        // MODE 2: exact crossings, MODE 3: induced signals, each alone in a
+        // run without B or sub-steps, known at compile time; MODE 0: any run
+        constexpr bool XONLY = MODE == 2, SONLY = MODE == 3, ONE = XONLY || SONLY;
+        const bool sig = SONLY || (!XONLY && p.signal_bins != 0);
+        const bool cross = XONLY || (!SONLY && p.crossing != 0);
+        const int ns = ONE ? 1 : (p.substeps > 1 ? p.substeps : 1);
+        const bool zonly = ONE && (FK == GT_FIELD_PLATE || FK == GT_FIELD_UNIFORM);
         const float h = ns > 1 ? dt / (float)ns : dt;
         const unsigned S = blockDim.x;
         for (int sub = 0; sub < ns; ++sub) {
             if (sub > 0) efield<FK>(p, ex, ey, ez);
             const float ax = -kAccelF * ex, ay = -kAccelF * ey, az = -kAccelF * ez;
             const float sox = ox, soy = oy, soz = oz, sot = ot, svx = vx, svy = vy, svz = vz;
-            move(p, ax, ay, az, h, XONLY, zonly);
+            move(p, ax, ay, az, h, ONE, zonly);
             ot += h;
             int st = boundary<FK>(p);
             float tc = h;
-            if (FK == GT_FIELD_PLATE && (XONLY || (p.crossing && !p.field.has_b)) && az != 0.0f) {
+            if (FK == GT_FIELD_PLATE && cross && (ONE || !p.field.has_b) && az != 0.0f) {
                 // a sub-step that leaves the gap and returns: the vertex of z(t)
                 const float tv = -svz / az;
                 if (tv > 0.0f && tv < h) {
@@ -1692,7 +1694,7 @@ struct MixedElectron {
                     }
                 }
             }
-            if ((XONLY || p.crossing) && st) {
+            if (cross && st) {
                 // first crossing within (0, tc], by bisection on the FP32
                 // motion of the offsets (2^-32 of tc: below FP32 resolution);
                 // the point found is on the surface to FP32 rounding
@@ -1702,7 +1704,7 @@ struct MixedElectron {
                 for (int it = 0; it < 32; ++it) {
                     const float mid = 0.5f * (lo + hi);
                     ox = sox; oy = soy; oz = soz; vx = svx; vy = svy; vz = svz;
-                    move(p, ax, ay, az, mid, XONLY, zonly);
+                    move(p, ax, ay, az, mid, ONE, zonly);
                     if (outside32<FK>(p.field, zg, zc, px + ox, py + oy,
                                       FK == GT_FIELD_PLATE ? oz : pz + oz))
                         hi = mid;
@@ -1710,7 +1712,7 @@ struct MixedElectron {
                         lo = mid;
                 }
                 ox = sox; oy = soy; oz = soz; vx = svx; vy = svy; vz = svz;
-                move(p, ax, ay, az, hi, XONLY, zonly);
+                move(p, ax, ay, az, hi, ONE, zonly);
                 ot = sot + hi;
                 timed = false;  // the electron left before the time limit
                 if (sig && ot >= sg_toff)
@@ -1735,7 +1737,8 @@ struct MixedElectron {
     // that rise with energy, an elastic level 0, no magnetic field and the
     // field held over the flight (the common case), without the run-time
     // tests of the others; MAJ = 2 the same with exact crossings and neither
-    // sub-steps nor signals.
+    // sub-steps nor signals; MAJ = 3 with induced signals and neither
+    // sub-steps nor crossings.
     template <int FK, bool GEO, int MAJ = 0>
     __device__ __forceinline__ int advance(const RunParams &p, const Tables &tb, Pending &pd)
     {
@@ -1776,8 +1779,8 @@ struct MixedElectron {
             timed = c.y != 0.0f;
         }
         int st;
-        if (GEO && (MAJ == 2 || p.substeps > 1 || p.crossing || p.signal_bins)) {
-            st = fly_steps<FK, MAJ == 2>(p, dt, ex, ey, ez);
+        if (GEO && (MAJ >= 2 || p.substeps > 1 || p.crossing || p.signal_bins)) {
+            st = fly_steps<FK, MAJ>(p, dt, ex, ey, ez);
         } else {
             move(p, ax, ay, az, dt, MAJ >= 1, FK == GT_FIELD_PLATE || FK == GT_FIELD_UNIFORM);
             ot += dt;

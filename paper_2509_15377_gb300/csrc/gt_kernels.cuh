@@ -291,8 +291,8 @@ __global__ void __launch_bounds__(MAXT) k_batched(const RunParams p)
             // real one; then the warp applies its lanes' collisions together.
             // MP = 1 builds the one-flight round (M = 1) at compile time.
             // MP = 2: one flight per round and the step built for the common
-            // run (MixedElectron::advance with MAJ = 1); MP = 3: the same with
-            // exact crossings only (MAJ = 2)
+            // run (MixedElectron::advance with MAJ = 1); MP = 3 / 4: the same
+            // with exact crossings / induced signals alone (MAJ = 2 / 3)
             constexpr int MPF = MP >= 2 ? 1 : MP;
             constexpr int MAJ = MP >= 2 ? MP - 1 : 0;
             const int M = MPF ? MPF : p.flights_per_phase;

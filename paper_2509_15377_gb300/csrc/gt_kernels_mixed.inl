@@ -37,12 +37,23 @@ static bool crossing_only_run(const RunParams &p)
     return common_run(p) && p.crossing && p.substeps <= 1 && !p.signal_bins;
 }
 
+// The common run with induced signals and neither sub-steps nor crossings
+// (MP = 4, the plate field in the GEO variant).
+static bool signal_only_run(const RunParams &p)
+{
+    return common_run(p) && p.signal_bins > 0 && !p.crossing && p.substeps <= 1;
+}
+
 template <int FK, bool TAB, int MAXT, bool PHYS, bool GEO>
 static cudaError_t batched_t(const RunParams &p, int grid, int block, size_t smem, cudaStream_t s)
 {
     if constexpr (GEO && FK == GT_FIELD_PLATE) {
         if (crossing_only_run(p)) {
             k_batched<MixedElectron, FK, TAB, MAXT, 3, PHYS, GEO><<<grid, block, smem, s>>>(p);
+            return cudaGetLastError();
+        }
+        if (signal_only_run(p)) {
+            k_batched<MixedElectron, FK, TAB, MAXT, 4, PHYS, GEO><<<grid, block, smem, s>>>(p);
             return cudaGetLastError();
         }
     }
@@ -166,6 +177,7 @@ static cudaError_t configure_one(size_t max_smem)
     }
     if constexpr (GEO && FK == GT_FIELD_PLATE) {
         if ((e = configure_mp<FK, TAB, 3, PHYS, GEO>(max_smem)) != cudaSuccess) return e;
+        if ((e = configure_mp<FK, TAB, 4, PHYS, GEO>(max_smem)) != cudaSuccess) return e;
     }
     return allow_dynamic_smem(k_plain_transport<MixedElectron, FK, TAB, kPlainThreadsMixed, PHYS, GEO>,
                               max_smem);
