@@ -59,7 +59,7 @@ ALGORITHMIC_LANE_INST_PER_FLIGHT = 190.0
 # --calibrate --calibrate-field grid --block B --refill-period 16
 # --flights-per-phase 1`: straight-line flights at r = 1 mm in the map, the
 # step plus eight float4 gathers and the trilinear interpolation per flight).
-GRID_LANE_INST_PER_FLIGHT_BY_BLOCK = {512: 439.4, 768: 457.1, 1024: 455.7}
+GRID_LANE_INST_PER_FLIGHT_BY_BLOCK = {512: 419.7, 768: 442.3, 1024: 414.1}
 
 
 def lane_inst_per_flight(block: int, table=None) -> float:

@@ -524,18 +524,23 @@ __device__ __forceinline__ void field32(const DevField &f, float plate_e, float 
         const float4 c010 = __ldg(b + sy), c110 = __ldg(b + sy + 1);
         const float4 c001 = __ldg(b + sz), c101 = __ldg(b + sz + 1);
         const float4 c011 = __ldg(b + sz + sy), c111 = __ldg(b + sz + sy + 1);
-        // interpolate along x, then y, then z
+        // interpolate along x, then y, then z: Ex and Ey together in paired
+        // FP32 instructions (FFMA2, sm_100 and later: each half rounds as
+        // fmaf), Ez alone; b - a as fma(a, -1, b), the same rounding as a
+        // subtraction
         auto lerp = [](float a, float b, float t) { return fmaf(t, b - a, a); };
-        float e[3];
-        const float *p000 = &c000.x, *p100 = &c100.x, *p010 = &c010.x, *p110 = &c110.x;
-        const float *p001 = &c001.x, *p101 = &c101.x, *p011 = &c011.x, *p111 = &c111.x;
-#pragma unroll
-        for (int d = 0; d < 3; ++d) {
-            const float a00 = lerp(p000[d], p100[d], wx), a10 = lerp(p010[d], p110[d], wx);
-            const float a01 = lerp(p001[d], p101[d], wx), a11 = lerp(p011[d], p111[d], wx);
-            e[d] = lerp(lerp(a00, a10, wy), lerp(a01, a11, wy), wz);
-        }
-        ex = e[0]; ey = e[1]; ez = e[2];
+        auto lerp2 = [](float2 a, float2 b, float2 t) {
+            return __ffma2_rn(t, __ffma2_rn(a, make_float2(-1.0f, -1.0f), b), a);
+        };
+        auto xy = [](const float4 &c) { return make_float2(c.x, c.y); };
+        const float2 tx = make_float2(wx, wx), ty = make_float2(wy, wy), tz = make_float2(wz, wz);
+        const float2 a00 = lerp2(xy(c000), xy(c100), tx), a10 = lerp2(xy(c010), xy(c110), tx);
+        const float2 a01 = lerp2(xy(c001), xy(c101), tx), a11 = lerp2(xy(c011), xy(c111), tx);
+        const float2 exy = lerp2(lerp2(a00, a10, ty), lerp2(a01, a11, ty), tz);
+        const float z00 = lerp(c000.z, c100.z, wx), z10 = lerp(c010.z, c110.z, wx);
+        const float z01 = lerp(c001.z, c101.z, wx), z11 = lerp(c011.z, c111.z, wx);
+        ex = exy.x; ey = exy.y;
+        ez = lerp(lerp(z00, z10, wy), lerp(z01, z11, wy), wz);
     }
 }
 
