@@ -21,6 +21,13 @@ namespace gt {
 
 constexpr unsigned FULL = 0xFFFFFFFFu;
 
+// Builds of the batched kernel's collision round (its template parameter MP).
+constexpr int kRoundAny = 0;       // flights per round from the run (flights_per_phase)
+constexpr int kRoundOne = 1;       // one flight per round
+constexpr int kRoundCommon = 2;    // one flight per round, the step built for the common run
+constexpr int kRoundCrossing = 3;  // the same with exact crossings alone
+constexpr int kRoundSignal = 4;    // the same with induced signals alone
+
 // Row stride of the FP32 table staged in shared memory: odd, so that the
 // rows of a warp's random energies start on all 32 banks.
 __host__ __device__ inline int smem_stride(int n_levels) { return n_levels | 1; }
@@ -215,7 +222,7 @@ __global__ void __launch_bounds__(MAXT) k_batched(const RunParams p)
     // round trip overlaps that iteration's endpoint writes and flushes); in
     // the common-run builds without sub-steps, crossings or signals, whose
     // registers have room for it
-    constexpr bool kPrefetch = MP == 2 && !GEO;
+    constexpr bool kPrefetch = MP == kRoundCommon && !GEO;
     unsigned pre_m = 0u;
     unsigned long long pre_base = 0ull;
     for (; !stop0;) {
@@ -289,12 +296,13 @@ __global__ void __launch_bounds__(MAXT) k_batched(const RunParams p)
             // K collision rounds between refills.  In each, lanes without a
             // pending collision fly (at most M flights) until they meet a
             // real one; then the warp applies its lanes' collisions together.
-            // MP = 1 builds the one-flight round (M = 1) at compile time.
-            // MP = 2: one flight per round and the step built for the common
-            // run (MixedElectron::advance with MAJ = 1); MP = 3 / 4: the same
-            // with exact crossings / induced signals alone (MAJ = 2 / 3)
-            constexpr int MPF = MP >= 2 ? 1 : MP;
-            constexpr int MAJ = MP >= 2 ? MP - 1 : 0;
+            // kRoundOne builds the one-flight round (M = 1) at compile time;
+            // kRoundCommon, kRoundCrossing and kRoundSignal do too, with the
+            // step built for the common run (MixedElectron::advance with
+            // MAJ = 1), and with exact crossings / induced signals alone
+            // (MAJ = 2 / 3)
+            constexpr int MPF = MP >= kRoundCommon ? 1 : MP;
+            constexpr int MAJ = MP >= kRoundCommon ? MP - kRoundOne : 0;
             const int M = MPF ? MPF : p.flights_per_phase;
             // an electron that finishes during the rounds keeps its lane (a
             // lane takes a new electron only at the next refill) and is

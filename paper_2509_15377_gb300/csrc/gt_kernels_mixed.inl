@@ -20,7 +20,7 @@ namespace gt {
 constexpr int kMaxThreadsMixed = 1024;
 constexpr int kPlainThreadsMixed = 512;
 
-// The run the step has a build of its own for (MP = 2): one flight per
+// The run the step has a build of its own for (kRoundCommon): one flight per
 // round, the banded majorant with band bounds rising with energy, an
 // elastic level 0, no magnetic field, the field held over each flight.
 static bool common_run(const RunParams &p)
@@ -31,14 +31,14 @@ static bool common_run(const RunParams &p)
 }
 
 // The common run with exact crossings and neither sub-steps nor signals
-// (MP = 3, the plate field in the GEO variant).
+// (kRoundCrossing, the plate field in the GEO variant).
 static bool crossing_only_run(const RunParams &p)
 {
     return common_run(p) && p.crossing && p.substeps <= 1 && !p.signal_bins;
 }
 
 // The common run with induced signals and neither sub-steps nor crossings
-// (MP = 4, the plate field in the GEO variant).
+// (kRoundSignal, the plate field in the GEO variant).
 static bool signal_only_run(const RunParams &p)
 {
     return common_run(p) && p.signal_bins > 0 && !p.crossing && p.substeps <= 1;
@@ -49,25 +49,28 @@ static cudaError_t batched_t(const RunParams &p, int grid, int block, size_t sme
 {
     if constexpr (GEO && FK == GT_FIELD_PLATE) {
         if (crossing_only_run(p)) {
-            k_batched<MixedElectron, FK, TAB, MAXT, 3, PHYS, GEO><<<grid, block, smem, s>>>(p);
+            k_batched<MixedElectron, FK, TAB, MAXT, kRoundCrossing, PHYS, GEO>
+                <<<grid, block, smem, s>>>(p);
             return cudaGetLastError();
         }
         if (signal_only_run(p)) {
-            k_batched<MixedElectron, FK, TAB, MAXT, 4, PHYS, GEO><<<grid, block, smem, s>>>(p);
+            k_batched<MixedElectron, FK, TAB, MAXT, kRoundSignal, PHYS, GEO>
+                <<<grid, block, smem, s>>>(p);
             return cudaGetLastError();
         }
     }
     // built for every field in the basic variant, for the plate field in the others
     if constexpr ((!PHYS && !GEO) || FK == GT_FIELD_PLATE) {
         if (common_run(p)) {
-            k_batched<MixedElectron, FK, TAB, MAXT, 2, PHYS, GEO><<<grid, block, smem, s>>>(p);
+            k_batched<MixedElectron, FK, TAB, MAXT, kRoundCommon, PHYS, GEO>
+                <<<grid, block, smem, s>>>(p);
             return cudaGetLastError();
         }
     }
     if (p.flights_per_phase == 1)
-        k_batched<MixedElectron, FK, TAB, MAXT, 1, PHYS, GEO><<<grid, block, smem, s>>>(p);
+        k_batched<MixedElectron, FK, TAB, MAXT, kRoundOne, PHYS, GEO><<<grid, block, smem, s>>>(p);
     else
-        k_batched<MixedElectron, FK, TAB, MAXT, 0, PHYS, GEO><<<grid, block, smem, s>>>(p);
+        k_batched<MixedElectron, FK, TAB, MAXT, kRoundAny, PHYS, GEO><<<grid, block, smem, s>>>(p);
     return cudaGetLastError();
 }
 
@@ -170,14 +173,14 @@ template <int FK, bool TAB, bool PHYS, bool GEO>
 static cudaError_t configure_one(size_t max_smem)
 {
     cudaError_t e;
-    if ((e = configure_mp<FK, TAB, 0, PHYS, GEO>(max_smem)) != cudaSuccess) return e;
-    if ((e = configure_mp<FK, TAB, 1, PHYS, GEO>(max_smem)) != cudaSuccess) return e;
+    if ((e = configure_mp<FK, TAB, kRoundAny, PHYS, GEO>(max_smem)) != cudaSuccess) return e;
+    if ((e = configure_mp<FK, TAB, kRoundOne, PHYS, GEO>(max_smem)) != cudaSuccess) return e;
     if constexpr ((!PHYS && !GEO) || FK == GT_FIELD_PLATE) {
-        if ((e = configure_mp<FK, TAB, 2, PHYS, GEO>(max_smem)) != cudaSuccess) return e;
+        if ((e = configure_mp<FK, TAB, kRoundCommon, PHYS, GEO>(max_smem)) != cudaSuccess) return e;
     }
     if constexpr (GEO && FK == GT_FIELD_PLATE) {
-        if ((e = configure_mp<FK, TAB, 3, PHYS, GEO>(max_smem)) != cudaSuccess) return e;
-        if ((e = configure_mp<FK, TAB, 4, PHYS, GEO>(max_smem)) != cudaSuccess) return e;
+        if ((e = configure_mp<FK, TAB, kRoundCrossing, PHYS, GEO>(max_smem)) != cudaSuccess) return e;
+        if ((e = configure_mp<FK, TAB, kRoundSignal, PHYS, GEO>(max_smem)) != cudaSuccess) return e;
     }
     return allow_dynamic_smem(k_plain_transport<MixedElectron, FK, TAB, kPlainThreadsMixed, PHYS, GEO>,
                               max_smem);
@@ -215,16 +218,16 @@ static int occ(int block, size_t smem)
     cudaError_t e;
     if (block <= 512)
         e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(
-            &n, k_batched<MixedElectron, FK, TAB, 512, 0, PHYS, GEO>, block, smem);
+            &n, k_batched<MixedElectron, FK, TAB, 512, kRoundAny, PHYS, GEO>, block, smem);
     else if (block <= 768)
         e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(
-            &n, k_batched<MixedElectron, FK, TAB, 768, 0, PHYS, GEO>, block, smem);
+            &n, k_batched<MixedElectron, FK, TAB, 768, kRoundAny, PHYS, GEO>, block, smem);
     else if (block <= 896)
         e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(
-            &n, k_batched<MixedElectron, FK, TAB, 896, 0, PHYS, GEO>, block, smem);
+            &n, k_batched<MixedElectron, FK, TAB, 896, kRoundAny, PHYS, GEO>, block, smem);
     else
         e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(
-            &n, k_batched<MixedElectron, FK, TAB, 1024, 0, PHYS, GEO>, block, smem);
+            &n, k_batched<MixedElectron, FK, TAB, 1024, kRoundAny, PHYS, GEO>, block, smem);
     return e == cudaSuccess ? n : 0;
 }
 
